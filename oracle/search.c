@@ -1,0 +1,272 @@
+/*
+ * Oracle refinement loop, FP64, plain C.  TEST INFRASTRUCTURE ONLY: the
+ * product path never links or calls this file.
+ *
+ * What it computes (arXiv 2404.16322):
+ *  - Candidates of a query are the members of its probed IVF buckets
+ *    (Section II-A), visited in canonical order: probe rank, then bucket
+ *    storage order.
+ *  - For a candidate x, the partial distance after s steps is
+ *    dis'_s = sum_{j < s*dd} (q'_j - x'_j)^2 over the rotated query and the
+ *    stored rotated vector: the plain PCA partial distance of Section V-B
+ *    ("Approximate Distances"), grown dd dimensions at a time as in the loop
+ *    of Algorithm 2.
+ *  - After each step s < S the learned test of Section V-A is applied:
+ *    prune iff m1_s * dis'_s + beta_s > tau ("Incremental Correction" gives
+ *    one classifier per step).  A disabled step has m1 = 0, beta = -inf.
+ *  - A candidate that passes every test reaches d = D and gets its exact
+ *    distance sum_j (x_j - q_j)^2 from the original FP32 vectors
+ *    (Section II-A), and enters the result queue iff it beats the queue's
+ *    largest entry (Section I: tau is the largest distance in the queue).
+ *    Ties are ordered by id; tau = +inf while the queue holds fewer than K.
+ *
+ * tau schedules (the paper updates tau after every insertion and is silent
+ * on parallel order):
+ *  - SEQUENTIAL: tau is re-read before every candidate (Section I heap loop).
+ *  - WAVES: probe ranks are cut into waves [b_w, b_{w+1}) with b_0 = 0,
+ *    b_1 = first_wave, b_{w+1} = 2 b_w; every candidate of a wave is tested
+ *    against the tau left by the previous waves; survivors are then merged.
+ *  - FROZEN: every candidate is tested against a given tau_q; survivors with
+ *    exact distance <= tau_q form the result (top-K by (distance, id)).
+ */
+#include <math.h>
+#include <omp.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { MODE_SEQUENTIAL = 0, MODE_WAVES = 1, MODE_FROZEN = 2 };
+
+typedef struct {
+    double d;
+    int64_t id;
+} entry;
+
+static int entry_less(entry a, entry b) { return a.d < b.d || (a.d == b.d && a.id < b.id); }
+
+/* Result queue: the K best entries so far, kept sorted ascending. */
+typedef struct {
+    entry* e;
+    int n;
+    int K;
+} result_queue;
+
+static double queue_tau(const result_queue* q) { return q->n < q->K ? INFINITY : q->e[q->K - 1].d; }
+
+static void queue_offer(result_queue* q, entry x)
+{
+    if (q->K <= 0) return;
+    if (q->n == q->K) {
+        if (!entry_less(x, q->e[q->n - 1])) return;
+        q->n--;
+    }
+    int i = q->n;
+    while (i > 0 && entry_less(x, q->e[i - 1])) {
+        q->e[i] = q->e[i - 1];
+        i--;
+    }
+    q->e[i] = x;
+    q->n++;
+}
+
+static double exact_distance(const float* x, const float* q, int D)
+{
+    double s = 0.0;
+    for (int j = 0; j < D; j++) {
+        double t = (double)x[j] - (double)q[j];
+        s += t * t;
+    }
+    return s;
+}
+
+/* Steps s = 1..S-1 of the estimate-and-test loop.  Returns the number of
+ * steps taken (the step at which the candidate was pruned, or S-1 when it
+ * passed every test); *pruned tells which.  partials (may be NULL) receives
+ * dis'_s for every step taken. */
+static int estimate_and_test(const double* qr, const double* xs, int D, int dd, int S,
+                             const double* m1, const double* beta, double tau,
+                             int* pruned, double* partials)
+{
+    double p = 0.0;
+    *pruned = 0;
+    for (int s = 1; s < S; s++) {
+        int j1 = s * dd < D ? s * dd : D;
+        for (int j = (s - 1) * dd; j < j1; j++) {
+            double t = qr[j] - xs[j];
+            p += t * t;
+        }
+        if (partials) partials[s - 1] = p;
+        if (m1[s - 1] * p + beta[s - 1] > tau) {
+            *pruned = 1;
+            return s;
+        }
+    }
+    return S - 1;
+}
+
+static int64_t wave_end(int64_t b, int first_wave) { return b == 0 ? first_wave : 2 * b; }
+
+typedef struct {
+    int32_t D, dd, S, P, Kmax, mode, first_wave;
+    const double* Qr;
+    const float* Q;
+    const double* Xs;
+    const float* X;
+    const int64_t* ids;
+    const int64_t* list_off;
+    const int64_t* members;
+    const int32_t* probes;
+    const int32_t* nprobe;
+    const int32_t* K;
+    const double* m1;
+    const double* beta;
+    const double* tau_in;
+    int64_t* out_ids;
+    double* out_d;
+    int64_t* stats; /* per query: candidates, pruned, exact, dims scanned */
+} oracle_args;
+
+/* One candidate: estimate, test, and if it survives, its exact distance. */
+static int visit(const oracle_args* a, int64_t b, int64_t pos, double tau, entry* out, int64_t* st)
+{
+    const double* qr = a->Qr + b * a->D;
+    int pruned;
+    int steps = estimate_and_test(qr, a->Xs + pos * a->D, a->D, a->dd, a->S, a->m1, a->beta, tau,
+                                  &pruned, NULL);
+    st[0] += 1;
+    if (pruned) {
+        int64_t dims = (int64_t)steps * a->dd;
+        st[1] += 1;
+        st[3] += dims < a->D ? dims : a->D;
+        return 0;
+    }
+    st[2] += 1;
+    st[3] += a->D;
+    out->d = exact_distance(a->X + pos * a->D, a->Q + b * a->D, a->D);
+    out->id = a->ids[pos];
+    return 1;
+}
+
+static void search_one(const oracle_args* a, int64_t b)
+{
+    int K = a->K[b];
+    int np = a->nprobe[b];
+    const int32_t* pr = a->probes + b * a->P;
+    int64_t* st = a->stats + 4 * b;
+    st[0] = st[1] = st[2] = st[3] = 0;
+    result_queue q;
+    q.K = K;
+    q.n = 0;
+    q.e = (entry*)malloc(sizeof(entry) * (size_t)(K > 0 ? K : 1));
+
+    if (a->mode == MODE_SEQUENTIAL) {
+        for (int r = 0; r < np; r++) {
+            int l = pr[r];
+            for (int64_t m = a->list_off[l]; m < a->list_off[l + 1]; m++) {
+                entry e;
+                if (visit(a, b, a->members[m], queue_tau(&q), &e, st)) queue_offer(&q, e);
+            }
+        }
+    } else {
+        int64_t b0 = 0;
+        while (b0 < np) {
+            int64_t b1 = a->mode == MODE_FROZEN ? np : wave_end(b0, a->first_wave);
+            if (b1 > np) b1 = np;
+            double tau = a->mode == MODE_FROZEN ? a->tau_in[b] : queue_tau(&q);
+            int64_t cap = 0;
+            for (int64_t r = b0; r < b1; r++) cap += a->list_off[pr[r] + 1] - a->list_off[pr[r]];
+            entry* surv = (entry*)malloc(sizeof(entry) * (size_t)(cap > 0 ? cap : 1));
+            int64_t ns = 0;
+            for (int64_t r = b0; r < b1; r++) {
+                int l = pr[r];
+                for (int64_t m = a->list_off[l]; m < a->list_off[l + 1]; m++)
+                    if (visit(a, b, a->members[m], tau, &surv[ns], st)) ns++;
+            }
+            for (int64_t i = 0; i < ns; i++)
+                if (a->mode != MODE_FROZEN || surv[i].d <= tau) queue_offer(&q, surv[i]);
+            free(surv);
+            b0 = b1;
+        }
+    }
+    for (int k = 0; k < a->Kmax; k++) {
+        a->out_ids[b * a->Kmax + k] = k < q.n ? q.e[k].id : -1;
+        a->out_d[b * a->Kmax + k] = k < q.n ? q.e[k].d : INFINITY;
+    }
+    free(q.e);
+}
+
+int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t Kmax,
+                  int32_t mode, int32_t first_wave, const double* Qr, const float* Q,
+                  const double* Xs, const float* X, const int64_t* ids, const int64_t* list_off,
+                  const int64_t* members, const int32_t* probes, const int32_t* nprobe,
+                  const int32_t* K, const double* m1, const double* beta, const double* tau_in,
+                  int64_t* out_ids, double* out_d, int64_t* stats)
+{
+    if (delta_d <= 0 || S < 1 || first_wave < 1 || mode < 0 || mode > 2) return 1;
+    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, Qr, Q, Xs, X, ids, list_off,
+                     members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < B; b++) search_one(&a, b);
+    return 0;
+}
+
+/* Replay with pruning off under the WAVES schedule and record, for every
+ * candidate, its partial distances dis'_1..dis'_{S-1}, the tau it would be
+ * tested against, its exact distance, query index and id.  Row offsets per
+ * query are given by the caller (row_off[b] = first row of query b). */
+int oracle_collect(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t first_wave,
+                   const double* Qr, const float* Q, const double* Xs, const float* X,
+                   const int64_t* ids, const int64_t* list_off, const int64_t* members,
+                   const int32_t* probes, const int32_t* nprobe, const int32_t* K,
+                   const int64_t* row_off, double* partials, double* tau_out, double* dis_out,
+                   int64_t* id_out)
+{
+    if (delta_d <= 0 || S < 1 || first_wave < 1) return 1;
+    double* never = (double*)malloc(sizeof(double) * (size_t)(S > 1 ? S - 1 : 1));
+    for (int s = 0; s < S - 1; s++) never[s] = 0.0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < B; b++) {
+        const int32_t* pr = probes + b * P;
+        int np = nprobe[b];
+        result_queue q;
+        q.K = K[b];
+        q.n = 0;
+        q.e = (entry*)malloc(sizeof(entry) * (size_t)(q.K > 0 ? q.K : 1));
+        int64_t row = row_off[b];
+        int64_t b0 = 0;
+        double* neg_inf = (double*)malloc(sizeof(double) * (size_t)(S > 1 ? S - 1 : 1));
+        for (int s = 0; s < S - 1; s++) neg_inf[s] = -INFINITY;
+        while (b0 < np) {
+            int64_t b1 = wave_end(b0, first_wave);
+            if (b1 > np) b1 = np;
+            double tau = queue_tau(&q);
+            int64_t row0 = row;
+            for (int64_t r = b0; r < b1; r++) {
+                int l = pr[r];
+                for (int64_t m = list_off[l]; m < list_off[l + 1]; m++) {
+                    int64_t pos = members[m];
+                    int pruned;
+                    estimate_and_test(Qr + b * D, Xs + pos * D, D, delta_d, S, never, neg_inf, tau,
+                                      &pruned, partials + row * (S > 1 ? S - 1 : 0));
+                    tau_out[row] = tau;
+                    dis_out[row] = exact_distance(X + pos * D, Q + b * D, D);
+                    id_out[row] = ids[pos];
+                    row++;
+                }
+            }
+            for (int64_t i = row0; i < row; i++) {
+                entry e = {dis_out[i], id_out[i]};
+                queue_offer(&q, e);
+            }
+            b0 = b1;
+        }
+        free(neg_inf);
+        free(q.e);
+    }
+    free(never);
+    return 0;
+}
+
+void oracle_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+
+int oracle_max_threads(void) { return omp_get_max_threads(); }

@@ -1,0 +1,153 @@
+"""ctypes wrapper around the oracle refinement loop (``search.c``).
+
+``prepare`` lays out an oracle index from FP64 inputs (rotation, centroids,
+assignment); ``search`` runs the estimate / test / exact-distance loop of
+Section V-B with one of the tau schedules; ``collect`` replays searches with
+pruning off and records the per-step partial distances used to fit the
+correction.  Test infrastructure only.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+from . import ivf as _ivf
+from . import pca as _pca
+from . import storage as _storage
+
+MODES = {"sequential": 0, "waves": 1, "frozen": 2}
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build.build())
+        _lib.oracle_search.restype = ctypes.c_int
+        _lib.oracle_collect.restype = ctypes.c_int
+        _lib.oracle_max_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(ctypes.c_int(int(n)))
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def n_steps(D: int, delta_d: int) -> int:
+    """S = ceil(D / Delta_d): the number of Delta_d slabs covering D dims."""
+    return -(-D // delta_d)
+
+
+def disabled_tables(S: int):
+    """Pruning off at every step: m1 = 0, beta = -inf."""
+    return np.zeros(max(S - 1, 0)), np.full(max(S - 1, 0), -np.inf)
+
+
+class OracleIndex:
+    """Everything the oracle loop reads, in FP64 / original FP32."""
+
+    def __init__(self, X, mu, R, centroids_r, assign, dtype="f32", ids=None, fp8_scale=None):
+        self.X = np.ascontiguousarray(X, dtype=np.float32)
+        self.N, self.D = self.X.shape
+        self.mu = np.asarray(mu, dtype=np.float64)
+        self.R = np.asarray(R, dtype=np.float64)
+        self.C = np.asarray(centroids_r, dtype=np.float64)
+        self.nlist = self.C.shape[0]
+        self.assign = np.asarray(assign, dtype=np.int32)
+        self.ids = (np.arange(self.N, dtype=np.int64) if ids is None
+                    else np.ascontiguousarray(ids, dtype=np.int64))
+        self.dtype = dtype
+        Xr = _pca.rotate(self.X, self.mu, self.R)
+        self.Xs = np.ascontiguousarray(_storage.stored(Xr, dtype, fp8_scale))
+        self.list_off, self.members = _ivf.lists_from_assignment(self.assign, self.nlist)
+
+    def rotate_queries(self, Q):
+        return np.ascontiguousarray(_pca.rotate(Q, self.mu, self.R))
+
+    def probe(self, Qr, nprobe: int):
+        return _ivf.probe(Qr, self.C, nprobe)[0]
+
+
+def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode="waves",
+           first_wave: int = 1, tau=None):
+    """Returns (ids[B, Kmax], dists[B, Kmax], stats[B, 4]) where stats holds
+    candidates visited, candidates pruned, exact distances taken, dims scanned."""
+    lib = _load()
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    B = Q.shape[0]
+    Qr = idx.rotate_queries(Q)
+    probes = np.ascontiguousarray(probes, dtype=np.int32)
+    P = probes.shape[1]
+    nprobe = np.ascontiguousarray(np.broadcast_to(np.asarray(nprobe, np.int32), (B,)))
+    K = np.ascontiguousarray(np.broadcast_to(np.asarray(K, np.int32), (B,)))
+    Kmax = int(K.max()) if B else 0
+    S = n_steps(idx.D, delta_d)
+    m1 = np.ascontiguousarray(m1, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    assert m1.shape == (max(S - 1, 0),) and beta.shape == m1.shape
+    tau_in = np.ascontiguousarray(np.full(B, np.inf) if tau is None else tau, dtype=np.float64)
+    out_ids = np.empty((B, Kmax), dtype=np.int64)
+    out_d = np.empty((B, Kmax))
+    stats = np.zeros((B, 4), dtype=np.int64)
+    rc = lib.oracle_search(
+        ctypes.c_int64(B), ctypes.c_int32(idx.D), ctypes.c_int32(delta_d), ctypes.c_int32(S),
+        ctypes.c_int32(P), ctypes.c_int32(Kmax), ctypes.c_int32(MODES[mode]),
+        ctypes.c_int32(first_wave), _p(Qr), _p(Q), _p(idx.Xs), _p(idx.X), _p(idx.ids),
+        _p(idx.list_off), _p(idx.members), _p(probes), _p(nprobe), _p(K), _p(m1), _p(beta),
+        _p(tau_in), _p(out_ids), _p(out_d), _p(stats))
+    if rc != 0:
+        raise ValueError("oracle_search rejected its arguments")
+    return out_ids, out_d, stats
+
+
+def collect(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, first_wave: int = 1):
+    """Replay with pruning off; returns a dict of per-candidate rows:
+    partials[n, S-1], tau[n], dis[n], id[n], query[n]."""
+    lib = _load()
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    B = Q.shape[0]
+    Qr = idx.rotate_queries(Q)
+    probes = np.ascontiguousarray(probes, dtype=np.int32)
+    P = probes.shape[1]
+    nprobe = np.ascontiguousarray(np.broadcast_to(np.asarray(nprobe, np.int32), (B,)))
+    K = np.ascontiguousarray(np.broadcast_to(np.asarray(K, np.int32), (B,)))
+    sizes = np.diff(idx.list_off)
+    per_q = np.array([sizes[probes[b, :nprobe[b]]].sum() for b in range(B)], dtype=np.int64)
+    row_off = np.zeros(B + 1, dtype=np.int64)
+    np.cumsum(per_q, out=row_off[1:])
+    n = int(row_off[-1])
+    S = n_steps(idx.D, delta_d)
+    partials = np.zeros((n, max(S - 1, 0)))
+    tau = np.empty(n)
+    dis = np.empty(n)
+    ids = np.empty(n, dtype=np.int64)
+    rc = lib.oracle_collect(
+        ctypes.c_int64(B), ctypes.c_int32(idx.D), ctypes.c_int32(delta_d), ctypes.c_int32(S),
+        ctypes.c_int32(P), ctypes.c_int32(first_wave), _p(Qr), _p(Q), _p(idx.Xs), _p(idx.X),
+        _p(idx.ids), _p(idx.list_off), _p(idx.members), _p(probes), _p(nprobe), _p(K),
+        _p(row_off), _p(partials), _p(tau), _p(dis), _p(ids))
+    if rc != 0:
+        raise ValueError("oracle_collect rejected its arguments")
+    query = np.repeat(np.arange(B, dtype=np.int64), per_q)
+    return dict(partials=partials, tau=tau, dis=dis, id=ids, query=query, S=S)
+
+
+def wave_bounds(nprobe: int, first_wave: int = 1):
+    """Probe-rank boundaries of the WAVES schedule: 0, f, 2f, 4f, ... capped."""
+    b = [0]
+    while b[-1] < nprobe:
+        nxt = first_wave if b[-1] == 0 else 2 * b[-1]
+        b.append(min(nxt, nprobe))
+    return b
+

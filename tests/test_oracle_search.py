@@ -1,0 +1,199 @@
+"""Pins of the oracle refinement loop (Section I result queue, Algorithm 2 loop
+structure, Section V-A/B learned test and incremental correction)."""
+import numpy as np
+import pytest
+
+from oracle import ivf, knn, search
+
+
+def _worked_index(order_b=(3, 2, 4)):
+    # D = 4, Delta_d = 2 (S = 2: one test after two dims, then the exact
+    # distance), identity rotation, query at the origin, K = 2.
+    X = np.array([[1, 0, 1, 0],   # id 0: dis'_1 = 1, dis = 2
+                  [0, 2, 0, 0],   # id 1: dis'_1 = 4, dis = 4
+                  [1, 1, 0, 3],   # id 2: dis'_1 = 2, dis = 11
+                  [0, 1, 1, 1],   # id 3: dis'_1 = 1, dis = 3
+                  [2, 0, 0, 0]],  # id 4: dis'_1 = 4, dis = 4
+                 dtype=np.float32)
+    assign = np.array([0, 0, 1, 1, 1], dtype=np.int32)
+    idx = search.OracleIndex(X, np.zeros(4), np.eye(4), np.zeros((2, 4)), assign, dtype="f64")
+    # storage order inside list 1 chosen by the caller (3, 2, 4 by default)
+    idx.members = np.array([0, 1] + list(order_b), dtype=np.int64)
+    return idx
+
+
+def test_worked_example_by_hand():
+    """Hand evaluation with m1 = 1.75, beta = 0 (prune iff 1.75 dis'_1 > tau).
+
+    Probe order: list 0 = {0, 1}, then list 1 = {3, 2, 4}.
+    SEQUENTIAL: 0 -> dis 2 (tau inf); 1 -> dis 4, queue full, tau = 4;
+      3: 1.75 > 4? no -> dis 3 enters, tau = 3; 2: 3.5 > 3 -> pruned;
+      4: 7 > 3 -> pruned.  Result (0, 2), (3, 3); pruned 2, exact 3;
+      dims 4 + 4 + 4 + 2 + 2 = 16.
+    WAVES (first wave 1): wave 0 = list 0 at tau inf -> 2, 4, tau = 4;
+      wave 1 at tau 4: 3 -> no (dis 3); 2: 3.5 > 4? no -> dis 11 (does not
+      enter); 4: 7 > 4 -> pruned.  Same result; pruned 1, exact 4, dims 18.
+    FROZEN tau = 3.5: 0: 1.75 > 3.5? no -> 2; 1: 7 > 3.5 pruned; 3 -> 3;
+      2: 3.5 > 3.5? no -> 11 (> tau, not kept); 4 pruned.  Result (0,2),(3,3);
+      pruned 2, exact 3, dims 16.
+    """
+    idx = _worked_index()
+    Q = np.zeros((1, 4), dtype=np.float32)
+    probes = np.array([[0, 1]], dtype=np.int32)
+    m1, beta = np.array([1.75]), np.array([0.0])
+    for mode, tau, st_exp in [("sequential", None, [5, 2, 3, 16]), ("waves", None, [5, 1, 4, 18]),
+                              ("frozen", np.array([3.5]), [5, 2, 3, 16])]:
+        ids, d, st = search.search(idx, Q, probes, 2, 2, 2, m1, beta, mode=mode, tau=tau)
+        assert list(ids[0]) == [0, 3], mode
+        assert list(d[0]) == [2.0, 3.0], mode
+        assert list(st[0]) == st_exp, mode
+
+
+def test_worked_example_ties_and_padding():
+    # ids 1 and 4 are both at distance 4: with K = 3 and no pruning the third
+    # entry is id 1 (lower id wins the tie); with K = 7 the tail is padded.
+    idx = _worked_index(order_b=(4, 3, 2))
+    Q = np.zeros((1, 4), dtype=np.float32)
+    m1, beta = search.disabled_tables(2)
+    ids, d, _ = search.search(idx, Q, np.array([[1, 0]], np.int32), 2, 3, 2, m1, beta,
+                              mode="sequential")
+    assert list(ids[0]) == [0, 3, 1] and list(d[0]) == [2, 3, 4]
+    ids, d, _ = search.search(idx, Q, np.array([[0, 1]], np.int32), 2, 7, 2, m1, beta)
+    assert list(ids[0]) == [0, 3, 1, 4, 2, -1, -1]
+    assert list(d[0][:5]) == [2, 3, 4, 4, 11] and np.all(np.isinf(d[0][5:]))
+
+
+@pytest.fixture(scope="module")
+def small():
+    rng = np.random.default_rng(21)
+    D, N, nlist = 24, 3000, 12
+    X = (rng.standard_normal((N, D)) * np.linspace(3, 0.2, D)).astype(np.float32)
+    centers = X[rng.choice(N, nlist, replace=False)].astype(np.float64)
+    C, a, _ = ivf.kmeans(X.astype(np.float64), np.arange(nlist), 4)
+    a = ivf.assign(X.astype(np.float64), C)
+    del centers
+    Q = (rng.standard_normal((40, D)) * np.linspace(3, 0.2, D)).astype(np.float32)
+    idx = search.OracleIndex(X, np.zeros(D), np.eye(D), C, a, dtype="f64")
+    return dict(X=X, Q=Q, idx=idx, D=D, nlist=nlist)
+
+
+def _probed_brute_force(idx, Q, probes, K):
+    out = []
+    for b in range(len(Q)):
+        cand = np.concatenate([idx.members[idx.list_off[l]:idx.list_off[l + 1]] for l in probes[b]])
+        d = ((idx.X[cand].astype(np.float64) - Q[b].astype(np.float64)) ** 2).sum(1)
+        o = np.lexsort((cand, d))[:K]
+        out.append((cand[o], d[o]))
+    return out
+
+
+@pytest.mark.parametrize("mode", ["sequential", "waves"])
+def test_pruning_off_equals_brute_force_over_probed_candidates(small, mode):
+    idx, Q = small["idx"], small["Q"]
+    probes = idx.probe(idx.rotate_queries(Q), 4)
+    m1, beta = search.disabled_tables(search.n_steps(small["D"], 8))
+    ids, d, st = search.search(idx, Q, probes, 4, 10, 8, m1, beta, mode=mode)
+    for b, (ri, rd) in enumerate(_probed_brute_force(idx, Q, probes, 10)):
+        # FP64 sums in another order: equal up to rounding
+        assert np.array_equal(ids[b], ri) and np.allclose(d[b], rd, rtol=1e-13, atol=0)
+    assert np.all(st[:, 1] == 0) and np.all(st[:, 2] == st[:, 0])
+
+
+def test_all_lists_probed_equals_exact_knn(small):
+    idx, Q = small["idx"], small["Q"]
+    probes = idx.probe(idx.rotate_queries(Q), small["nlist"])
+    m1, beta = search.disabled_tables(search.n_steps(small["D"], 8))
+    ids, d, _ = search.search(idx, Q, probes, small["nlist"], 10, 8, m1, beta)
+    gi, gd = knn.exact_knn(small["X"], Q, 10)
+    assert np.array_equal(ids, gi) and np.allclose(d, gd, rtol=1e-13, atol=0)
+
+
+def test_exact_safe_tables_match_pruning_off_for_every_schedule(small):
+    # m1 = 1, beta = 0 prunes iff dis'_s > tau.  dis'_s <= dis (a partial sum
+    # of the same non-negative terms after an orthogonal rotation) and every
+    # schedule's tau is >= the final K-th distance, so nothing in the final
+    # result is ever pruned.
+    idx, Q = small["idx"], small["Q"]
+    probes = idx.probe(idx.rotate_queries(Q), 6)
+    S = search.n_steps(small["D"], 8)
+    off = search.disabled_tables(S)
+    safe = (np.ones(S - 1), np.zeros(S - 1))
+    ref_ids, ref_d, _ = search.search(idx, Q, probes, 6, 10, 8, *off)
+    for mode, fw in [("sequential", 1), ("waves", 1), ("waves", 2), ("waves", 6)]:
+        ids, d, st = search.search(idx, Q, probes, 6, 10, 8, *safe, mode=mode, first_wave=fw)
+        assert np.array_equal(ids, ref_ids) and np.array_equal(d, ref_d)
+    ids, d, st = search.search(idx, Q, probes, 6, 10, 8, *safe, mode="frozen", tau=ref_d[:, -1])
+    assert np.array_equal(ids, ref_ids) and np.array_equal(d, ref_d)
+    assert st[:, 1].sum() > 0  # and it does prune
+
+
+def test_containment_of_unprunable_true_neighbours(small):
+    # tau under any schedule is >= tau_F (final K-th distance); the test is
+    # monotone in tau, so every exact top-K member that survives a frozen
+    # test at tau_F is returned by every schedule.
+    idx, Q = small["idx"], small["Q"]
+    probes = idx.probe(idx.rotate_queries(Q), 6)
+    S = search.n_steps(small["D"], 8)
+    aggressive = (np.full(S - 1, 1.6), np.full(S - 1, 2.0))
+    ref_ids, ref_d, _ = search.search(idx, Q, probes, 6, 10, 8, *search.disabled_tables(S))
+    fz_ids, _, _ = search.search(idx, Q, probes, 6, 10, 8, *aggressive, mode="frozen",
+                                 tau=ref_d[:, -1])
+    for mode in ["sequential", "waves"]:
+        ids, _, st = search.search(idx, Q, probes, 6, 10, 8, *aggressive, mode=mode)
+        assert st[:, 1].sum() > 0
+        for b in range(len(Q)):
+            A = set(ref_ids[b]) & set(fz_ids[b][fz_ids[b] >= 0])
+            assert A <= set(ids[b])
+
+
+def test_partial_distances_monotone_lower_bounds(small):
+    idx, Q = small["idx"], small["Q"]
+    probes = idx.probe(idx.rotate_queries(Q[:10]), 3)
+    rows = search.collect(idx, Q[:10], probes, 3, 10, 8)
+    P = rows["partials"]
+    assert np.all(np.diff(P, axis=1) >= 0)
+    assert np.all(P[:, -1] <= rows["dis"] * (1 + 1e-12) + 1e-12)
+    # adding the last slab closes the gap exactly (f64 storage, identity R)
+    last = ((idx.Xs[np.searchsorted(idx.ids, rows["id"])][:, 16:] -
+             idx.rotate_queries(Q[:10])[rows["query"]][:, 16:]) ** 2).sum(1)
+    assert np.allclose(P[:, -1] + last, rows["dis"], rtol=1e-12, atol=1e-12)
+
+
+def test_collect_tau_is_the_waves_schedule_tau(small):
+    idx, Q = small["idx"], small["Q"]
+    probes = idx.probe(idx.rotate_queries(Q[:5]), 5)
+    rows = search.collect(idx, Q[:5], probes, 5, 10, 8, first_wave=1)
+    for b in range(5):
+        r = rows["query"] == b
+        n0 = idx.list_off[probes[b, 0] + 1] - idx.list_off[probes[b, 0]]
+        tb = rows["tau"][r]
+        assert np.all(np.isinf(tb[:n0]))
+        if n0 >= 10:
+            assert tb[n0] == np.sort(rows["dis"][r][:n0])[9]
+
+
+def test_rotation_invariance_of_results(small):
+    # An orthogonal rotation changes partial distances but not exact ones:
+    # with pruning off the result is the same under any rotation.
+    idx0, Q = small["idx"], small["Q"]
+    rng = np.random.default_rng(8)
+    Rq, _ = np.linalg.qr(rng.standard_normal((small["D"], small["D"])))
+    mu = rng.standard_normal(small["D"])
+    idx1 = search.OracleIndex(small["X"], mu, Rq, (idx0.C - 0) @ Rq.T - mu @ Rq.T,
+                              idx0.assign, dtype="f64")
+    probes = idx0.probe(idx0.rotate_queries(Q), 4)
+    S = search.n_steps(small["D"], 8)
+    a = search.search(idx0, Q, probes, 4, 10, 8, *search.disabled_tables(S))
+    b = search.search(idx1, Q, probes, 4, 10, 8, *search.disabled_tables(S))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_integer_data_gives_integer_distances():
+    rng = np.random.default_rng(2)
+    X = rng.integers(0, 256, size=(500, 16)).astype(np.float32)
+    Q = rng.integers(0, 256, size=(4, 16)).astype(np.float32)
+    idx = search.OracleIndex(X, np.zeros(16), np.eye(16), np.zeros((1, 16)),
+                             np.zeros(500, np.int32))
+    ids, d, _ = search.search(idx, Q, np.zeros((4, 1), np.int32), 1, 20, 8,
+                              *search.disabled_tables(2))
+    assert np.all(d == np.rint(d)) and np.all(d < 2 ** 24)
