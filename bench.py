@@ -1,0 +1,468 @@
+#!/usr/bin/env python
+"""Benchmark: queries/s at recall@10 >= 0.95 of the estimate-and-prune IVF
+search (SIFT-shaped 1M x 128, nlist 4096, K 100) on one GB300, next to the
+full-dimension FP32 IVF scan on the same GPU and the oracle on host cores.
+
+One "step" is one dade_search over the whole 10,000-query batch (rotation,
+centroid scan, top-nprobe, work units, every wave's estimate-and-prune scan
+and top-K merge, output), with the batch and the index resident in HBM.
+The index (1.0 GB of slabs and original vectors) is larger than L2 (129 MB).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank runs its own replica of the workload on its GPU
+(the search is replicated, not sharded); value = all ranks' queries / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TARGET_RECALL = 0.95
+NPROBES = [8, 12, 16, 24, 32, 48, 64, 96, 128]
+DELTAS = [8, 16, 32]
+METRIC = "QPS at recall@10>=0.95 (estimate-and-prune IVF search, SIFT-shaped 1M x 128, nlist 4096, K 100)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=None, help="database size override (debug)")
+    ap.add_argument("--queries", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-queries", type=int, default=400)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running (SM clock, reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        self.marks = []
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- workload
+def make_workload(n=None, nq=None):
+    import synth
+    X, Q, T, cfg = synth.workload("sift1m", N=n, n_queries=nq)
+    return X, Q, T, cfg
+
+
+def ground_truth(X, Q, k=10, chunk=1024):
+    """Exact top-k by brute force: torch GEMM-based shortlist of 64 on the GPU,
+    then FP64 re-ranking of the shortlist on the host (plumbing for the
+    recall metric, not the measured path)."""
+    import torch
+    dev = torch.device("cuda")
+    Xt = torch.from_numpy(X).to(dev)
+    xn = (Xt * Xt).sum(1)
+    out = np.empty((len(Q), k), np.int64)
+    for a in range(0, len(Q), chunk):
+        q = torch.from_numpy(Q[a:a + chunk]).to(dev)
+        d = xn[None, :] - 2.0 * (q @ Xt.T)
+        cand = torch.topk(d, 64, dim=1, largest=False).indices.cpu().numpy()
+        for i in range(cand.shape[0]):
+            c = cand[i]
+            dd = ((X[c].astype(np.float64) - Q[a + i].astype(np.float64)) ** 2).sum(1)
+            o = np.lexsort((c, dd))[:k]
+            out[a + i] = c[o]
+        del d
+    del Xt
+    torch.cuda.empty_cache()
+    return out
+
+
+def recall_at(ids, gt, k=10):
+    hit = 0
+    for b in range(len(gt)):
+        hit += len(set(ids[b, :k].tolist()) & set(gt[b, :k].tolist()))
+    return hit / (k * len(gt))
+
+
+class Runner:
+    """Device-resident batch and outputs for repeated dade_search calls."""
+
+    def __init__(self, G, idx, Q, K, max_nprobe):
+        import torch
+        self.G, self.idx, self.torch = G, idx, torch
+        dev = torch.device("cuda")
+        self.B = len(Q)
+        self.K = K
+        self.q = torch.from_numpy(Q).to(dev)
+        self.k = torch.full((self.B,), K, dtype=torch.int32, device=dev)
+        self.np = torch.zeros(self.B, dtype=torch.int32, device=dev)
+        self.ids = torch.empty(self.B * K, dtype=torch.int64, device=dev)
+        self.d = torch.empty(self.B * K, dtype=torch.float32, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.stats = torch.zeros((self.B, 4), dtype=torch.int64, device=dev)
+        ws = max(G.dade_search_workspace_size(idx, self.B, 16, K, max_nprobe, mode=m) for m in ("prune", "full"))
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.max_nprobe = max_nprobe
+
+    def run(self, nprobe, delta_d, mode, stats=False):
+        self.np.fill_(nprobe)
+        if stats:
+            self.stats.zero_()
+        self.G.dade_search(self.idx, self.q, self.k, self.np, delta_d, self.ids, self.d, max_K=self.K,
+                           max_nprobe=self.max_nprobe, mode=mode, status=self.status,
+                           stats=self.stats if stats else None, workspace=self.ws)
+
+    def result(self):
+        self.torch.cuda.synchronize()
+        assert int(self.status.item()) == 0, f"device status {int(self.status.item())}"
+        return self.ids.view(self.B, self.K).cpu().numpy()
+
+    def time(self, nprobe, delta_d, mode, steps, warmup):
+        torch = self.torch
+        for _ in range(warmup):
+            self.run(nprobe, delta_d, mode)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for e0, e1 in evs:
+            e0.record()
+            self.run(nprobe, delta_d, mode)
+            e1.record()
+        t1.record()
+        torch.cuda.synchronize()
+        per = [a.elapsed_time(b) for a, b in evs]
+        return t0.elapsed_time(t1), per
+
+
+def n_waves(nprobe, first_wave=1):
+    b, w = 0, 0
+    while b < nprobe:
+        b = first_wave if b == 0 else 2 * b
+        w += 1
+    return w
+
+
+def traffic_from_profiles(kernel_src_hash):
+    """Per-launch DRAM bytes of the scan kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "wave_scan_sift1m.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"kernel source sha256: ([0-9a-f]{12})", txt)
+    t = re.search(r"dram bytes per launch \(full-size equivalent\): ([0-9.e+]+)", txt)
+    if not m or not t or m.group(1) != kernel_src_hash:
+        return None
+    return float(t.group(1))
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ["scan.cu", "scan.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_2404_16322_gb300", "csrc", "kernels", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, seed_queries=None, steps=1):
+    """The oracle (plain FP64 C loop, all host threads) on a bounded sample of
+    the workload: a 100k-vector instance of the same mixture with the same
+    bucket size (nlist 410, ~244 vectors per bucket), the same nprobe, K and
+    Delta_d, its own PCA, k-means (2 Lloyd iterations) and fitted tables."""
+    import synth
+    from oracle import fit, ivf, pca, search
+    spec = synth.WORKLOADS["sift1m"]["spec"]
+    N = 100_000
+    nlist = max(1, round(N / (cfg_full["N"] / cfg_full["nlist"])))
+    X = spec.sample(N, synth.mixtures.SEED_DATA)
+    Q = spec.sample(n_queries * max(1, steps), synth.mixtures.SEED_QUERIES)
+    T = spec.sample(200, synth.mixtures.SEED_TRAIN)
+    mu, R, _ = pca.train_rotation(X)
+    Xr = pca.rotate(X, mu, R)
+    init = np.random.default_rng(1).choice(N, nlist, replace=False)
+    C, a, _ = ivf.kmeans(Xr, init, 2)
+    oidx = search.OracleIndex(X, mu, R, C, a, dtype="f32")
+    S = search.n_steps(oidx.D, delta_d)
+    prt = oidx.probe(oidx.rotate_queries(T), nprobe)
+    rows = search.collect(oidx, T, prt, nprobe, K, delta_d)
+    top, _, _ = search.search(oidx, T, prt, nprobe, K, delta_d, *search.disabled_tables(S))
+    P, tau, lab = fit.label_rows(rows, top, cap=200_000)
+    m1, beta, _ = fit.fit_correction(P, tau, lab, oidx.D, delta_d, min_label0=20)
+    del rows, P
+    threads = search.max_threads()
+    search.set_threads(threads)
+    times = []
+    for s in range(max(1, steps)):
+        q = Q[s * n_queries:(s + 1) * n_queries]
+        t0 = time.perf_counter()
+        pr = oidx.probe(oidx.rotate_queries(q), nprobe)  # probing is part of the query
+        search.search(oidx, q, pr, nprobe, K, delta_d, m1, beta)
+        times.append(time.perf_counter() - t0)
+    qps = n_queries / float(np.median(times))
+    sample = (f"oracle FP64 C loop on {n_queries} queries per step against a {N}-vector SIFT-shaped instance "
+              f"(nlist {nlist}, ~{N // nlist}/bucket like the full 1M/4096), nprobe {nprobe}, K {K}, "
+              f"delta_d {delta_d}; probing included")
+    return dict(value=qps, unit="queries/s", cores=threads, kind="oracle", sample=sample), times
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    cfg = dict(synth.WORKLOADS["sift1m"])
+    n_q = 40
+    t0 = time.perf_counter()
+    cb, times = oracle_baseline(cfg, 64, 16, 100, n_q, steps=args.steps + args.warmup)
+    wall = time.perf_counter() - t0
+    timed = times[args.warmup:] or times
+    ms = 1000.0 * float(np.mean(timed))
+    value = n_q / (ms / 1000.0)
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sift1m-shaped sample (see cpu_baseline.sample)", "nprobe": 64, "K": 100,
+                       "delta_d": 16},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- main arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2404_16322_gb300 as G
+    from paper_2404_16322_gb300 import build as gbuild
+    gbuild.build()
+
+    t_setup = time.perf_counter()
+    X, Q, T, cfg = make_workload(args.n, args.queries)
+    K, nlist = cfg["K"], cfg["nlist"]
+    if args.n is not None:
+        nlist = max(16, int(round(args.n / 244)))
+    mean, R, _ = G.dade_train_rotation(X, sample_n=min(len(X), 1_000_000), seed=1)
+    idx = G.ivf_build(X, mean, R, nlist, kmeans_iters=10, seed=1, dtype="f32")
+    fit_nprobe = min(64, nlist)
+    for dd in DELTAS:
+        G.dade_fit_correction(idx, T, K, fit_nprobe, dd, target_recall=0.995, seed=1)
+    gt = ground_truth(X, Q, 10)
+    setup_s = time.perf_counter() - t_setup
+
+    maxp = min(max(NPROBES), nlist)
+    run = Runner(G, idx, Q, K, maxp)
+    # --- sweep: recall per (mode, delta_d, nprobe); short timing of each
+    sweep = []
+    for mode, dds in (("full", [0]), ("prune", DELTAS)):
+        for dd in dds:
+            for npb in [p for p in NPROBES if p <= maxp]:
+                run.run(npb, dd, mode)
+                rec = recall_at(run.result(), gt)
+                total, per = run.time(npb, dd, mode, 5, 2)
+                sweep.append(dict(mode=mode, delta_d=dd, nprobe=npb, recall=rec, ms=float(np.median(per))))
+                if rec >= TARGET_RECALL + 0.02:
+                    break
+
+    def best(mode):
+        ok = [s for s in sweep if s["mode"] == mode and s["recall"] >= TARGET_RECALL]
+        return min(ok, key=lambda s: s["ms"]) if ok else max((s for s in sweep if s["mode"] == mode),
+                                                              key=lambda s: s["recall"])
+
+    bd, bf = best("prune"), best("full")
+
+    # --- timed region: exactly K steps of the chosen configuration
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    sampler = ClockSampler(local)
+    for _ in range(args.warmup):
+        run.run(bd["nprobe"], bd["delta_d"], "prune")
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, per = run.time(bd["nprobe"], bd["delta_d"], "prune", args.steps, 0)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * run.B / (ms_step / 1000.0)
+
+    # --- full-scan reference point on the same GPU, same timing
+    f_total, f_per = run.time(bf["nprobe"], 0, "full", args.steps, args.warmup)
+    full_qps = run.B / (f_total / args.steps / 1000.0)
+
+    # --- stage timing of the dominant kernel (the refinement scan)
+    G.dade_stage_timing(True)
+    G.dade_stage_timing_read()
+    for _ in range(args.steps):
+        run.run(bd["nprobe"], bd["delta_d"], "prune")
+    scan_ms, scan_launches, scan_bytes = G.dade_stage_timing_read()
+    G.dade_stage_timing(False)
+    per_launch_ms = scan_ms / max(1, scan_launches)
+    per_launch_bytes = scan_bytes / max(1, scan_launches)
+    peak, peak_kind = peaks()
+    achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
+    khash = kernel_hash()
+    traffic = traffic_from_profiles(khash)
+
+    # --- work accounting (bytes per query) for both modes
+    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True)
+    run.result()
+    st = run.stats.cpu().numpy()
+    S = G.n_steps(128, bd["delta_d"])
+    pruned_dims = st[:, 3] - st[:, 2] * 128
+    dade_bytes = (pruned_dims * 4 + st[:, 2] * ((S - 1) * bd["delta_d"] * 4 + 128 * 4)).sum() / run.B
+    run.run(bf["nprobe"], 0, "full", stats=True)
+    run.result()
+    stf = run.stats.cpu().numpy()
+    full_bytes = (stf[:, 0] * 128 * 4).sum() / run.B
+    scan_ratio = st[:, 3].sum() / (st[:, 0].sum() * 128)
+
+    # --- end to end through the C ABI with host buffers
+    q_h = torch.from_numpy(Q).pin_memory()
+    k_h = torch.full((run.B,), K, dtype=torch.int32).pin_memory()
+    n_h = torch.full((run.B,), bd["nprobe"], dtype=torch.int32).pin_memory()
+    ids_h = torch.empty(run.B * K, dtype=torch.int64).pin_memory()
+    d_h = torch.empty(run.B * K, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        run.q.copy_(q_h, non_blocking=True)
+        run.k.copy_(k_h, non_blocking=True)
+        run.np.copy_(n_h, non_blocking=True)
+        G.dade_search(idx, run.q, run.k, run.np, bd["delta_d"], run.ids, run.d, max_K=K, max_nprobe=maxp,
+                      status=run.status, workspace=run.ws)
+        ids_h.copy_(run.ids, non_blocking=True)
+        d_h.copy_(run.d, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_qps = world * run.B / (e2e_ms / 1000.0)
+    h2d = Q.nbytes + 2 * run.B * 4
+    d2h = run.B * K * (8 + 4)
+    assert np.array_equal(ids_h.view(run.B, K).numpy()[:, :10], run.result()[:, :10])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K, args.cpu_sample_queries)
+
+    launches = 11 + 2 * n_waves(bd["nprobe"])
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"sift1m-shaped: N={len(X)}, D=128 integer [0,255], 256-comp mixture lambda~i^-0.8; "
+                               f"B={run.B} queries; nlist={nlist}, K={K}",
+                   "nprobe": bd["nprobe"], "delta_d": bd["delta_d"], "slabs": "f32", "recall@10": bd["recall"],
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (index 1.0 GB > 129 MB L2)"},
+        "full_scan": {"value": full_qps, "unit": "queries/s", "nprobe": bf["nprobe"], "recall@10": bf["recall"]},
+        "speedup_vs_full_scan": value / world / full_qps,
+        "bytes_per_query": {"prune": dade_bytes, "full_scan": full_bytes, "ratio": dade_bytes / full_bytes},
+        "scanned_dims_ratio": scan_ratio,
+        "latency_ms": {"batch_p50": float(np.percentile(per, 50)), "batch_p99": float(np.percentile(per, 99))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "wave_scan_kernel", "per_launch_ms": per_launch_ms,
+                     "algorithmic_bytes_per_launch": per_launch_bytes, "launches": scan_launches},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+        "sweep": sweep,
+        "setup_s": setup_s,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,264 @@
+/*
+ * dade.h -- C ABI of the GB300 data-aware distance estimation library.
+ *
+ * Method: "Effective and General Distance Computation for Approximate Nearest
+ * Neighbor Search" (arXiv 2404.16322).  The database and the queries are
+ * rotated by a PCA matrix learned from the data (Section IV-B, Theorem 1);
+ * IVF buckets supply the candidates (Section II-A); each candidate's squared
+ * L2 distance is accumulated Delta_d rotated dimensions at a time (the loop
+ * of Algorithm 2) and after each step the learned test
+ * m1_s * dis' + beta_s > tau decides whether to prune it (Section V-A, V-B
+ * "Incremental Correction"); a candidate that passes every test gets its
+ * exact distance and competes for the result queue whose largest entry is
+ * tau (Section I).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a dade_status; none aborts or exits.  On failure
+ *    dade_last_error() gives a message (per calling thread).
+ *  - Pointers named *_host are host memory, *_dev device memory of the
+ *    current CUDA device.  The caller owns every buffer it passes and the
+ *    library never frees or retains them past the call (device buffers
+ *    passed to dade_search must stay valid until the stream reaches the end
+ *    of the call's work).
+ *  - Matrices are row-major, float32 unless stated, with no padding between
+ *    rows.  D is the dimensionality of the vectors (1 <= D <= 4096).
+ *  - A dade_index is owned by the library: create it with ivf_build or
+ *    dade_index_load and release it with dade_index_free.  Its data live in
+ *    device memory of the device that was current when it was created.
+ */
+#ifndef DADE_H
+#define DADE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dade_index dade_index;
+
+typedef enum {
+    DADE_OK = 0,
+    DADE_EINVAL = 1,   /* an argument is out of range or inconsistent        */
+    DADE_ENOMEM = 2,   /* a host or device allocation failed                 */
+    DADE_ECUDA = 3,    /* a CUDA runtime call failed                         */
+    DADE_ETIMEOUT = 4, /* a bounded device wait gave up (status word)        */
+    DADE_ESTATE = 5,   /* the index lacks what the call needs (e.g. table)   */
+    DADE_ENOTIMPL = 6, /* the combination of options is not supported        */
+    DADE_EIO = 7       /* file read/write failed or the file is malformed    */
+} dade_status;
+
+/* Precision of the rotated slabs read by the estimate-and-prune stage.  The
+ * exact distance always uses the original FP32 vectors. */
+typedef enum {
+    DADE_SLAB_F32 = 0,
+    DADE_SLAB_BF16 = 1,    /* round-to-nearest-even of the FP32 value       */
+    DADE_SLAB_FP8E4M3 = 2  /* per-dimension scale amax_j / 448, RNE, saturate */
+} dade_slab_dtype;
+
+/* ------------------------------------------------------------------------
+ * dade_train_rotation -- PCA rotation (Section IV-B, Theorem 1; data centred
+ * per the footnote to Section IV-B).
+ *
+ * X_host: n x D FP32 rows.  If 0 < sample_n < n, a seeded uniform sample of
+ * sample_n distinct rows is used (the paper samples 1M rows for large sets,
+ * Section VII "Exp-1"); otherwise every row.  Computes, in FP64 on the host,
+ * mean_out[D], the covariance 1/(m-1) sum (x-mean)(x-mean)^T and its
+ * eigendecomposition (cyclic Jacobi): eigvals_out[D] descending and R_out
+ * [D x D] whose row i is the i-th eigenvector, with the sign making the
+ * entry of largest magnitude in each row positive.  All outputs are host
+ * buffers owned by the caller.  Errors: DADE_EINVAL (n < 2, D out of range,
+ * null pointers), DADE_ENOMEM.
+ * ---------------------------------------------------------------------- */
+dade_status dade_train_rotation(const float* X_host, int64_t n, int32_t D, int64_t sample_n,
+                                uint64_t seed, double* mean_out, double* R_out,
+                                double* eigvals_out);
+
+/* ------------------------------------------------------------------------
+ * ivf_build -- rotate the database and build the IVF index (Section II-A).
+ *
+ * X_host: N x D FP32 rows; mean[D], R[D x D] FP64 from dade_train_rotation
+ * (or any orthogonal matrix).  The rows are rotated on the device,
+ * x' = R (x - mean), clustered into nlist buckets by Lloyd k-means in the
+ * rotated space (kmeans_iters iterations from a seeded sample of nlist
+ * rows; a point goes to the nearest centroid, the lower id on a tie; an
+ * empty bucket keeps its centroid), and laid out per bucket:
+ *  - rotated slabs, dimension-blocked: 8 dimensions per block, block b of
+ *    the bucket's vector i at ((b * npad + i) * 8 + j) elements from the
+ *    bucket's base, npad = bucket size rounded up to 32, in params->dtype;
+ *  - the original FP32 vectors in the same blocked layout (exact distance);
+ *  - the ids (params->ids, or the row numbers when NULL) as int64.
+ * Inside a bucket, vectors keep increasing row order.  params->centroids
+ * (nlist x D rotated-space FP32, host) replaces k-means when non-NULL;
+ * params->assign (N bucket ids, host) also replaces the assignment.
+ * Errors: DADE_EINVAL, DADE_ENOMEM, DADE_ECUDA.  *out is set only on success.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t nlist;
+    int32_t kmeans_iters;
+    uint64_t seed;
+    dade_slab_dtype dtype;
+    const float* centroids;  /* optional, host, nlist x D (rotated space) */
+    const int32_t* assign;   /* optional, host, N (needs centroids)       */
+    const int64_t* ids;      /* optional, host, N                         */
+} dade_build_params;
+
+dade_status ivf_build(const float* X_host, int64_t N, int32_t D, const double* mean,
+                      const double* R, const dade_build_params* params, dade_index** out);
+
+/* ------------------------------------------------------------------------
+ * Correction tables.  For a step width delta_d (a multiple of 8) the index
+ * holds S - 1 pairs (m1_s, beta_s), S = ceil(D / delta_d): after s slabs the
+ * candidate is pruned iff m1_s * dis'_s + beta_s > tau (Section V-A, one
+ * classifier per step as in "Incremental Correction", Section V-B).  m1 = 0,
+ * beta = -inf disables a step.
+ *
+ * dade_fit_correction learns them (Section V-A "Parameter Learning" and
+ * "Adaptive Adjustment", labels per Section VII-A): train_q_host (nt x D
+ * FP32) are searched with pruning off under the same tau schedule as
+ * dade_search (nprobe, K, first wave 1); every candidate tested against a
+ * finite tau gives a sample (dis'_1..dis'_{S-1}, tau) labelled 0 if it is in
+ * the query's exact top-K, 1 if its exact distance exceeds tau (others are
+ * dropped); label-1 samples are thinned to about label1_cap by a
+ * counter-based SplitMix64 draw of (seed, query, id).  Then, per step on the
+ * samples no earlier step prunes, an FP64 logistic regression on
+ * (dis'/tau_bar, tau/tau_bar) gives m1 = -w1/w2, and beta' is the largest
+ * value keeping label-0 recall >= r_s = 1 - (1 - target_recall) / S.
+ * m1_out / beta_out (host, S - 1 floats, may be NULL) receive the table,
+ * which is also installed in the index.  Steps with w2 >= 0, fewer than 100
+ * label-0 samples or no label-1 sample are disabled.
+ * Errors: DADE_EINVAL, DADE_ENOMEM, DADE_ECUDA.
+ *
+ * dade_fit_samples runs the host FP64 fit alone on caller samples:
+ * partials (n x (S-1)), tau (n), label (n: 0 or 1); outputs S - 1 doubles.
+ *
+ * dade_set_correction installs a caller table (host floats, S - 1 each).
+ * dade_get_correction copies the installed table out (DADE_ESTATE if none).
+ * ---------------------------------------------------------------------- */
+dade_status dade_fit_correction(dade_index* idx, const float* train_q_host, int64_t nt,
+                                int32_t K, int32_t nprobe, int32_t delta_d,
+                                double target_recall, uint64_t seed, int64_t label1_cap,
+                                float* m1_out, float* beta_out);
+
+dade_status dade_fit_samples(const double* partials, const double* tau, const int8_t* label,
+                             int64_t n, int32_t D, int32_t delta_d, double target_recall,
+                             int32_t min_label0, double* m1_out, double* beta_out);
+
+dade_status dade_set_correction(dade_index* idx, int32_t delta_d, const float* m1_host,
+                                const float* beta_host);
+
+dade_status dade_get_correction(const dade_index* idx, int32_t delta_d, float* m1_host,
+                                float* beta_host);
+
+/* ------------------------------------------------------------------------
+ * dade_search -- batched AKNN search on one stream.
+ *
+ * Q_dev: B x D FP32 queries.  K_dev[B], nprobe_dev[B]: per-query K
+ * (1..opts->max_K) and nprobe (1..min(opts->max_nprobe, nlist)).
+ * Pipeline, all on cuda_stream (a cudaStream_t; NULL = legacy default):
+ *  1. q' = R (q - mean) for every query (Section IV-A x_D = R x).
+ *  2. squared distance of q' to every centroid; the nprobe nearest, ordered
+ *     by (distance, list id), are the query's buckets (Section II-A).
+ *  3. probe ranks are cut into waves [b_w, b_{w+1}): b_0 = 0,
+ *     b_1 = first_wave, b_{w+1} = 2 b_w.  Every candidate of wave w is tested
+ *     against the query's tau at the end of wave w - 1 (tau = +inf before the
+ *     queue holds K entries), in parallel over (bucket, query) work units.
+ *  4. mode DADE_SCAN_PRUNE: the candidate's partial distance over the rotated
+ *     slabs grows delta_d dims per step and the installed table for delta_d
+ *     decides pruning after each of the first S - 1 steps; survivors get the
+ *     exact FP32 distance from the original vectors.  mode DADE_SCAN_FULL:
+ *     every candidate gets the exact FP32 distance (no estimate, no table).
+ *  5. candidates with exact distance <= tau join the query's top-K, ordered
+ *     by (distance, id); tau becomes its K-th distance.
+ * Outputs: for query b, ids_dev / dists_dev at [off_b, off_b + K_b) with
+ * off = out_offsets_dev (B + 1 int64 prefix of K) or, when it is NULL,
+ * off_b = b * max_K.  Fewer than K results pad with id -1 and +inf.
+ * The call is asynchronous: it enqueues work and returns.  It performs no
+ * host synchronisation; with opts->workspace given it allocates nothing.
+ * Errors found on the host return at once (DADE_EINVAL, DADE_ESTATE when
+ * delta_d has no table in PRUNE mode, DADE_ECUDA on a launch failure).
+ * Errors found on the device (K or nprobe out of range, a timed-out wait)
+ * set the int32 at opts->status_dev (if given) to a nonzero dade_status;
+ * it is never cleared by the library.
+ * ---------------------------------------------------------------------- */
+typedef enum { DADE_SCAN_PRUNE = 0, DADE_SCAN_FULL = 1 } dade_scan_mode;
+
+typedef struct {
+    int32_t mode;            /* dade_scan_mode                                    */
+    int32_t max_K;           /* required: bound on K_dev[b], <= 1024              */
+    int32_t max_nprobe;      /* required: bound on nprobe_dev[b]                  */
+    int32_t first_wave;      /* buckets in the first wave; 0 means 1              */
+    const float* tau_dev;    /* optional B floats: one frozen tau per query and a */
+                             /* single wave (candidates with exact dist > tau are */
+                             /* dropped).  NULL: the wave schedule above.         */
+    const int32_t* probe_in_dev; /* optional B x max_nprobe: given buckets       */
+    int32_t* probe_out_dev;  /* optional B x max_nprobe: buckets probed           */
+    float* qrot_out_dev;     /* optional B x D: the rotated queries q'            */
+    int64_t* stats_dev;      /* optional B x 4, accumulated: candidates, pruned,  */
+                             /* exact distances, rotated+exact dims scanned       */
+    int32_t* status_dev;     /* optional int32 device status word                 */
+    void* workspace;         /* optional device scratch of workspace_bytes        */
+    size_t workspace_bytes;
+} dade_search_opts;
+
+dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,
+                        const int32_t* K_dev, const int32_t* nprobe_dev, int32_t delta_d,
+                        const dade_search_opts* opts, int64_t* ids_dev, float* dists_dev,
+                        const int64_t* out_offsets_dev, void* cuda_stream);
+
+/* Device scratch bytes dade_search needs for B queries with these bounds
+ * (the same opts fields as dade_search reads).  0 on invalid arguments. */
+size_t dade_search_workspace_size(const dade_index* idx, int64_t B, int32_t delta_d,
+                                  const dade_search_opts* opts);
+
+/* ------------------------------------------------------------------------
+ * Index inspection, persistence and release.
+ * dade_index_info fills the sizes.  dade_index_centroids copies the
+ * nlist x D rotated-space centroids to the host; dade_index_assignment the
+ * bucket of each input row (N int32, host); dade_index_list_sizes the
+ * nlist bucket sizes (int64, host).
+ * dade_index_save writes a versioned binary file (header, rotation, mean,
+ * centroids, buckets, slabs, original vectors, ids, correction tables, and
+ * an FNV-1a checksum); dade_index_load reads it back onto the current device
+ * and reproduces identical search results.  Errors: DADE_EIO, DADE_ENOMEM,
+ * DADE_ECUDA, DADE_EINVAL.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int64_t N;
+    int32_t D;
+    int32_t Dpad;       /* D rounded up to a multiple of 8 */
+    int32_t nlist;
+    int32_t dtype;      /* dade_slab_dtype */
+    int64_t max_list;   /* largest bucket */
+    int64_t device_bytes;
+} dade_index_info;
+
+dade_status dade_index_info_get(const dade_index* idx, dade_index_info* out);
+dade_status dade_index_centroids(const dade_index* idx, float* centroids_host);
+dade_status dade_index_assignment(const dade_index* idx, int32_t* assign_host);
+dade_status dade_index_list_sizes(const dade_index* idx, int64_t* sizes_host);
+dade_status dade_index_save(const dade_index* idx, const char* path);
+dade_status dade_index_load(const char* path, dade_index** out);
+void dade_index_free(dade_index* idx);
+
+/* ------------------------------------------------------------------------
+ * Stage timing (tracing).  dade_stage_timing(1) makes every later
+ * dade_search record a CUDA event pair around each refinement-scan launch
+ * (on the search's stream) and count the bytes that launch stages from
+ * device memory (slab blocks copied to shared memory plus original vectors
+ * read for exact distances); dade_stage_timing(0) stops.
+ * dade_stage_timing_read synchronises the recorded events and returns the
+ * summed milliseconds, the number of launches and the staged bytes since the
+ * last read, then resets them.  Process-wide; not for concurrent searches.
+ * ---------------------------------------------------------------------- */
+dade_status dade_stage_timing(int32_t enable);
+dade_status dade_stage_timing_read(double* scan_ms, int64_t* scan_launches, double* scan_bytes);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dade_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DADE_H */

@@ -85,7 +85,7 @@ static double exact_distance(const float* x, const float* q, int D)
  * dis'_s for every step taken. */
 static int estimate_and_test(const double* qr, const double* xs, int D, int dd, int S,
                              const double* m1, const double* beta, double tau,
-                             int* pruned, double* partials)
+                             int* pruned, double* partials, double amb, int64_t* n_amb)
 {
     double p = 0.0;
     *pruned = 0;
@@ -96,6 +96,9 @@ static int estimate_and_test(const double* qr, const double* xs, int D, int dd, 
             p += t * t;
         }
         if (partials) partials[s - 1] = p;
+        /* a decision within amb * tau of the threshold may flip under another
+         * rounding of the same arithmetic: count it */
+        if (n_amb && isfinite(tau) && fabs(m1[s - 1] * p + beta[s - 1] - tau) <= amb * tau) (*n_amb)++;
         if (m1[s - 1] * p + beta[s - 1] > tau) {
             *pruned = 1;
             return s;
@@ -108,6 +111,7 @@ static int64_t wave_end(int64_t b, int first_wave) { return b == 0 ? first_wave 
 
 typedef struct {
     int32_t D, dd, S, P, Kmax, mode, first_wave;
+    double amb;
     const double* Qr;
     const float* Q;
     const double* Xs;
@@ -123,7 +127,7 @@ typedef struct {
     const double* tau_in;
     int64_t* out_ids;
     double* out_d;
-    int64_t* stats; /* per query: candidates, pruned, exact, dims scanned */
+    int64_t* stats; /* per query: candidates, pruned, exact, dims scanned, ambiguous tests */
 } oracle_args;
 
 /* One candidate: estimate, test, and if it survives, its exact distance. */
@@ -132,7 +136,7 @@ static int visit(const oracle_args* a, int64_t b, int64_t pos, double tau, entry
     const double* qr = a->Qr + b * a->D;
     int pruned;
     int steps = estimate_and_test(qr, a->Xs + pos * a->D, a->D, a->dd, a->S, a->m1, a->beta, tau,
-                                  &pruned, NULL);
+                                  &pruned, NULL, a->amb, &st[4]);
     st[0] += 1;
     if (pruned) {
         int64_t dims = (int64_t)steps * a->dd;
@@ -152,8 +156,8 @@ static void search_one(const oracle_args* a, int64_t b)
     int K = a->K[b];
     int np = a->nprobe[b];
     const int32_t* pr = a->probes + b * a->P;
-    int64_t* st = a->stats + 4 * b;
-    st[0] = st[1] = st[2] = st[3] = 0;
+    int64_t* st = a->stats + 5 * b;
+    st[0] = st[1] = st[2] = st[3] = st[4] = 0;
     result_queue q;
     q.K = K;
     q.n = 0;
@@ -196,14 +200,14 @@ static void search_one(const oracle_args* a, int64_t b)
 }
 
 int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t Kmax,
-                  int32_t mode, int32_t first_wave, const double* Qr, const float* Q,
+                  int32_t mode, int32_t first_wave, double amb, const double* Qr, const float* Q,
                   const double* Xs, const float* X, const int64_t* ids, const int64_t* list_off,
                   const int64_t* members, const int32_t* probes, const int32_t* nprobe,
                   const int32_t* K, const double* m1, const double* beta, const double* tau_in,
                   int64_t* out_ids, double* out_d, int64_t* stats)
 {
     if (delta_d <= 0 || S < 1 || first_wave < 1 || mode < 0 || mode > 2) return 1;
-    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, Qr, Q, Xs, X, ids, list_off,
+    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, amb, Qr, Q, Xs, X, ids, list_off,
                      members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < B; b++) search_one(&a, b);
@@ -247,7 +251,7 @@ int oracle_collect(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, 
                     int64_t pos = members[m];
                     int pruned;
                     estimate_and_test(Qr + b * D, Xs + pos * D, D, delta_d, S, never, neg_inf, tau,
-                                      &pruned, partials + row * (S > 1 ? S - 1 : 0));
+                                      &pruned, partials + row * (S > 1 ? S - 1 : 0), 0.0, NULL);
                     tau_out[row] = tau;
                     dis_out[row] = exact_distance(X + pos * D, Q + b * D, D);
                     id_out[row] = ids[pos];

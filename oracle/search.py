@@ -80,9 +80,11 @@ class OracleIndex:
 
 
 def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode="waves",
-           first_wave: int = 1, tau=None):
-    """Returns (ids[B, Kmax], dists[B, Kmax], stats[B, 4]) where stats holds
-    candidates visited, candidates pruned, exact distances taken, dims scanned."""
+           first_wave: int = 1, tau=None, amb: float = 0.0):
+    """Returns (ids[B, Kmax], dists[B, Kmax], stats[B, 5]) where stats holds
+    candidates visited, candidates pruned, exact distances taken, dims
+    scanned, and tests whose left side m1 dis' + beta lay within amb * tau
+    of tau (decisions another rounding could flip)."""
     lib = _load()
     Q = np.ascontiguousarray(Q, dtype=np.float32)
     B = Q.shape[0]
@@ -99,11 +101,12 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
     tau_in = np.ascontiguousarray(np.full(B, np.inf) if tau is None else tau, dtype=np.float64)
     out_ids = np.empty((B, Kmax), dtype=np.int64)
     out_d = np.empty((B, Kmax))
-    stats = np.zeros((B, 4), dtype=np.int64)
+    stats = np.zeros((B, 5), dtype=np.int64)
     rc = lib.oracle_search(
         ctypes.c_int64(B), ctypes.c_int32(idx.D), ctypes.c_int32(delta_d), ctypes.c_int32(S),
         ctypes.c_int32(P), ctypes.c_int32(Kmax), ctypes.c_int32(MODES[mode]),
-        ctypes.c_int32(first_wave), _p(Qr), _p(Q), _p(idx.Xs), _p(idx.X), _p(idx.ids),
+        ctypes.c_int32(first_wave), ctypes.c_double(amb), _p(Qr), _p(Q), _p(idx.Xs), _p(idx.X),
+        _p(idx.ids),
         _p(idx.list_off), _p(idx.members), _p(probes), _p(nprobe), _p(K), _p(m1), _p(beta),
         _p(tau_in), _p(out_ids), _p(out_d), _p(stats))
     if rc != 0:

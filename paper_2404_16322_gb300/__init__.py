@@ -1,0 +1,243 @@
+"""GB300 data-aware distance estimation for IVF refinement (arXiv 2404.16322).
+
+A thin binding over the C ABI of ``include/dade.h``: every function below
+has the C entry point's name and only marshals arguments (NumPy arrays for
+host buffers, torch CUDA tensors for device buffers and streams).  Every step
+of the search runs in the library's CUDA kernels; if the library is not
+built, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["dade_train_rotation", "ivf_build", "dade_fit_correction", "dade_fit_samples",
+           "dade_set_correction", "dade_get_correction", "dade_search", "dade_search_workspace_size",
+           "dade_index_info_get", "dade_index_centroids", "dade_index_assignment",
+           "dade_index_list_sizes", "dade_index_save", "dade_index_load", "dade_index_free",
+           "dade_stage_timing", "dade_stage_timing_read", "dade_last_error", "Index", "library",
+           "n_steps"]
+
+_LIB = None
+
+
+def library() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = L.load()
+    return _LIB
+
+
+def dade_last_error() -> str:
+    return library().dade_last_error().decode()
+
+
+def _check(st: int) -> None:
+    if st != 0:
+        raise L.DadeError(st, dade_last_error())
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def n_steps(D: int, delta_d: int) -> int:
+    return -(-(-(-D // 8) * 8) // delta_d)
+
+
+class Index:
+    """Owner of a ``dade_index*``; released by ``dade_index_free`` on close/del."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    @property
+    def ptr(self):
+        if not self.handle:
+            raise ValueError("index is closed")
+        return self.handle
+
+    def close(self):
+        if self.handle:
+            library().dade_index_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+    def info(self) -> dict:
+        return dade_index_info_get(self)
+
+
+def dade_train_rotation(X, sample_n: int = 0, seed: int = 0):
+    """PCA rotation on the host in FP64: returns (mean[D], R[D, D], eigvals[D])."""
+    X = _host(X, np.float32)
+    n, D = X.shape
+    mean = np.empty(D)
+    R = np.empty((D, D))
+    lam = np.empty(D)
+    _check(library().dade_train_rotation(X.ctypes.data, n, D, int(sample_n), int(seed), mean.ctypes.data,
+                                         R.ctypes.data, lam.ctypes.data))
+    return mean, R, lam
+
+
+def ivf_build(X, mean, R, nlist: int, kmeans_iters: int = 10, seed: int = 0, dtype: str = "f32",
+              centroids=None, assign=None, ids=None) -> Index:
+    X = _host(X, np.float32)
+    N, D = X.shape
+    mean = _host(mean, np.float64)
+    R = _host(R, np.float64)
+    c = None if centroids is None else _host(centroids, np.float32)
+    a = None if assign is None else _host(assign, np.int32)
+    i = None if ids is None else _host(ids, np.int64)
+    p = L.BuildParams(int(nlist), int(kmeans_iters), int(seed), L.SLAB[dtype], _ptr(c), _ptr(a), _ptr(i))
+    out = ctypes.c_void_p()
+    _check(library().ivf_build(X.ctypes.data, N, D, mean.ctypes.data, R.ctypes.data, ctypes.byref(p),
+                               ctypes.byref(out)))
+    return Index(out.value)
+
+
+def dade_fit_correction(idx: Index, T, K: int, nprobe: int, delta_d: int, target_recall: float = 0.995,
+                        seed: int = 0, label1_cap: int = 500_000):
+    T = _host(T, np.float32)
+    info = dade_index_info_get(idx)
+    S = n_steps(info["D"], delta_d)
+    m1 = np.zeros(max(S - 1, 1), np.float32)
+    beta = np.zeros(max(S - 1, 1), np.float32)
+    _check(library().dade_fit_correction(idx.ptr, T.ctypes.data, T.shape[0], int(K), int(nprobe),
+                                         int(delta_d), float(target_recall), int(seed), int(label1_cap),
+                                         m1.ctypes.data, beta.ctypes.data))
+    return m1[:S - 1], beta[:S - 1]
+
+
+def dade_fit_samples(partials, tau, label, D: int, delta_d: int, target_recall: float = 0.995,
+                     min_label0: int = 100):
+    P = _host(partials, np.float64)
+    t = _host(tau, np.float64)
+    lab = _host(label, np.int8)
+    S = n_steps(D, delta_d)
+    m1 = np.zeros(max(S - 1, 1))
+    beta = np.zeros(max(S - 1, 1))
+    _check(library().dade_fit_samples(P.ctypes.data, t.ctypes.data, lab.ctypes.data, len(t), int(D),
+                                      int(delta_d), float(target_recall), int(min_label0), m1.ctypes.data,
+                                      beta.ctypes.data))
+    return m1[:S - 1], beta[:S - 1]
+
+
+def dade_set_correction(idx: Index, delta_d: int, m1, beta) -> None:
+    m1 = _host(m1, np.float32)
+    beta = _host(beta, np.float32)
+    _check(library().dade_set_correction(idx.ptr, int(delta_d), m1.ctypes.data, beta.ctypes.data))
+
+
+def dade_get_correction(idx: Index, delta_d: int):
+    info = dade_index_info_get(idx)
+    S = n_steps(info["D"], delta_d)
+    m1 = np.zeros(max(S - 1, 1), np.float32)
+    beta = np.zeros(max(S - 1, 1), np.float32)
+    _check(library().dade_get_correction(idx.ptr, int(delta_d), m1.ctypes.data, beta.ctypes.data))
+    return m1[:S - 1], beta[:S - 1]
+
+
+def _opts(mode, max_K, max_nprobe, first_wave=0, tau=None, probe_in=None, probe_out=None, qrot_out=None,
+          stats=None, status=None, workspace=None):
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    return L.SearchOpts(L.MODE[mode], int(max_K), int(max_nprobe), int(first_wave), _ptr(tau),
+                        _ptr(probe_in), _ptr(probe_out), _ptr(qrot_out), _ptr(stats), _ptr(status),
+                        _ptr(workspace), ws_bytes)
+
+
+def dade_search_workspace_size(idx: Index, B: int, delta_d: int, max_K: int, max_nprobe: int,
+                               mode: str = "prune", first_wave: int = 0, frozen: bool = False,
+                               probe_in: bool = False) -> int:
+    o = _opts(mode, max_K, max_nprobe, first_wave)
+    if frozen:
+        o.tau_dev = 1  # only its presence matters for sizing
+    if probe_in:
+        o.probe_in_dev = 1
+    return int(library().dade_search_workspace_size(idx.ptr, int(B), int(delta_d), ctypes.byref(o)))
+
+
+def dade_search(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: int, max_nprobe: int,
+                mode: str = "prune", first_wave: int = 0, tau=None, probe_in=None, probe_out=None,
+                qrot_out=None, stats=None, status=None, workspace=None, offsets=None, stream=None) -> None:
+    """Enqueue a search on ``stream`` (a torch.cuda.Stream; default: current).
+
+    Q: (B, D) float32 CUDA tensor; K, nprobe: (B,) int32 CUDA tensors; ids
+    (int64) and dists (float32) are output CUDA tensors of B * max_K (or
+    offsets[-1]) elements.  Optional tensors as in dade_search_opts."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    o = _opts(mode, max_K, max_nprobe, first_wave, tau, probe_in, probe_out, qrot_out, stats, status,
+              workspace)
+    _check(library().dade_search(idx.ptr, _ptr(Q), int(Q.shape[0]), _ptr(K), _ptr(nprobe), int(delta_d),
+                                 ctypes.byref(o), _ptr(ids), _ptr(dists), _ptr(offsets),
+                                 ctypes.c_void_p(s.cuda_stream)))
+
+
+def dade_index_info_get(idx: Index) -> dict:
+    info = L.IndexInfo()
+    _check(library().dade_index_info_get(idx.ptr, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in L.IndexInfo._fields_}
+
+
+def dade_index_centroids(idx: Index):
+    info = dade_index_info_get(idx)
+    out = np.empty((info["nlist"], info["D"]), np.float32)
+    _check(library().dade_index_centroids(idx.ptr, out.ctypes.data))
+    return out
+
+
+def dade_index_assignment(idx: Index):
+    info = dade_index_info_get(idx)
+    out = np.empty(info["N"], np.int32)
+    _check(library().dade_index_assignment(idx.ptr, out.ctypes.data))
+    return out
+
+
+def dade_index_list_sizes(idx: Index):
+    info = dade_index_info_get(idx)
+    out = np.empty(info["nlist"], np.int64)
+    _check(library().dade_index_list_sizes(idx.ptr, out.ctypes.data))
+    return out
+
+
+def dade_index_save(idx: Index, path: str) -> None:
+    _check(library().dade_index_save(idx.ptr, str(path).encode()))
+
+
+def dade_index_load(path: str) -> Index:
+    out = ctypes.c_void_p()
+    _check(library().dade_index_load(str(path).encode(), ctypes.byref(out)))
+    return Index(out.value)
+
+
+def dade_index_free(idx: Index) -> None:
+    idx.close()
+
+
+def dade_stage_timing(enable: bool) -> None:
+    _check(library().dade_stage_timing(1 if enable else 0))
+
+
+def dade_stage_timing_read():
+    """Returns (scan_ms, scan_launches, staged_bytes) since the last read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    by = ctypes.c_double()
+    _check(library().dade_stage_timing_read(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
+    return ms.value, n.value, by.value

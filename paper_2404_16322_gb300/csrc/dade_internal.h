@@ -1,0 +1,173 @@
+// Internal declarations of the GB300 library behind include/dade.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "dade.h"
+
+namespace dade {
+
+// ---------------------------------------------------------------- errors
+dade_status fail(dade_status st, const char* fmt, ...);
+void clear_error();
+
+#define DADE_CUDA_TRY(expr)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return ::dade::fail(DADE_ECUDA, "%s failed: %s (%s:%d)", #expr,                  \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+#define DADE_TRY(expr)                                                                        \
+    do {                                                                                      \
+        dade_status s_ = (expr);                                                              \
+        if (s_ != DADE_OK) return s_;                                                         \
+    } while (0)
+
+constexpr int kBlock = 8;        // dimensions per layout block
+constexpr int kListAlign = 32;   // bucket sizes are padded to a multiple of this
+constexpr int kMaxK = 1024;
+constexpr int kMaxD = 4096;
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// Probe rank r belongs to wave w: [0, f) is wave 0, [f 2^(w-1), f 2^w) wave w.
+inline int wave_of_rank_host(int r, int f) {
+    if (r < f) return 0;
+    int q = r / f, w = 0;
+    while (q) { q >>= 1; ++w; }
+    return w;
+}
+inline int num_waves(int nprobe, int f) { return nprobe <= 0 ? 0 : wave_of_rank_host(nprobe - 1, f) + 1; }
+inline int wave_begin(int w, int f) { return w == 0 ? 0 : f << (w - 1); }
+
+struct CorrectionTable {
+    int32_t S = 0;
+    std::vector<float> m1, beta;  // S - 1 each
+    float* m1_dev = nullptr;
+    float* beta_dev = nullptr;
+};
+
+// Device buffer with RAII release.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    dade_status alloc(size_t n);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace dade
+
+struct dade_index {
+    int device = 0;
+    int64_t N = 0;
+    int32_t D = 0, Dpad = 0, nb = 0, nlist = 0;
+    dade_slab_dtype dtype = DADE_SLAB_F32;
+    std::vector<double> mean, R;       // host FP64 (D, D x D)
+    std::vector<float> centroids;      // host nlist x D (rotated space)
+    std::vector<int32_t> assign;       // host N: bucket of each input row
+    std::vector<int64_t> ids;          // host N: id of each input row
+    std::vector<int64_t> list_size;    // nlist
+    std::vector<int64_t> list_slot;    // nlist + 1: first slot of each bucket
+    std::vector<int64_t> sizes_desc_prefix;  // prefix sums of bucket sizes, largest first
+    std::vector<float> fp8_scale;      // Dpad (FP8 only)
+    int64_t total_slots = 0, max_list = 0;
+    // device copies
+    dade::DevBuf R_dev;        // Dpad x Dpad FP32 (zero beyond D)
+    dade::DevBuf mean_dev;     // Dpad FP32
+    dade::DevBuf cent_dev;     // nlist x Dpad FP32
+    dade::DevBuf list_size_dev;  // nlist int32
+    dade::DevBuf list_slot_dev;  // nlist + 1 int64
+    dade::DevBuf slab_dev;     // total_slots x Dpad elements of dtype, blocked
+    dade::DevBuf orig_dev;     // total_slots x Dpad FP32, blocked
+    dade::DevBuf ids_dev;      // total_slots int64 (-1 on padding)
+    dade::DevBuf scale_dev;    // Dpad FP32 (FP8 only)
+    std::map<int, dade::CorrectionTable> tables;  // by delta_d
+    // internal scratch used when the caller gives no workspace
+    mutable dade::DevBuf ws;
+    mutable dade::DevBuf status;
+};
+
+namespace dade {
+
+// ----------------------------------------------------------- host math
+dade_status covariance_fp64(const float* X, int64_t n, int32_t D, const int64_t* rows,
+                            int64_t m, double* mean, double* cov);
+dade_status jacobi_eigh(int32_t D, const double* A, double* eigvals, double* R);
+dade_status fit_tables(const double* partials, const double* tau, const int8_t* label,
+                       int64_t n, int32_t S, double target_recall, int32_t min_label0,
+                       double* m1_out, double* beta_out);
+uint64_t splitmix64(uint64_t z);
+double sample_uniform(uint64_t seed, uint64_t query, uint64_t id);
+
+// ----------------------------------------------------------- kernels
+enum GemmOp { GEMM_DOT = 0, GEMM_L2 = 1 };
+// C[M x N] = op(A - sub, B): DOT = sum (a - sub) b, L2 = sum (a - b)^2 over k < Kd.
+cudaError_t launch_gemm_store(int op, const float* A, int64_t lda, const float* sub,
+                              const float* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                              int64_t N, int Kd, cudaStream_t st);
+// out[m] = min over n of (bits(L2(A_m, B_n)) << 32 | n), atomically (out preset to ~0).
+cudaError_t launch_gemm_argmin(const float* A, int64_t lda, const float* B, int64_t ldb,
+                               unsigned long long* out, int64_t M, int64_t N, int Kd,
+                               cudaStream_t st);
+// Per row b: the nprobe[b] smallest of scores[b, 0:n] ordered by (score, column).
+cudaError_t launch_select_probes(const float* scores, int64_t B, int n, const int32_t* nprobe,
+                                 int P, int32_t* probes, int32_t* status, cudaStream_t st);
+
+struct LayoutArgs {
+    const float* xrot;       // N x Dpad rotated FP32 rows
+    const float* x;          // N x D original rows
+    const int32_t* slot_row; // total_slots: source row or -1
+    const int32_t* slot_list;
+    const int64_t* list_slot;
+    int64_t total_slots;
+    int32_t D, Dpad;
+    int dtype;
+    const float* scale;      // FP8 per-dim scale
+    void* slab;
+    float* orig;
+};
+cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st);
+cudaError_t launch_amax(const float* xrot, int64_t N, int32_t Dpad, float* amax_bits_as_float,
+                        cudaStream_t st);
+cudaError_t launch_fp8_scale(float* amax_to_scale, int32_t Dpad, cudaStream_t st);
+
+// ----------------------------------------------------------- search
+struct SearchPlan;  // defined in search.cu
+dade_status search_impl(const dade_index* idx, const float* Q_dev, int64_t B,
+                        const int32_t* K_dev, const int32_t* nprobe_dev, int32_t delta_d,
+                        const dade_search_opts& opts, int64_t* ids_dev, float* dists_dev,
+                        const int64_t* out_offsets_dev, cudaStream_t st,
+                        const struct CollectArgs* collect);
+size_t workspace_bytes(const dade_index* idx, int64_t B, int32_t delta_d,
+                       const dade_search_opts& opts, const struct CollectArgs* collect);
+
+// Sample collection for the correction fit (replay with pruning off).
+struct CollectArgs {
+    int32_t pass;             // 0: count label-1 rows; 1: emit rows
+    const int64_t* topk_ids;  // B x K_max sorted ids of the exact top-K
+    int32_t topk_stride;
+    uint64_t seed;
+    int64_t query_offset;     // index of the batch's first query in the training set
+    double keep_rate;         // label-1 keep probability (pass 1)
+    unsigned long long* n_label1;  // pass 0 counter
+    unsigned long long* n_rows;    // pass 1 counter
+    int64_t row_cap;
+    float* partials;          // row_cap x (S - 1)
+    float* tau;               // row_cap
+    int8_t* label;            // row_cap
+};
+
+}  // namespace dade

@@ -1,0 +1,159 @@
+// dade_fit_correction: learn the per-step table (m1_s, beta'_s) of the
+// data-driven correction (Section V-A "Parameter Learning", "Adaptive
+// Adjustment"; one classifier per step, Section V-B; labels as in
+// Section VII-A).
+//
+// The training queries are searched three times on the device with pruning
+// off, under the same wave schedule as dade_search: (A) the exact top-K per
+// query; (B) a replay counting label-1 candidates; (C) a replay emitting the
+// kept samples (every label-0 candidate, label-1 candidates thinned to about
+// label1_cap by a SplitMix64 draw).  The samples' partial distances come from
+// the stored slabs with the same arithmetic as the search.  The fit itself is
+// host FP64 (fit_tables).
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "dade_internal.h"
+
+namespace dade {
+dade_status install_table_public(dade_index* idx, int delta_d, int S, const float* m1, const float* beta);
+}
+
+using namespace dade;
+
+extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int64_t nt, int32_t K,
+                                           int32_t nprobe, int32_t delta_d, double target_recall,
+                                           uint64_t seed, int64_t label1_cap, float* m1_out,
+                                           float* beta_out) {
+    clear_error();
+    if (!idx || !Tq) return fail(DADE_EINVAL, "null argument");
+    if (nt < 1) return fail(DADE_EINVAL, "need training queries");
+    if (K < 1 || K > kMaxK) return fail(DADE_EINVAL, "K out of range");
+    if (nprobe < 1 || nprobe > std::min(idx->nlist, 1024)) return fail(DADE_EINVAL, "nprobe out of range");
+    if (delta_d != 8 && delta_d != 16 && delta_d != 32) return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32");
+    if (!(target_recall > 0 && target_recall <= 1)) return fail(DADE_EINVAL, "target_recall in (0, 1]");
+    if (label1_cap < 1) return fail(DADE_EINVAL, "label1_cap must be >= 1");
+    const int S = (int)ceil_div(idx->Dpad, delta_d);
+    std::vector<float> m1f((size_t)std::max(1, S - 1), 0.f), btf((size_t)std::max(1, S - 1), -INFINITY);
+    if (S <= 1) return install_table_public(idx, delta_d, S, m1f.data(), btf.data());
+
+    cudaStream_t st;
+    DADE_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct G {
+        cudaStream_t s;
+        ~G() { cudaStreamDestroy(s); }
+    } guard{st};
+
+    const int64_t Bc = std::min<int64_t>(nt, 4096);
+    const int D = idx->D;
+    DevBuf q, kk, np, top_all, dists, cnt, status;
+    DADE_TRY(q.alloc(sizeof(float) * Bc * D));
+    DADE_TRY(kk.alloc(sizeof(int32_t) * Bc));
+    DADE_TRY(np.alloc(sizeof(int32_t) * Bc));
+    DADE_TRY(top_all.alloc(sizeof(int64_t) * nt * K));
+    DADE_TRY(dists.alloc(sizeof(float) * Bc * K));
+    DADE_TRY(cnt.alloc(sizeof(unsigned long long) * 2));
+    DADE_TRY(status.alloc(sizeof(int32_t)));
+    {
+        std::vector<int32_t> kh((size_t)Bc, K), nh((size_t)Bc, nprobe);
+        DADE_CUDA_TRY(cudaMemcpy(kk.p, kh.data(), sizeof(int32_t) * Bc, cudaMemcpyHostToDevice));
+        DADE_CUDA_TRY(cudaMemcpy(np.p, nh.data(), sizeof(int32_t) * Bc, cudaMemcpyHostToDevice));
+        DADE_CUDA_TRY(cudaMemset(cnt.p, 0, sizeof(unsigned long long) * 2));
+        DADE_CUDA_TRY(cudaMemset(status.p, 0, sizeof(int32_t)));
+    }
+    dade_search_opts o{};
+    o.mode = DADE_SCAN_FULL;
+    o.max_K = K;
+    o.max_nprobe = nprobe;
+    o.first_wave = 1;
+    o.status_dev = status.as<int32_t>();
+
+    CollectArgs ca{};
+    ca.seed = seed;
+    ca.topk_stride = K;
+    ca.n_label1 = cnt.as<unsigned long long>();
+    ca.n_rows = cnt.as<unsigned long long>() + 1;
+
+
+    // The collect replays write their own top-K to a scratch output.
+    DevBuf scratch_ids;
+    DADE_TRY(scratch_ids.alloc(sizeof(int64_t) * Bc * K));
+    auto replay = [&](int pass) -> dade_status {
+        for (int64_t b0 = 0; b0 < nt; b0 += Bc) {
+            const int64_t B = std::min(Bc, nt - b0);
+            DADE_CUDA_TRY(cudaMemcpyAsync(q.p, Tq + b0 * D, sizeof(float) * B * D, cudaMemcpyHostToDevice, st));
+            int64_t* top = top_all.as<int64_t>() + b0 * K;
+            if (pass < 0) {
+                DADE_TRY(search_impl(idx, q.as<float>(), B, kk.as<int32_t>(), np.as<int32_t>(), delta_d, o, top,
+                                     dists.as<float>(), nullptr, st, nullptr));
+            } else {
+                ca.pass = pass;
+                ca.topk_ids = top;
+                ca.query_offset = b0;
+                DADE_TRY(search_impl(idx, q.as<float>(), B, kk.as<int32_t>(), np.as<int32_t>(), delta_d, o,
+                                     scratch_ids.as<int64_t>(), dists.as<float>(), nullptr, st, &ca));
+            }
+        }
+        DADE_CUDA_TRY(cudaStreamSynchronize(st));
+        return DADE_OK;
+    };
+
+    DADE_TRY(replay(-1));  // (A) exact top-K
+    DADE_TRY(replay(0));   // (B) count label-1
+    unsigned long long counts[2] = {0, 0};
+    DADE_CUDA_TRY(cudaMemcpy(counts, cnt.p, sizeof counts, cudaMemcpyDeviceToHost));
+    const double n1 = (double)counts[0];
+    ca.keep_rate = n1 > (double)label1_cap ? (double)label1_cap / n1 : 1.0;
+    ca.row_cap = nt * K + label1_cap + (int64_t)(6.0 * sqrt((double)label1_cap)) + 1024;
+    DevBuf rp, rt, rl;
+    DADE_TRY(rp.alloc(sizeof(float) * ca.row_cap * (S - 1)));
+    DADE_TRY(rt.alloc(sizeof(float) * ca.row_cap));
+    DADE_TRY(rl.alloc(sizeof(int8_t) * ca.row_cap));
+    ca.partials = rp.as<float>();
+    ca.tau = rt.as<float>();
+    ca.label = rl.as<int8_t>();
+    DADE_TRY(replay(1));   // (C) emit samples
+    DADE_CUDA_TRY(cudaMemcpy(counts, cnt.p, sizeof counts, cudaMemcpyDeviceToHost));
+    int32_t dev_status = 0;
+    DADE_CUDA_TRY(cudaMemcpy(&dev_status, status.p, sizeof dev_status, cudaMemcpyDeviceToHost));
+    if (dev_status) return fail((dade_status)dev_status, "device status %d during the replay", dev_status);
+    const int64_t n = std::min<int64_t>((int64_t)counts[1], ca.row_cap);
+    std::vector<float> pf((size_t)n * (S - 1)), tf((size_t)n);
+    std::vector<int8_t> lab((size_t)n);
+    DADE_CUDA_TRY(cudaMemcpy(pf.data(), rp.p, sizeof(float) * pf.size(), cudaMemcpyDeviceToHost));
+    DADE_CUDA_TRY(cudaMemcpy(tf.data(), rt.p, sizeof(float) * tf.size(), cudaMemcpyDeviceToHost));
+    DADE_CUDA_TRY(cudaMemcpy(lab.data(), rl.p, sizeof(int8_t) * lab.size(), cudaMemcpyDeviceToHost));
+    // rows arrive in atomic order: sort them so the fit is reproducible
+    std::vector<int64_t> ord((size_t)n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+        if (lab[a] != lab[b]) return lab[a] < lab[b];
+        if (tf[a] != tf[b]) return tf[a] < tf[b];
+        for (int s = 0; s < S - 1; ++s) {
+            float x = pf[(size_t)a * (S - 1) + s], y = pf[(size_t)b * (S - 1) + s];
+            if (x != y) return x < y;
+        }
+        return false;
+    });
+    std::vector<double> P((size_t)n * (S - 1)), T((size_t)n);
+    std::vector<int8_t> L((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t o2 = ord[(size_t)i];
+        for (int s = 0; s < S - 1; ++s) P[(size_t)i * (S - 1) + s] = pf[(size_t)o2 * (S - 1) + s];
+        T[(size_t)i] = tf[(size_t)o2];
+        L[(size_t)i] = lab[(size_t)o2];
+    }
+    std::vector<double> m1d((size_t)S - 1), btd((size_t)S - 1);
+    DADE_TRY(fit_tables(P.data(), T.data(), L.data(), n, S, target_recall, 100, m1d.data(), btd.data()));
+    for (int s = 0; s < S - 1; ++s) {
+        m1f[(size_t)s] = (float)m1d[(size_t)s];
+        btf[(size_t)s] = (float)btd[(size_t)s];
+    }
+    DADE_TRY(install_table_public(idx, delta_d, S, m1f.data(), btf.data()));
+    if (m1_out) std::copy(m1f.begin(), m1f.begin() + (S - 1), m1_out);
+    if (beta_out) std::copy(btf.begin(), btf.begin() + (S - 1), beta_out);
+    return DADE_OK;
+}

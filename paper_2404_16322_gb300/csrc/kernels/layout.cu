@@ -1,0 +1,85 @@
+// Bucket layout of the index: rotated vectors in the slab precision and the
+// original FP32 vectors, both dimension-blocked (8 dims per block, block b
+// of a bucket's vector i at (b * npad + i) * 8), so that a Delta_d slab of a
+// run of vectors is one contiguous range.  FP8-E4M3 uses a per-dimension
+// scale amax_j / 448 (round to nearest even, saturating).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "../dade_internal.h"
+
+namespace dade {
+namespace {
+
+__global__ void layout_kernel(LayoutArgs a) {
+    const int nb = a.Dpad / kBlock;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.total_slots * nb) return;
+    int64_t slot = idx / nb;
+    int b = (int)(idx % nb);
+    int l = a.slot_list[slot];
+    int64_t s0 = a.list_slot[l];
+    int64_t npad = a.list_slot[l + 1] - s0;
+    int64_t i = slot - s0;
+    int64_t elem = s0 * a.Dpad + (b * npad + i) * kBlock;
+    int64_t row = a.slot_row[slot];
+#pragma unroll
+    for (int j = 0; j < kBlock; ++j) {
+        int d = b * kBlock + j;
+        float xr = row >= 0 ? a.xrot[row * a.Dpad + d] : 0.f;
+        float xo = (row >= 0 && d < a.D) ? a.x[row * a.D + d] : 0.f;
+        a.orig[elem + j] = xo;
+        if (a.dtype == DADE_SLAB_F32) {
+            static_cast<float*>(a.slab)[elem + j] = xr;
+        } else if (a.dtype == DADE_SLAB_BF16) {
+            static_cast<__nv_bfloat16*>(a.slab)[elem + j] = __float2bfloat16_rn(xr);
+        } else {
+            float y = xr / a.scale[d];
+            static_cast<__nv_fp8_storage_t*>(a.slab)[elem + j] =
+                __nv_cvt_float_to_fp8(y, __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
+
+__global__ void amax_kernel(const float* __restrict__ xrot, int64_t N, int32_t Dpad,
+                            unsigned int* __restrict__ amax) {
+    int d = blockIdx.y;
+    float m = 0.f;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+         r += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(xrot[r * Dpad + d]));
+    for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&amax[d], __float_as_uint(m));
+}
+
+__global__ void scale_kernel(float* v, int32_t Dpad) {
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < Dpad) {
+        float a = v[d];
+        v[d] = a > 0.f ? a / 448.f : 1.f;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st) {
+    int64_t n = a.total_slots * (a.Dpad / kBlock);
+    if (n == 0) return cudaSuccess;
+    layout_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amax(const float* xrot, int64_t N, int32_t Dpad, float* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * Dpad, st);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)std::min<int64_t>(64, ceil_div(N, 256)), (unsigned)Dpad);
+    amax_kernel<<<grid, 256, 0, st>>>(xrot, N, Dpad, reinterpret_cast<unsigned int*>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp8_scale(float* v, int32_t Dpad, cudaStream_t st) {
+    scale_kernel<<<(unsigned)ceil_div(Dpad, 128), 128, 0, st>>>(v, Dpad);
+    return cudaGetLastError();
+}
+
+}  // namespace dade

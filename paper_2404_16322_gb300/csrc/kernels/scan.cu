@@ -1,0 +1,861 @@
+// Refinement kernels: work units per wave, the persistent estimate-and-prune
+// scan, the exact distance, the per-query top-K merge and the replay that
+// collects training samples for the correction.
+//
+// Method (arXiv 2404.16322): a candidate's distance is accumulated Delta_d
+// rotated dimensions at a time (the loop of Algorithm 2); after each step the
+// learned test m1_s * dis' + beta_s > tau prunes it (Section V-A; one
+// classifier per step, Section V-B "Incremental Correction"); survivors get
+// the exact distance and join the result queue whose largest entry is tau
+// (Section I).  tau is frozen per wave of probe ranks so that all
+// (bucket, query) pairs of a wave run in parallel.
+//
+// Work unit = (bucket l, tile of up to kT candidates, group of up to kG
+// queries probing l in this wave).  The unit's Delta_d slab of the tile is
+// one bulk copy per 8-dim block (cp.async.bulk into shared memory, double
+// buffered, completion on an mbarrier) and is shared by every query of the
+// group.  Each warp owns queries; a query's live candidates are a compacted
+// list (index, partial distance) rebuilt after each test with a warp ballot.
+//
+// Distance arithmetic (identical in every path, so a pair's distance does
+// not depend on which path computed it): per 8-dim block b,
+// s_b = sum_j fma((q_j - x_j)^2) from 0 in j order; the distance adds s_b in
+// block order.  This bounds the FP32 rounding by (8 + D/8) ulp-terms.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "scan.cuh"
+
+namespace dade {
+namespace {
+
+constexpr int kWarps = kScanThreads / 32;
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: gives up after ~2 s, records DADE_ETIMEOUT and returns false.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > 2000000000ull) {
+            if (status) atomicCAS(status, 0, (int)DADE_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ------------------------------------------------------------ element loads
+template <int DT> struct Elem;
+template <> struct Elem<DADE_SLAB_F32> { using T = float; };
+template <> struct Elem<DADE_SLAB_BF16> { using T = __nv_bfloat16; };
+template <> struct Elem<DADE_SLAB_FP8E4M3> { using T = __nv_fp8_storage_t; };
+
+// 8 consecutive elements of one block as FP32 (FP8: times the per-dim scale).
+__device__ __forceinline__ void load8(const float* p, const float*, float (&x)[8]) {
+    float4 a = reinterpret_cast<const float4*>(p)[0];
+    float4 b = reinterpret_cast<const float4*>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, const float*, float (&x)[8]) {
+    uint4 u = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        x[2 * i] = __uint_as_float(w[i] << 16);
+        x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+__device__ __forceinline__ void load8(const __nv_fp8_storage_t* p, const float* scale8, float (&x)[8]) {
+    uint2 u = *reinterpret_cast<const uint2*>(p);
+    const uint32_t w[2] = {u.x, u.y};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[i] >> (16 * h)) & 0xffffu);
+            __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
+            float2 f = __half22float2(*reinterpret_cast<__half2*>(&hr));
+            int j = 4 * i + 2 * h;
+            x[j] = f.x * scale8[j];
+            x[j + 1] = f.y * scale8[j + 1];
+        }
+    }
+}
+
+// s_b = sum over the block's 8 dims of (q - x)^2, FMA in dim order from 0.
+__device__ __forceinline__ float block_sq(const float (&q)[8], const float (&x)[8]) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float t = q[j] - x[j];
+        s = fmaf(t, t, s);
+    }
+    return s;
+}
+
+__device__ __forceinline__ void load_q8(const float* p, float (&q)[8]) {
+    float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+    q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+}
+
+// Exact distance of one candidate from the original blocked FP32 vector.
+__device__ float exact_distance(const float* xo, int64_t npad, const float* qp, int nb) {
+    float d = 0.f;
+    for (int b = 0; b < nb; ++b) {
+        float x[8], q[8];
+        load8(xo + (int64_t)b * npad * kBlock, nullptr, x);
+        load_q8(qp + b * kBlock, q);
+        d += block_sq(q, x);
+    }
+    return d;
+}
+
+// ------------------------------------------------------------ unit decode
+struct Unit {
+    int l, t, nq, nt, item;
+};
+
+__device__ Unit decode_unit(const IndexView& ix, const WaveView& wv, int w, int u) {
+    const int32_t* uo = wv.unit_off + (int64_t)w * (ix.nlist + 1);
+    int lo = 0, hi = ix.nlist;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (uo[mid] <= u) lo = mid; else hi = mid;
+    }
+    Unit r;
+    r.l = lo;
+    int local = u - uo[lo];
+    int nl = ix.list_size[lo];
+    int ntile = (nl + kT - 1) / kT;
+    int g = local / ntile;
+    r.t = local - g * ntile;
+    int key = w * ix.nlist + lo;
+    int cnt = wv.cnt_wl[key];
+    r.nq = min(kG, cnt - g * kG);
+    r.nt = min(kT, nl - r.t * kT);
+    r.item = wv.off_wl[key] + g * kG;
+    return r;
+}
+
+// Append (d, slot) to query q's candidate buffer of wave w when app is set.
+__device__ __forceinline__ void append(const WaveView& wv, int w, int q, bool app, float d,
+                                       int32_t slot, int lane) {
+    unsigned bal = __ballot_sync(0xffffffffu, app);
+    if (!bal) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&wv.cand_cnt[q], __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (app) {
+        const int64_t* co = wv.cand_off + (int64_t)w * (wv.B + 1);
+        int64_t off = co[q], cap = co[q + 1] - off;
+        int s = base + __popc(bal & lanemask_lt());
+        if (s < cap) {
+            wv.cand_d[off + s] = d;
+            wv.cand_pos[off + s] = slot;
+        } else {
+            atomicCAS(wv.status, 0, (int)DADE_EINVAL);
+        }
+    }
+}
+
+// ------------------------------------------------------------ step pipeline
+struct StepShared {
+    unsigned char* buf[2];
+    uint64_t* bar;
+    uint16_t* alive;  // kG x kT candidate indices (compacted)
+    float* part;      // kG x kT partial distances
+    int* n;           // kG live counts
+    const int* q;     // kG query ids
+    const float* tau; // kG
+};
+
+// Runs `nsteps` slab steps over the tile: slab k covers blocks
+// [k*NBLK, min((k+1)*NBLK, nb)) of the source (rotated slabs in PRUNE mode,
+// original vectors otherwise).  PRUNE tests after each slab and compacts;
+// otherwise every candidate accumulates every slab.  Queries whose tau is
+// +inf are skipped in PRUNE mode (they cannot be pruned).  Returns false if
+// a bounded wait gave up.
+template <class E, int NBLK, bool PRUNE>
+__device__ bool run_steps(const E* src, int64_t npad, int t, int nt, int nq, int nsteps, int nb,
+                          int D, StepShared& sh, uint32_t (&ph)[2], const float* qsrc, int Dpad,
+                          const float* m1, const float* beta, const float* scale,
+                          int32_t* status, int64_t (&wstat)[2][4], unsigned long long* staged) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nt_copy = (nt + 31) & ~31;
+    const uint32_t blk_bytes = (uint32_t)nt_copy * kBlock * sizeof(E);
+    auto issue = [&](int k) {
+        int b0 = k * NBLK, nbk = min(NBLK, nb - b0);
+        unsigned char* dst = sh.buf[k & 1];
+        fence_proxy_async();
+        mbar_expect_tx(&sh.bar[k & 1], blk_bytes * nbk);
+        for (int bb = 0; bb < nbk; ++bb)
+            bulk_g2s(dst + (size_t)bb * kT * kBlock * sizeof(E),
+                     src + ((int64_t)(b0 + bb) * npad + (int64_t)t * kT) * kBlock, blk_bytes,
+                     &sh.bar[k & 1]);
+        if (staged) atomicAdd(staged, (unsigned long long)blk_bytes * nbk);
+    };
+    if (nsteps <= 0) return true;
+    if (tid == 0) issue(0);
+    int k = 0;
+    bool pending_next = false;
+    for (; k < nsteps; ++k) {
+        bool got = mbar_wait(&sh.bar[k & 1], ph[k & 1], status);
+        ph[k & 1] ^= 1u;
+        if (!__syncthreads_and(got)) return false;
+        pending_next = k + 1 < nsteps;
+        if (tid == 0 && pending_next) issue(k + 1);
+        const E* bk = reinterpret_cast<const E*>(sh.buf[k & 1]);
+        const int b0 = k * NBLK, nbk = min(NBLK, nb - b0);
+        const int dims_k = min((k + 1) * NBLK * kBlock, D);
+        for (int g = warp; g < nq; g += kWarps) {
+            const float tau = sh.tau[g];
+            if (PRUNE && isinf(tau)) continue;
+            const float* qp = qsrc + (int64_t)sh.q[g] * Dpad + b0 * kBlock;
+            float qv[NBLK][8];
+            float sc[NBLK][8];
+#pragma unroll
+            for (int bb = 0; bb < NBLK; ++bb) {
+                if (bb < nbk) {
+                    load_q8(qp + bb * kBlock, qv[bb]);
+                    if (scale) load_q8(scale + (b0 + bb) * kBlock, sc[bb]);
+                }
+            }
+            const float mm = PRUNE ? m1[k] : 0.f, bt = PRUNE ? beta[k] : 0.f;
+            const int n = sh.n[g];
+            int out = 0;
+            int64_t pruned = 0;
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                const bool valid = i < n;
+                int c = 0;
+                float p = 0.f;
+                if (valid) {
+                    c = sh.alive[g * kT + i];
+                    p = sh.part[g * kT + i];
+#pragma unroll
+                    for (int bb = 0; bb < NBLK; ++bb) {
+                        if (bb < nbk) {
+                            float x[8];
+                            load8(bk + ((size_t)bb * kT + c) * kBlock, sc[bb], x);
+                            p += block_sq(qv[bb], x);
+                        }
+                    }
+                }
+                const bool keep = valid && !(PRUNE && fmaf(mm, p, bt) > tau);
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                __syncwarp();
+                if (keep) {
+                    const int pos = out + __popc(bal & lanemask_lt());
+                    sh.alive[g * kT + pos] = (uint16_t)c;
+                    sh.part[g * kT + pos] = p;
+                }
+                out += __popc(bal);
+                if (PRUNE) pruned += __popc(__ballot_sync(0xffffffffu, valid && !keep));
+            }
+            __syncwarp();
+            if (lane == 0) {
+                sh.n[g] = out;
+                if (PRUNE) {
+                    wstat[g / kWarps][1] += pruned;
+                    wstat[g / kWarps][3] += pruned * dims_k;
+                }
+            }
+        }
+        __syncthreads();
+        if (PRUNE) {
+            int live = 0;
+            for (int g = 0; g < nq; ++g) live |= (!isinf(sh.tau[g]) && sh.n[g] > 0);
+            if (!live) break;
+        }
+    }
+    if (PRUNE && k < nsteps && pending_next) {
+        // the loop left early with the next slab in flight: drain it
+        int kn = k + 1;
+        bool got = mbar_wait(&sh.bar[kn & 1], ph[kn & 1], status);
+        ph[kn & 1] ^= 1u;
+        if (!__syncthreads_and(got)) return false;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------ wave scan
+template <int DT, int NBLK, bool FULL>
+__global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, WaveView wv, int w,
+                                                                 const float* __restrict__ m1,
+                                                                 const float* __restrict__ beta,
+                                                                 int S) {
+    using E = typename Elem<DT>::T;
+    constexpr int BUF = NBLK * kT * kBlock * 4;  // sized for FP32 (original vectors)
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_unit, s_l, s_t, s_nq, s_nt, s_inf;
+    __shared__ int s_q[kG], s_n[kG];
+    __shared__ float s_tau[kG];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    StepShared sh;
+    sh.buf[0] = smem;
+    sh.buf[1] = smem + BUF;
+    sh.alive = reinterpret_cast<uint16_t*>(smem + 2 * BUF);
+    sh.part = reinterpret_cast<float*>(smem + 2 * BUF + kG * kT * sizeof(uint16_t));
+    sh.bar = bar;
+    sh.n = s_n;
+    sh.q = s_q;
+    sh.tau = s_tau;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t ph[2] = {0u, 0u};
+    const int total = wv.unit_off[(int64_t)w * (ix.nlist + 1) + ix.nlist];
+    const int nsteps_full = (ix.nb + NBLK - 1) / NBLK;
+
+    for (;;) {
+        if (tid == 0) s_unit = atomicAdd(&wv.work[w], 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= total) break;
+        if (tid == 0) {
+            Unit un = decode_unit(ix, wv, w, u);
+            s_l = un.l;
+            s_t = un.t;
+            s_nq = un.nq;
+            s_nt = un.nt;
+            int all_inf = 1;
+            for (int g = 0; g < un.nq; ++g) {
+                int q = wv.items[un.item + g];
+                s_q[g] = q;
+                s_tau[g] = wv.tau[q];
+                s_n[g] = un.nt;
+                all_inf &= isinf(s_tau[g]) ? 1 : 0;
+            }
+            s_inf = all_inf;
+        }
+        __syncthreads();
+        const int l = s_l, t = s_t, nq = s_nq, nt = s_nt;
+        for (int e = tid; e < nq * kT; e += kScanThreads) {
+            sh.alive[e] = (uint16_t)(e % kT);
+            sh.part[e] = 0.f;
+        }
+        __syncthreads();
+        const int64_t slot_l = ix.list_slot[l];
+        const int64_t npad = ix.list_slot[l + 1] - slot_l;
+        const int64_t ebase = slot_l * ix.Dpad;
+        const int32_t slot0 = (int32_t)(slot_l + (int64_t)t * kT);
+        int64_t wstat[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        bool ok;
+        const bool exact_all = FULL || s_inf;
+        if (exact_all) {
+            // every candidate's exact distance through the staged pipeline
+            ok = run_steps<float, NBLK, false>(ix.orig + ebase, npad, t, nt, nq, nsteps_full, ix.nb,
+                                               ix.D, sh, ph, wv.qpad, ix.Dpad, nullptr, nullptr,
+                                               nullptr, wv.status, wstat, wv.staged_bytes);
+            if (!ok) break;
+            for (int g = warp; g < nq; g += kWarps) {
+                const int q = s_q[g];
+                const float tau = s_tau[g];
+                for (int base = 0; base < nt; base += 32) {
+                    const int i = base + lane;
+                    const bool valid = i < nt;
+                    const float d = valid ? sh.part[g * kT + i] : 0.f;
+                    append(wv, w, q, valid && d <= tau, d, slot0 + i, lane);
+                }
+                if (lane == 0) {
+                    wstat[g / kWarps][0] += nt;
+                    wstat[g / kWarps][2] += nt;
+                    wstat[g / kWarps][3] += (int64_t)nt * ix.D;
+                }
+            }
+        } else {
+            const E* slab = reinterpret_cast<const E*>(ix.slab) + ebase;
+            ok = run_steps<E, NBLK, true>(slab, npad, t, nt, nq, S - 1, ix.nb, ix.D, sh, ph, wv.qrot,
+                                          ix.Dpad, m1, beta,
+                                          DT == DADE_SLAB_FP8E4M3 ? ix.scale : nullptr, wv.status,
+                                          wstat, wv.staged_bytes);
+            if (!ok) break;
+            for (int g = warp; g < nq; g += kWarps) {
+                const int q = s_q[g];
+                const float tau = s_tau[g];
+                const int n = s_n[g];
+                const float* qp = wv.qpad + (int64_t)q * ix.Dpad;
+                for (int base = 0; base < n; base += 32) {
+                    const int i = base + lane;
+                    const bool valid = i < n;
+                    float d = 0.f;
+                    int c = 0;
+                    if (valid) {
+                        c = sh.alive[g * kT + i];
+                        d = exact_distance(ix.orig + ebase + ((int64_t)t * kT + c) * kBlock, npad, qp,
+                                           ix.nb);
+                    }
+                    append(wv, w, q, valid && d <= tau, d, slot0 + c, lane);
+                }
+                if (lane == 0) {
+                    wstat[g / kWarps][0] += nt;
+                    wstat[g / kWarps][2] += n;
+                    wstat[g / kWarps][3] += (int64_t)n * ix.D;
+                    if (wv.staged_bytes && n)
+                        atomicAdd(wv.staged_bytes, (unsigned long long)n * ix.nb * kBlock * sizeof(float));
+                }
+            }
+        }
+        if (wv.stats && lane == 0) {
+            for (int g = warp, j = 0; g < nq; g += kWarps, ++j)
+                for (int f = 0; f < 4; ++f)
+                    if (wstat[j][f]) atomicAdd((unsigned long long*)&wv.stats[(int64_t)s_q[g] * 4 + f],
+                                               (unsigned long long)wstat[j][f]);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ merge
+__device__ __forceinline__ bool pair_less(float da, int64_t ia, float db, int64_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+__global__ void __launch_bounds__(256) merge_kernel(IndexView ix, WaveView wv, int w) {
+    __shared__ float sd[kMergeCap];
+    __shared__ int64_t sid[kMergeCap];
+    const int q = blockIdx.x, tid = threadIdx.x;
+    const int64_t* co = wv.cand_off + (int64_t)w * (wv.B + 1);
+    const int64_t off = co[q], cap = co[q + 1] - off;
+    const int cnt = (int)((int64_t)wv.cand_cnt[q] < cap ? (int64_t)wv.cand_cnt[q] : cap);
+    const int K = wv.K[q];
+    if (cnt == 0 || K < 1 || K > wv.Kmax) {
+        __syncthreads();
+        if (tid == 0) wv.cand_cnt[q] = 0;
+        return;
+    }
+    int cur = wv.top_n[q];
+    float* td = wv.top_d + (int64_t)q * wv.Kmax;
+    int64_t* ti = wv.top_id + (int64_t)q * wv.Kmax;
+    for (int i = tid; i < cur; i += 256) {
+        sd[i] = td[i];
+        sid[i] = ti[i];
+    }
+    int done = 0;
+    while (done < cnt) {
+        const int chunk = min(cnt - done, kMergeCap - cur);
+        for (int i = tid; i < chunk; i += 256) {
+            sd[cur + i] = wv.cand_d[off + done + i];
+            sid[cur + i] = ix.ids[wv.cand_pos[off + done + i]];
+        }
+        int M = 1;
+        while (M < cur + chunk) M <<= 1;
+        for (int i = cur + chunk + tid; i < M; i += 256) {
+            sd[i] = INFINITY;
+            sid[i] = INT64_MAX;
+        }
+        __syncthreads();
+        for (int size = 2; size <= M; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < M; i += 256) {
+                    int j = i ^ stride;
+                    if (j > i) {
+                        bool up = (i & size) == 0;
+                        bool sw = up ? pair_less(sd[j], sid[j], sd[i], sid[i])
+                                     : pair_less(sd[i], sid[i], sd[j], sid[j]);
+                        if (sw) {
+                            float a = sd[i];
+                            sd[i] = sd[j];
+                            sd[j] = a;
+                            int64_t b = sid[i];
+                            sid[i] = sid[j];
+                            sid[j] = b;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        cur = min(K, cur + chunk);
+        done += chunk;
+    }
+    for (int i = tid; i < cur; i += 256) {
+        td[i] = sd[i];
+        ti[i] = sid[i];
+    }
+    if (tid == 0) {
+        wv.top_n[q] = cur;
+        wv.tau[q] = cur == K ? sd[K - 1] : INFINITY;
+        wv.cand_cnt[q] = 0;
+    }
+}
+
+__global__ void output_kernel(WaveView wv, int64_t* ids, float* dists, const int64_t* offsets) {
+    const int64_t q = blockIdx.x;
+    const int K = wv.K[q];
+    const int64_t off = offsets ? offsets[q] : q * wv.Kmax;
+    const int kk = offsets ? (int)(offsets[q + 1] - offsets[q]) : wv.Kmax;
+    const int n = (K >= 1 && K <= wv.Kmax) ? wv.top_n[q] : 0;
+    for (int k = threadIdx.x; k < kk; k += blockDim.x) {
+        bool v = k < n && k < K;
+        ids[off + k] = v ? wv.top_id[q * wv.Kmax + k] : -1;
+        dists[off + k] = v ? wv.top_d[q * wv.Kmax + k] : INFINITY;
+    }
+}
+
+// ------------------------------------------------------------ work units
+__global__ void count_kernel(IndexView ix, WaveView wv) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= wv.B) return;
+    int np = wv.nprobe[b];
+    const int K = wv.K[b];
+    if (np < 1 || np > wv.P || K < 1 || K > wv.Kmax) {
+        atomicCAS(wv.status, 0, (int)DADE_EINVAL);
+        return;
+    }
+    for (int r = 0; r < np; ++r) {
+        const int l = wv.probes[b * wv.P + r];
+        if (l < 0 || l >= ix.nlist) {
+            atomicCAS(wv.status, 0, (int)DADE_EINVAL);
+            continue;
+        }
+        int wr = 0;
+        if (r >= wv.first_wave) {
+            int qq = r / wv.first_wave;
+            wr = 32 - __clz(qq);
+        }
+        atomicAdd(&wv.cnt_wl[wr * ix.nlist + l], 1);
+        wv.cand_off[(int64_t)wr * (wv.B + 1) + b] += ix.list_size[l];
+    }
+}
+
+__global__ void scatter_kernel(IndexView ix, WaveView wv) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= wv.B) return;
+    int np = wv.nprobe[b];
+    const int K = wv.K[b];
+    if (np < 1 || np > wv.P || K < 1 || K > wv.Kmax) return;
+    for (int r = 0; r < np; ++r) {
+        const int l = wv.probes[b * wv.P + r];
+        if (l < 0 || l >= ix.nlist) continue;
+        int wr = 0;
+        if (r >= wv.first_wave) wr = 32 - __clz(r / wv.first_wave);
+        const int key = wr * ix.nlist + l;
+        const int pos = atomicAdd(&wv.fill_wl[key], 1);
+        wv.items[wv.off_wl[key] + pos] = (int32_t)b;
+    }
+}
+
+// Exclusive scan of one segment per CTA: out[seg*ostride + i] for i < len
+// and the total at i = len.  In-place use is safe (each chunk is read
+// before any of it is written).
+template <class Load, class T>
+__global__ void __launch_bounds__(1024) seg_scan_kernel(Load load, T* out, int64_t len, int64_t ostride) {
+    __shared__ T warp_tot[32];
+    __shared__ T s_carry;
+    const int seg = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < len; base += 4096) {
+        T v[4], sum = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int64_t i = base + tid * 4 + u;
+            v[u] = i < len ? load(seg, i) : (T)0;
+            sum += v[u];
+        }
+        T incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            T o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            T x = warp_tot[lane];
+            T xi = x;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                T o = __shfl_up_sync(0xffffffffu, xi, off);
+                if (lane >= off) xi += o;
+            }
+            warp_tot[lane] = xi - x;  // exclusive warp offsets
+        }
+        __syncthreads();
+        T run = s_carry + warp_tot[wid] + incl - sum;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int64_t i = base + tid * 4 + u;
+            if (i < len) out[seg * ostride + i] = run;
+            run += v[u];
+        }
+        __syncthreads();
+        if (tid == 1023) s_carry = run;
+        __syncthreads();
+    }
+    if (tid == 0) out[seg * ostride + len] = s_carry;
+}
+
+struct LoadI32 {
+    const int32_t* p;
+    __device__ int32_t operator()(int, int64_t i) const { return p[i]; }
+};
+struct LoadUnits {
+    const int32_t* cnt;
+    const int32_t* size;
+    int nlist;
+    __device__ int32_t operator()(int seg, int64_t l) const {
+        int c = cnt[(int64_t)seg * nlist + l];
+        int s = size[l];
+        return c > 0 ? ((c + kG - 1) / kG) * ((s + kT - 1) / kT) : 0;
+    }
+};
+struct LoadCap {
+    const int64_t* p;
+    int64_t stride;
+    __device__ int64_t operator()(int seg, int64_t i) const { return p[seg * stride + i]; }
+};
+
+__global__ void prepare_queries_kernel(const float* Q, int64_t B, int32_t D, int32_t Dpad, float* qpad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * Dpad) return;
+    int64_t b = i / Dpad;
+    int d = (int)(i % Dpad);
+    qpad[i] = d < D ? Q[b * D + d] : 0.f;
+}
+
+__global__ void fill_kernel(float* p, int64_t n, float v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// ------------------------------------------------------------ collect
+// Replay of a wave with pruning off, emitting labelled training samples.
+template <int DT>
+__global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, WaveView wv, int w, int dd,
+                                                               int S, CollectArgs ca, int64_t qoff) {
+    using E = typename Elem<DT>::T;
+    __shared__ int s_unit;
+    __shared__ Unit s_un;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int total = wv.unit_off[(int64_t)w * (ix.nlist + 1) + ix.nlist];
+    const int nblk = dd / kBlock;
+    for (;;) {
+        if (tid == 0) s_unit = atomicAdd(&wv.work[wv.n_waves + w], 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= total) break;
+        if (tid == 0) s_un = decode_unit(ix, wv, w, u);
+        __syncthreads();
+        const Unit un = s_un;
+        const int64_t slot_l = ix.list_slot[un.l];
+        const int64_t npad = ix.list_slot[un.l + 1] - slot_l;
+        const int64_t ebase = slot_l * ix.Dpad;
+        for (int g = warp; g < un.nq; g += kWarps) {
+            const int q = wv.items[un.item + g];
+            const float tau = wv.tau[q];
+            if (isinf(tau)) continue;
+            const int K = wv.K[q];
+            const float* qp = wv.qpad + (int64_t)q * ix.Dpad;
+            const float* qr = wv.qrot + (int64_t)q * ix.Dpad;
+            for (int base = 0; base < un.nt; base += 32) {
+                const int c = base + lane;
+                const bool valid = c < un.nt;
+                bool lab0 = false, lab1 = false;
+                int64_t id = -1;
+                if (valid) {
+                    const int64_t pos = (int64_t)un.t * kT + c;
+                    const float d = exact_distance(ix.orig + ebase + pos * kBlock, npad, qp, ix.nb);
+                    id = ix.ids[slot_l + pos];
+                    const int64_t* top = ca.topk_ids + (int64_t)q * ca.topk_stride;
+                    for (int k = 0; k < K; ++k) lab0 |= top[k] == id;
+                    lab1 = !lab0 && d > tau;
+                }
+                if (ca.pass == 0) {
+                    unsigned bal = __ballot_sync(0xffffffffu, lab1);
+                    if (lane == 0 && bal) atomicAdd(ca.n_label1, (unsigned long long)__popc(bal));
+                    continue;
+                }
+                bool emit = lab0;
+                if (lab1) {
+                    // SplitMix64-derived uniform of (seed, query, id)
+                    uint64_t key = ((uint64_t)(qoff + q) << 32) ^ (uint64_t)id;
+                    auto mix = [](uint64_t z) {
+                        z += 0x9E3779B97F4A7C15ull;
+                        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+                        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+                        return z ^ (z >> 31);
+                    };
+                    uint64_t z = mix(ca.seed ^ mix(key));
+                    double uu = (double)(z >> 11) * 0x1.0p-53;
+                    emit = uu < ca.keep_rate;
+                }
+                if (!emit) continue;
+                unsigned long long row = atomicAdd(ca.n_rows, 1ull);
+                if ((int64_t)row >= ca.row_cap) continue;
+                const int64_t pos = (int64_t)un.t * kT + c;
+                const E* xs = reinterpret_cast<const E*>(ix.slab) + ebase + pos * kBlock;
+                float p = 0.f;
+                for (int k = 0; k + 1 < S; ++k) {
+                    const int b0 = k * nblk, nbk = min(nblk, ix.nb - b0);
+                    for (int bb = 0; bb < nbk; ++bb) {
+                        float x[8], qv[8], sc[8];
+                        if (DT == DADE_SLAB_FP8E4M3) load_q8(ix.scale + (b0 + bb) * kBlock, sc);
+                        load8(xs + (int64_t)(b0 + bb) * npad * kBlock, sc, x);
+                        load_q8(qr + (b0 + bb) * kBlock, qv);
+                        p += block_sq(qv, x);
+                    }
+                    ca.partials[(int64_t)row * (S - 1) + k] = p;
+                }
+                ca.tau[row] = tau;
+                ca.label[row] = lab1 ? 1 : 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ launchers
+template <int DT, int NBLK, bool FULL>
+cudaError_t launch_scan_t(const IndexView& ix, const WaveView& wv, int w, const float* m1,
+                          const float* beta, int S, cudaStream_t st) {
+    constexpr int BUF = NBLK * kT * kBlock * 4;
+    constexpr int SMEM = 2 * BUF + kG * kT * (int)(sizeof(uint16_t) + sizeof(float));
+    static int grid = 0;
+    auto kern = wave_scan_kernel<DT, NBLK, FULL>;
+    if (grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kScanThreads, SMEM);
+        if (e != cudaSuccess) return e;
+        grid = sms * (per > 0 ? per : 1);
+    }
+    kern<<<grid, kScanThreads, SMEM, st>>>(ix, wv, w, m1, beta, S);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_prepare_queries(const float* Q, int64_t B, int32_t D, int32_t Dpad, float* qpad,
+                                   cudaStream_t st) {
+    int64_t n = B * Dpad;
+    if (n == 0) return cudaSuccess;
+    prepare_queries_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(Q, B, D, Dpad, qpad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float* p, int64_t n, float v, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    fill_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStream_t st) {
+    const unsigned gb = (unsigned)ceil_div(wv.B, 128);
+    count_kernel<<<gb, 128, 0, st>>>(ix, wv);
+    const int64_t nwl = (int64_t)wv.n_waves * ix.nlist;
+    seg_scan_kernel<<<1, 1024, 0, st>>>(LoadI32{wv.cnt_wl}, wv.off_wl, nwl, 0);
+    seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(LoadUnits{wv.cnt_wl, ix.list_size, ix.nlist},
+                                                 wv.unit_off, (int64_t)ix.nlist,
+                                                 (int64_t)ix.nlist + 1);
+    seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(LoadCap{wv.cand_off, wv.B + 1}, wv.cand_off, wv.B,
+                                                 wv.B + 1);
+    scatter_kernel<<<gb, 128, 0, st>>>(ix, wv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wave_scan(const IndexView& ix, const WaveView& wv, int w, bool full,
+                             int delta_d, const float* m1, const float* beta, int S,
+                             cudaStream_t st) {
+    if (full) return launch_scan_t<DADE_SLAB_F32, 4, true>(ix, wv, w, m1, beta, S, st);
+#define DADE_SCAN_CASE(DT, NB)                                                               \
+    if (ix.dtype == DT && delta_d == NB * kBlock)                                            \
+        return launch_scan_t<DT, NB, false>(ix, wv, w, m1, beta, S, st);
+    DADE_SCAN_CASE(DADE_SLAB_F32, 1)
+    DADE_SCAN_CASE(DADE_SLAB_F32, 2)
+    DADE_SCAN_CASE(DADE_SLAB_F32, 4)
+    DADE_SCAN_CASE(DADE_SLAB_BF16, 1)
+    DADE_SCAN_CASE(DADE_SLAB_BF16, 2)
+    DADE_SCAN_CASE(DADE_SLAB_BF16, 4)
+    DADE_SCAN_CASE(DADE_SLAB_FP8E4M3, 1)
+    DADE_SCAN_CASE(DADE_SLAB_FP8E4M3, 2)
+    DADE_SCAN_CASE(DADE_SLAB_FP8E4M3, 4)
+#undef DADE_SCAN_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStream_t st) {
+    if (wv.B == 0) return cudaSuccess;
+    merge_kernel<<<(unsigned)wv.B, 256, 0, st>>>(ix, wv, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_output(const WaveView& wv, int64_t* ids, float* dists, const int64_t* offsets,
+                          cudaStream_t st) {
+    if (wv.B == 0) return cudaSuccess;
+    output_kernel<<<(unsigned)wv.B, 128, 0, st>>>(wv, ids, dists, offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collect(const IndexView& ix, const WaveView& wv, int w, int delta_d, int S,
+                           const CollectArgs& ca, int64_t qoff, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)sms * 4;
+    if (ix.dtype == DADE_SLAB_F32)
+        collect_kernel<DADE_SLAB_F32><<<grid, kScanThreads, 0, st>>>(ix, wv, w, delta_d, S, ca, qoff);
+    else if (ix.dtype == DADE_SLAB_BF16)
+        collect_kernel<DADE_SLAB_BF16><<<grid, kScanThreads, 0, st>>>(ix, wv, w, delta_d, S, ca, qoff);
+    else
+        collect_kernel<DADE_SLAB_FP8E4M3><<<grid, kScanThreads, 0, st>>>(ix, wv, w, delta_d, S, ca, qoff);
+    return cudaGetLastError();
+}
+
+}  // namespace dade

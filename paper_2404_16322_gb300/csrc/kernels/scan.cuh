@@ -1,0 +1,64 @@
+// Device views shared by the refinement kernels (scan.cu) and the search
+// orchestration (search.cu).
+#pragma once
+
+#include "../dade_internal.h"
+
+namespace dade {
+
+constexpr int kG = 16;             // queries per work unit
+constexpr int kT = 256;            // candidates per tile of a bucket
+constexpr int kScanThreads = 256;  // 8 warps, each owns kG / 8 queries
+constexpr int kMergeCap = 4096;    // (distance, id) pairs sorted at once by the merge
+
+struct IndexView {
+    const void* slab;          // rotated vectors, blocked, slab dtype
+    const float* orig;         // original vectors, blocked, FP32
+    const int64_t* ids;        // per slot
+    const int64_t* list_slot;  // nlist + 1
+    const int32_t* list_size;  // nlist
+    const float* scale;        // FP8 per-dimension scale (Dpad)
+    int32_t D, Dpad, nb, nlist, dtype;
+};
+
+struct WaveView {
+    int64_t B;
+    int32_t P, Kmax, first_wave, n_waves;
+    const float* qrot;        // B x Dpad rotated queries
+    const float* qpad;        // B x Dpad original queries, zero padded
+    const int32_t* probes;    // B x P
+    const int32_t* nprobe;    // B
+    const int32_t* K;         // B
+    int32_t* cnt_wl;          // n_waves x nlist: queries probing (wave, bucket)
+    int32_t* off_wl;          // n_waves x nlist + 1: exclusive prefix of cnt_wl
+    int32_t* fill_wl;         // n_waves x nlist: scatter cursors
+    int32_t* items;           // B x P query ids grouped by (wave, bucket)
+    int32_t* unit_off;        // n_waves x (nlist + 1): work units per wave, prefix
+    int64_t* cand_off;        // n_waves x (B + 1): candidate capacity per query, prefix
+    int32_t* cand_cnt;        // B: candidates appended in the current wave
+    float* cand_d;            // candidate buffer (capacity of the largest wave)
+    int32_t* cand_pos;
+    float* top_d;             // B x Kmax current top-K distances (sorted)
+    int64_t* top_id;          // B x Kmax
+    int32_t* top_n;           // B
+    float* tau;               // B: the K-th distance (+inf while fewer than K)
+    int32_t* work;            // 2 x n_waves work counters (scan, collect)
+    int32_t* status;          // device status word
+    int64_t* stats;           // B x 4 or null
+    unsigned long long* staged_bytes;  // bytes staged by the scan, or null
+};
+
+cudaError_t launch_prepare_queries(const float* Q, int64_t B, int32_t D, int32_t Dpad,
+                                   float* qpad, cudaStream_t st);
+cudaError_t launch_fill(float* p, int64_t n, float v, cudaStream_t st);
+cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStream_t st);
+cudaError_t launch_wave_scan(const IndexView& ix, const WaveView& wv, int w, bool full,
+                             int delta_d, const float* m1, const float* beta, int S,
+                             cudaStream_t st);
+cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStream_t st);
+cudaError_t launch_output(const WaveView& wv, int64_t* ids, float* dists,
+                          const int64_t* offsets, cudaStream_t st);
+cudaError_t launch_collect(const IndexView& ix, const WaveView& wv, int w, int delta_d, int S,
+                           const CollectArgs& ca, int64_t query_offset, cudaStream_t st);
+
+}  // namespace dade

@@ -1,0 +1,289 @@
+// dade_search: the batched search pipeline on one stream.
+//   rotate queries (GEMM) -> centroid distances (GEMM) -> top-nprobe select
+//   -> work units per wave -> per wave: estimate-and-prune scan, top-K merge
+//   -> output.
+// Every launch goes to the caller's stream; nothing synchronises the host.
+#include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "dade_internal.h"
+#include "kernels/scan.cuh"
+
+namespace dade {
+namespace {
+
+// Stage timing state (process-wide): event pairs around scan launches and a
+// device counter of staged bytes.
+struct StageTiming {
+    std::mutex mu;
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    unsigned long long* bytes = nullptr;
+};
+StageTiming& timing() {
+    static StageTiming t;
+    return t;
+}
+
+struct Carve {
+    char* base;
+    size_t off = 0;
+    template <class T> T* take(size_t n) {
+        off = (size_t)round_up((int64_t)off, 256);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+struct Plan {
+    WaveView wv{};
+    float* scores = nullptr;
+    char* zero_begin = nullptr;
+    size_t zero_bytes = 0;
+    int32_t* status_internal = nullptr;
+    int64_t cand_cap = 0;
+};
+
+// Upper bound of one wave's candidates for a query: the sum of the largest
+// (end - begin) bucket sizes.
+int64_t wave_bound(const dade_index* idx, int P, int f, int w) {
+    int b0 = wave_begin(w, f), b1 = std::min(P, wave_begin(w + 1, f));
+    int n = std::max(0, b1 - b0);
+    n = std::min<int>(n, idx->nlist);
+    return idx->sizes_desc_prefix[n];
+}
+
+size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* base, Plan* pl) {
+    const int P = o.max_nprobe, Kmax = o.max_K;
+    const bool frozen = o.tau_dev != nullptr;
+    const int f = frozen ? P : std::max(1, o.first_wave);
+    const int nw = num_waves(P, f);
+    const int64_t nl = idx->nlist;
+    int64_t cap_per_q = 0;
+    for (int w = 0; w < nw; ++w) cap_per_q = std::max(cap_per_q, wave_bound(idx, P, f, w));
+    Carve c{base};
+    WaveView& v = pl->wv;
+    v.B = B;
+    v.P = P;
+    v.Kmax = Kmax;
+    v.first_wave = f;
+    v.n_waves = nw;
+    v.qrot = c.take<float>((size_t)B * idx->Dpad);
+    v.qpad = c.take<float>((size_t)B * idx->Dpad);
+    pl->scores = o.probe_in_dev ? nullptr : c.take<float>((size_t)B * nl);
+    v.probes = c.take<int32_t>((size_t)B * P);
+    v.off_wl = c.take<int32_t>((size_t)nw * nl + 1);
+    v.items = c.take<int32_t>((size_t)B * P);
+    v.unit_off = c.take<int32_t>((size_t)nw * (nl + 1));
+    pl->cand_cap = B * cap_per_q;
+    v.cand_d = c.take<float>((size_t)std::max<int64_t>(1, pl->cand_cap));
+    v.cand_pos = c.take<int32_t>((size_t)std::max<int64_t>(1, pl->cand_cap));
+    v.top_d = c.take<float>((size_t)B * Kmax);
+    v.top_id = c.take<int64_t>((size_t)B * Kmax);
+    v.tau = c.take<float>((size_t)B);
+    // zero-initialised block
+    c.off = (size_t)round_up((int64_t)c.off, 256);
+    size_t z0 = c.off;
+    v.cnt_wl = c.take<int32_t>((size_t)nw * nl);
+    v.fill_wl = c.take<int32_t>((size_t)nw * nl);
+    v.cand_off = c.take<int64_t>((size_t)nw * (B + 1));
+    v.cand_cnt = c.take<int32_t>((size_t)B);
+    v.top_n = c.take<int32_t>((size_t)B);
+    v.work = c.take<int32_t>((size_t)2 * nw);
+    pl->status_internal = c.take<int32_t>(1);
+    pl->zero_begin = base ? base + z0 : nullptr;
+    pl->zero_bytes = c.off - z0;
+    return c.off + 256;
+}
+
+dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o) {
+    if (!idx) return fail(DADE_EINVAL, "null index");
+    if (B < 0 || B > (int64_t)1 << 24) return fail(DADE_EINVAL, "B out of range: %lld", (long long)B);
+    if (o.max_K < 1 || o.max_K > kMaxK) return fail(DADE_EINVAL, "max_K must be in [1, %d]", kMaxK);
+    if (o.max_nprobe < 1 || o.max_nprobe > std::min(idx->nlist, 1024))
+        return fail(DADE_EINVAL, "max_nprobe must be in [1, min(nlist, 1024)]");
+    if (o.mode != DADE_SCAN_PRUNE && o.mode != DADE_SCAN_FULL) return fail(DADE_EINVAL, "bad mode");
+    if (o.first_wave < 0) return fail(DADE_EINVAL, "first_wave < 0");
+    if (o.mode == DADE_SCAN_PRUNE) {
+        if (delta_d != 8 && delta_d != 16 && delta_d != 32)
+            return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32 (got %d)", delta_d);
+        int S = (int)ceil_div(idx->Dpad, delta_d);
+        if (S > 1 && !idx->tables.count(delta_d))
+            return fail(DADE_ESTATE, "no correction table for delta_d = %d", delta_d);
+    }
+    return DADE_OK;
+}
+
+}  // namespace
+
+size_t workspace_bytes(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o,
+                       const CollectArgs*) {
+    (void)delta_d;
+    Plan pl;
+    return carve(idx, B, o, nullptr, &pl);
+}
+
+dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const int32_t* K_dev,
+                        const int32_t* nprobe_dev, int32_t delta_d, const dade_search_opts& o,
+                        int64_t* ids_dev, float* dists_dev, const int64_t* offsets, cudaStream_t st,
+                        const CollectArgs* collect) {
+    DADE_TRY(check_args(idx, B, delta_d, o));
+    if (B == 0) return DADE_OK;
+    if (!Q || !K_dev || !nprobe_dev || !ids_dev || !dists_dev) return fail(DADE_EINVAL, "null buffer");
+    Plan pl;
+    size_t need = carve(idx, B, o, nullptr, &pl);
+    char* base;
+    if (o.workspace) {
+        if (o.workspace_bytes < need)
+            return fail(DADE_EINVAL, "workspace too small: %zu < %zu bytes", o.workspace_bytes, need);
+        base = static_cast<char*>(o.workspace);
+    } else {
+        if (idx->ws.bytes < need) {
+            idx->ws.release();
+            DADE_TRY(idx->ws.alloc(need));
+        }
+        base = idx->ws.as<char>();
+    }
+    base = reinterpret_cast<char*>(round_up(reinterpret_cast<int64_t>(base), 256));
+    carve(idx, B, o, base, &pl);
+    WaveView& v = pl.wv;
+    v.nprobe = nprobe_dev;
+    v.K = K_dev;
+    v.status = o.status_dev ? o.status_dev : pl.status_internal;
+    v.stats = o.stats_dev;
+    StageTiming& tm = timing();
+    const bool timed = tm.on && !collect;
+    v.staged_bytes = timed ? tm.bytes : nullptr;
+
+    IndexView ix;
+    ix.slab = idx->slab_dev.p;
+    ix.orig = idx->orig_dev.as<float>();
+    ix.ids = idx->ids_dev.as<int64_t>();
+    ix.list_slot = idx->list_slot_dev.as<int64_t>();
+    ix.list_size = idx->list_size_dev.as<int32_t>();
+    ix.scale = idx->scale_dev.as<float>();
+    ix.D = idx->D;
+    ix.Dpad = idx->Dpad;
+    ix.nb = idx->nb;
+    ix.nlist = idx->nlist;
+    ix.dtype = idx->dtype;
+
+    const bool full = o.mode == DADE_SCAN_FULL;
+    const int S = (int)ceil_div(idx->Dpad, delta_d > 0 ? delta_d : idx->Dpad);
+    const float *m1 = nullptr, *beta = nullptr;
+    if (!full && S > 1) {
+        const CorrectionTable& tb = idx->tables.at(delta_d);
+        m1 = tb.m1_dev;
+        beta = tb.beta_dev;
+    }
+
+    DADE_CUDA_TRY(cudaMemsetAsync(pl.zero_begin, 0, pl.zero_bytes, st));
+    if (o.tau_dev)
+        DADE_CUDA_TRY(cudaMemcpyAsync(v.tau, o.tau_dev, sizeof(float) * B, cudaMemcpyDeviceToDevice, st));
+    else
+        DADE_CUDA_TRY(launch_fill(v.tau, B, INFINITY, st));
+
+    // 1. q' = R (q - mean); the original query zero-padded to Dpad
+    DADE_CUDA_TRY(launch_gemm_store(GEMM_DOT, Q, idx->D, idx->mean_dev.as<float>(),
+                                    idx->R_dev.as<float>(), idx->Dpad, const_cast<float*>(v.qrot),
+                                    idx->Dpad, B, idx->Dpad, idx->D, st));
+    DADE_CUDA_TRY(launch_prepare_queries(Q, B, idx->D, idx->Dpad, const_cast<float*>(v.qpad), st));
+    if (o.qrot_out_dev) {
+        DADE_CUDA_TRY(cudaMemcpy2DAsync(o.qrot_out_dev, sizeof(float) * idx->D, v.qrot,
+                                        sizeof(float) * idx->Dpad, sizeof(float) * idx->D, B,
+                                        cudaMemcpyDeviceToDevice, st));
+    }
+    // 2. buckets to probe
+    if (o.probe_in_dev) {
+        DADE_CUDA_TRY(cudaMemcpyAsync(const_cast<int32_t*>(v.probes), o.probe_in_dev,
+                                      sizeof(int32_t) * B * v.P, cudaMemcpyDeviceToDevice, st));
+    } else {
+        DADE_CUDA_TRY(launch_gemm_store(GEMM_L2, v.qrot, idx->Dpad, nullptr, idx->cent_dev.as<float>(),
+                                        idx->Dpad, pl.scores, idx->nlist, B, idx->nlist, idx->Dpad, st));
+        DADE_CUDA_TRY(launch_select_probes(pl.scores, B, idx->nlist, nprobe_dev, v.P,
+                                           const_cast<int32_t*>(v.probes), v.status, st));
+    }
+    if (o.probe_out_dev)
+        DADE_CUDA_TRY(cudaMemcpyAsync(o.probe_out_dev, v.probes, sizeof(int32_t) * B * v.P,
+                                      cudaMemcpyDeviceToDevice, st));
+    // 3. work units of every wave
+    DADE_CUDA_TRY(launch_build_units(ix, v, st));
+    // 4-5. waves
+    for (int w = 0; w < v.n_waves; ++w) {
+        if (collect) DADE_CUDA_TRY(launch_collect(ix, v, w, delta_d, S, *collect, collect->query_offset, st));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed) {
+            DADE_CUDA_TRY(cudaEventCreate(&e0));
+            DADE_CUDA_TRY(cudaEventCreate(&e1));
+            DADE_CUDA_TRY(cudaEventRecord(e0, st));
+        }
+        DADE_CUDA_TRY(launch_wave_scan(ix, v, w, full || S <= 1, delta_d, m1, beta, S, st));
+        if (timed) {
+            DADE_CUDA_TRY(cudaEventRecord(e1, st));
+            std::lock_guard<std::mutex> lk(tm.mu);
+            tm.ev.emplace_back(e0, e1);
+        }
+        DADE_CUDA_TRY(launch_merge(ix, v, w, st));
+    }
+    DADE_CUDA_TRY(launch_output(v, ids_dev, dists_dev, offsets, st));
+    return DADE_OK;
+}
+
+}  // namespace dade
+
+extern "C" dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,
+                                   const int32_t* K_dev, const int32_t* nprobe_dev, int32_t delta_d,
+                                   const dade_search_opts* opts, int64_t* ids_dev, float* dists_dev,
+                                   const int64_t* out_offsets_dev, void* cuda_stream) {
+    dade::clear_error();
+    if (!opts) return dade::fail(DADE_EINVAL, "opts is required (max_K, max_nprobe)");
+    return dade::search_impl(idx, Q_dev, B, K_dev, nprobe_dev, delta_d, *opts, ids_dev, dists_dev,
+                             out_offsets_dev, static_cast<cudaStream_t>(cuda_stream), nullptr);
+}
+
+extern "C" dade_status dade_stage_timing(int32_t enable) {
+    dade::clear_error();
+    dade::StageTiming& t = dade::timing();
+    std::lock_guard<std::mutex> lk(t.mu);
+    if (enable && !t.bytes) {
+        DADE_CUDA_TRY(cudaMalloc(&t.bytes, sizeof(unsigned long long)));
+        DADE_CUDA_TRY(cudaMemset(t.bytes, 0, sizeof(unsigned long long)));
+    }
+    t.on = enable != 0;
+    return DADE_OK;
+}
+
+extern "C" dade_status dade_stage_timing_read(double* scan_ms, int64_t* launches, double* bytes) {
+    dade::clear_error();
+    dade::StageTiming& t = dade::timing();
+    std::lock_guard<std::mutex> lk(t.mu);
+    double ms = 0;
+    for (auto& e : t.ev) {
+        DADE_CUDA_TRY(cudaEventSynchronize(e.second));
+        float x = 0;
+        DADE_CUDA_TRY(cudaEventElapsedTime(&x, e.first, e.second));
+        ms += x;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    if (launches) *launches = (int64_t)t.ev.size();
+    t.ev.clear();
+    unsigned long long b = 0;
+    if (t.bytes) {
+        DADE_CUDA_TRY(cudaMemcpy(&b, t.bytes, sizeof b, cudaMemcpyDeviceToHost));
+        DADE_CUDA_TRY(cudaMemset(t.bytes, 0, sizeof b));
+    }
+    if (scan_ms) *scan_ms = ms;
+    if (bytes) *bytes = (double)b;
+    return DADE_OK;
+}
+
+extern "C" size_t dade_search_workspace_size(const dade_index* idx, int64_t B, int32_t delta_d,
+                                             const dade_search_opts* opts) {
+    if (!idx || !opts || B < 0) return 0;
+    if (dade::check_args(idx, B, delta_d, *opts) != DADE_OK) return 0;
+    return dade::workspace_bytes(idx, B, delta_d, *opts, nullptr);
+}

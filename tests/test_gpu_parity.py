@@ -1,0 +1,286 @@
+"""GPU parity: the CUDA path against the oracle on the same seeded inputs.
+
+Both sides get the oracle's rotation, centroids, bucket assignment and
+correction tables; the comparisons follow tests/parity.py."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ivf, knn, search
+
+from . import gpu_helpers as H
+from . import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2404_16322_gb300 import build
+    build.build()
+    import paper_2404_16322_gb300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def tiny_setup(G):
+    """The small workload with the rotation done by each side (FP64 oracle,
+    FP32 GEMM on the device)."""
+    X, Q, T, cfg = synth.workload("tiny")
+    inp = H.oracle_inputs(X, T, cfg["nlist"], K=10, nprobe=8, delta_d=16)
+    idx = H.build_gpu(G, X, inp, cfg["nlist"])
+    return dict(X=X, Q=Q, T=T, cfg=cfg, inp=inp, idx=idx, amb="f32", strict=0.85)
+
+
+@pytest.fixture(scope="module")
+def tiny_pre(G):
+    """The small workload pre-rotated by the oracle: both sides see the same
+    FP32 rotated vectors (R = I), so only FP32 accumulation differs."""
+    X, Q, T, cfg = synth.workload("tiny")
+    inp = H.oracle_inputs(X, T, cfg["nlist"], K=10, nprobe=8, delta_d=16, prerotate=True)
+    idx = H.build_gpu(G, None, inp, cfg["nlist"])
+    return dict(X=inp["X"], Q=inp["rot"](Q), cfg=cfg, inp=inp, idx=idx, amb="exact", strict=0.95)
+
+
+def _oracle(s, Q, K, nprobe, delta_d=16, m1=None, beta=None, mode="waves", tau=None, dtype_amb=None,
+            oidx=None, probes=None):
+    dtype_amb = dtype_amb or s.get("amb", "f32")
+    oidx = oidx or s["inp"]["oidx"]
+    P = int(np.max(nprobe))
+    pr = probes if probes is not None else oidx.probe(oidx.rotate_queries(Q), P)
+    m1 = s["inp"]["m1"] if m1 is None else m1
+    beta = s["inp"]["beta"] if beta is None else beta
+    ids, d, st = search.search(oidx, Q, pr, nprobe, K, delta_d, m1.astype(np.float64),
+                               beta.astype(np.float64), mode=mode, tau=tau, amb=H.AMB[dtype_amb])
+    return ids, d, st, pr
+
+
+def test_rotated_queries_match_oracle(G, tiny_setup):
+    s = tiny_setup
+    out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, want=("qrot",))
+    ref = s["inp"]["oidx"].rotate_queries(s["Q"])
+    err = np.abs(out["qrot"] - ref).max(axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() < 1e-5
+
+
+def test_probes_match_oracle_up_to_near_ties(G, tiny_setup):
+    s = tiny_setup
+    P = 8
+    out = H.gpu_search(G, s["idx"], s["Q"], 10, P, 16, want=("probes",))
+    oidx = s["inp"]["oidx"]
+    Qr = oidx.rotate_queries(s["Q"])
+    d = ivf.sq_dists(Qr, oidx.C)
+    lists, _ = ivf.probe(Qr, oidx.C, oidx.nlist)
+    n_exact = 0
+    for b in range(len(s["Q"])):
+        g, o = out["probes"][b], lists[b, :P]
+        if np.array_equal(g, o):
+            n_exact += 1
+            continue
+        # a difference is allowed only among centroids within 1e-5 of the boundary
+        kth = d[b, lists[b, P - 1]]
+        for l in set(g) ^ set(o):
+            assert abs(d[b, l] - kth) <= 1e-5 * kth
+    assert n_exact >= 0.95 * len(s["Q"])
+
+
+@pytest.mark.parametrize("setup", ["tiny_setup", "tiny_pre"])
+@pytest.mark.parametrize("mode", ["waves", "tables_off"])
+def test_prune_path_matches_oracle(G, request, setup, mode):
+    s = request.getfixturevalue(setup)
+    Q = s["Q"]
+    if mode == "waves":
+        ids, d, st, pr = _oracle(s, Q, 10, 8)
+        out = H.gpu_search(G, s["idx"], Q, 10, 8, 16, probe_in=pr, want=("stats",))
+    else:
+        S = search.n_steps(128, 16)
+        m1, beta = search.disabled_tables(S)
+        ids, d, st, pr = _oracle(s, Q, 10, 8, m1=m1, beta=beta)
+        G.dade_set_correction(s["idx"], 16, m1.astype(np.float32), beta.astype(np.float32))
+        try:
+            out = H.gpu_search(G, s["idx"], Q, 10, 8, 16, probe_in=pr, want=("stats",))
+        finally:
+            G.dade_set_correction(s["idx"], 16, s["inp"]["m1"], s["inp"]["beta"])
+    assert out["status"] == 0
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], Q, 10, amb=st[:, 4], min_strict=s["strict"])
+    # work accounting equals the oracle's wherever no decision was ambiguous
+    un = st[:, 4] == 0
+    assert np.array_equal(out["stats"][:, 0], st[:, 0])
+    assert np.array_equal(out["stats"][un], st[un, :4])
+    assert st[:, 1].sum() > 0 or mode != "waves"
+
+
+def test_full_scan_matches_oracle_exact_over_probed(G, tiny_setup):
+    s = tiny_setup
+    S = search.n_steps(128, 16)
+    ids, d, st, pr = _oracle(s, s["Q"], 10, 8, m1=search.disabled_tables(S)[0],
+                             beta=search.disabled_tables(S)[1])
+    out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 0, mode="full", probe_in=pr)
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb=None, min_strict=1.0)
+
+
+def test_end_to_end_without_given_probes(G, tiny_setup):
+    s = tiny_setup
+    out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, want=("probes",))
+    ids, d, st, pr = _oracle(s, s["Q"], 10, 8)
+    same = np.all(out["probes"] == pr, axis=1)
+    amb = np.where(same, st[:, 4], 1)
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb=amb, min_strict=0.8)
+
+
+def test_frozen_tau_matches_oracle(G, tiny_pre):
+    s = tiny_pre
+    S = search.n_steps(128, 16)
+    _, d0, _, pr = _oracle(s, s["Q"], 10, 8, m1=search.disabled_tables(S)[0],
+                           beta=search.disabled_tables(S)[1])
+    tau = (d0[:, -1] * 1.05).astype(np.float32)
+    ids, d, st, _ = _oracle(s, s["Q"], 10, 8, mode="frozen", tau=tau.astype(np.float64), probes=pr)
+    out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, tau=tau)
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb=st[:, 4], min_strict=s["strict"])
+
+
+def test_ragged_K_and_nprobe(G, tiny_pre):
+    s = tiny_pre
+    rng = np.random.default_rng(5)
+    B = len(s["Q"])
+    K = rng.integers(1, 21, B).astype(np.int32)
+    npb = rng.integers(1, 17, B).astype(np.int32)
+    ids, d, st, pr = _oracle(s, s["Q"], K, npb)
+    out = H.gpu_search(G, s["idx"], s["Q"], K, npb, 16, probe_in=pr, max_K=20, max_nprobe=16)
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], K, amb=st[:, 4], min_strict=s["strict"])
+    for b in range(B):  # beyond each query's K the output is padding
+        assert np.all(out["ids"][b, K[b]:] == -1)
+
+
+@pytest.mark.parametrize("dtype,delta_d", [("f32", 8), ("f32", 32), ("bf16", 8), ("bf16", 16),
+                                           ("bf16", 32), ("fp8", 8), ("fp8", 16), ("fp8", 32)])
+def test_slab_precisions_and_step_widths_strict(G, dtype, delta_d):
+    # pre-rotated inputs: both sides quantise the same FP32 values
+    X, Q, T, cfg = synth.workload("tiny", n_train=600)
+    inp = H.oracle_inputs(X, T, cfg["nlist"], K=10, nprobe=8, delta_d=delta_d, dtype=dtype, n_train=600,
+                          prerotate=True)
+    idx = H.build_gpu(G, None, inp, cfg["nlist"], dtype=dtype, delta_d=delta_d)
+    s = dict(inp=inp)
+    Qr = inp["rot"](Q)
+    ids, d, st, pr = _oracle(s, Qr, 10, 8, delta_d=delta_d, dtype_amb="exact")
+    out = H.gpu_search(G, idx, Qr, 10, 8, delta_d, probe_in=pr, want=("stats",))
+    parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, 10, amb=st[:, 4], min_strict=0.9)
+    un = st[:, 4] == 0
+    assert np.array_equal(out["stats"][un], st[un, :4])
+    idx.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_low_precision_slabs_with_device_rotation(G, dtype):
+    # the device rotates and quantises its own FP32 values: decisions inside
+    # the format's band may differ, so only distances, validity and recall
+    # against the exact top-K over the probed buckets are compared
+    X, Q, T, cfg = synth.workload("tiny", n_train=600)
+    inp = H.oracle_inputs(X, T, cfg["nlist"], K=10, nprobe=8, delta_d=16, dtype=dtype, n_train=600)
+    idx = H.build_gpu(G, X, inp, cfg["nlist"], dtype=dtype, delta_d=16)
+    s = dict(inp=inp)
+    ids, d, st, pr = _oracle(s, Q, 10, 8, dtype_amb=dtype)
+    out = H.gpu_search(G, idx, Q, 10, 8, 16, probe_in=pr)
+    parity.check(out["ids"], out["dists"], ids, d, X, Q, 10, amb=st[:, 4], min_strict=0.0)
+    S = search.n_steps(128, 16)
+    top, _, _, _ = _oracle(s, Q, 10, 8, m1=search.disabled_tables(S)[0], beta=search.disabled_tables(S)[1],
+                           probes=pr)
+    assert parity.recall(out["ids"], top, 10) >= parity.recall(ids, top, 10) - 0.02
+    idx.close()
+
+
+def test_multi_tile_buckets_many_queries_and_ragged_dimension(G):
+    # D = 100 (not a multiple of 8), 6 buckets of ~1000 vectors (several
+    # 256-candidate tiles), 300 queries (several 16-query groups per bucket).
+    spec = synth.MixtureSpec(D=100, n_comp=6, alpha=0.9)
+    X = spec.sample(6000, 1)
+    Q = spec.sample(300, 2)
+    T = spec.sample(400, 3)
+    inp = H.oracle_inputs(X, T, 6, K=20, nprobe=3, delta_d=16, n_train=400, prerotate=True)
+    idx = H.build_gpu(G, None, inp, 6)
+    s = dict(inp=inp)
+    X, Q = inp["X"], inp["rot"](Q)
+    ids, d, st, pr = _oracle(s, Q, 20, 3, dtype_amb="exact")
+    out = H.gpu_search(G, idx, Q, 20, 3, 16, probe_in=pr, want=("stats",))
+    parity.check(out["ids"], out["dists"], ids, d, X, Q, 20, amb=st[:, 4], min_strict=0.95)
+    assert np.array_equal(out["stats"][:, 0], st[:, 0])
+    # all buckets probed with pruning off: exact KNN
+    S = search.n_steps(100, 16)
+    out = H.gpu_search(G, idx, Q, 20, 6, 0, mode="full")
+    gi, gd = knn.exact_knn(X, Q, 20)
+    parity.check(out["ids"], out["dists"], gi, gd, X, Q, 20, amb=None, min_strict=1.0)
+    del S
+    idx.close()
+
+
+def test_large_K_padding_and_empty_batch(G, tiny_setup):
+    s = tiny_setup
+    # K larger than the probed candidates: the tail pads with -1 / +inf
+    ids, d, st, pr = _oracle(s, s["Q"][:5], 1024, 1)
+    out = H.gpu_search(G, s["idx"], s["Q"][:5], 1024, 1, 16, probe_in=pr)
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"][:5], 1024, amb=st[:, 4], min_strict=0.6)
+    assert (out["ids"] == -1).any()
+    out = H.gpu_search(G, s["idx"], s["Q"][:0], 10, 8, 16, max_K=10, max_nprobe=8)
+    assert out["ids"].shape == (0, 10)
+
+
+def test_device_status_reports_bad_per_query_values(G, tiny_setup):
+    s = tiny_setup
+    K = np.full(len(s["Q"]), 10, np.int32)
+    K[3] = 50  # above max_K
+    out = H.gpu_search(G, s["idx"], s["Q"], K, 8, 16, max_K=10)
+    assert out["status"] == 1
+    assert np.all(out["ids"][3] == -1)
+
+
+def test_host_errors(G, tiny_setup):
+    from paper_2404_16322_gb300 import _lib
+    s = tiny_setup
+    with pytest.raises(_lib.DadeError) as e:
+        H.gpu_search(G, s["idx"], s["Q"], 10, 8, 32)  # no table for delta_d = 32
+    assert e.value.status == 5
+    with pytest.raises(_lib.DadeError):
+        H.gpu_search(G, s["idx"], s["Q"], 10, 8, 12)
+    with pytest.raises(_lib.DadeError):
+        H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, max_K=2000)
+
+
+def test_save_load_roundtrip(G, tiny_setup, tmp_path):
+    s = tiny_setup
+    p = tmp_path / "tiny.dade"
+    G.dade_index_save(s["idx"], str(p))
+    idx2 = G.dade_index_load(str(p))
+    a = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16)
+    b = H.gpu_search(G, idx2, s["Q"], 10, 8, 16)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["dists"], b["dists"])
+    raw = bytearray(p.read_bytes())
+    raw[len(raw) // 2] ^= 0xFF
+    p.write_bytes(bytes(raw))
+    from paper_2404_16322_gb300 import _lib
+    with pytest.raises(_lib.DadeError):
+        G.dade_index_load(str(p))
+    idx2.close()
+
+
+def test_library_build_and_fit_end_to_end(G):
+    # The library's own rotation, k-means and fitted correction: invariants
+    # and recall against exact KNN.
+    X, Q, T, cfg = synth.workload("tiny")
+    mu, R, lam = G.dade_train_rotation(X)
+    idx = G.ivf_build(X, mu, R, cfg["nlist"], kmeans_iters=8, seed=3)
+    a = G.dade_index_assignment(idx)
+    C = G.dade_index_centroids(idx)
+    Xr = (X.astype(np.float64) - mu) @ R.T
+    d = ivf.sq_dists(Xr[:2000], C.astype(np.float64))
+    best = d.min(axis=1)
+    assert np.all(d[np.arange(2000), a[:2000]] <= best * (1 + 1e-5) + 1e-6)
+    m1, beta = G.dade_fit_correction(idx, T, 10, 8, 16)
+    assert np.all(np.isfinite(m1)) and np.any(np.isfinite(beta))
+    out = H.gpu_search(G, idx, Q, 10, 8, 16, want=("stats",))
+    full = H.gpu_search(G, idx, Q, 10, 8, 0, mode="full")
+    gi, _ = knn.exact_knn(X, Q, 10)
+    r_prune = parity.recall(out["ids"], gi, 10)
+    r_full = parity.recall(full["ids"], gi, 10)
+    assert r_prune >= r_full - 0.02
+    assert out["stats"][:, 1].sum() > 0.5 * out["stats"][:, 0].sum()
+    idx.close()
