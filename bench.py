@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 TARGET_RECALL = 0.95
-NPROBES = [8, 12, 16, 24, 32, 48, 64, 96, 128]
+NPROBES = [8, 16, 24, 32, 48, 64, 96, 128, 192, 256]
 DELTAS = [8, 16, 32]
 METRIC = "QPS at recall@10>=0.95 (estimate-and-prune IVF search, SIFT-shaped 1M x 128, nlist 4096, K 100)"
 
@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--queries", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-queries", type=int, default=400)
+    ap.add_argument("--profile", default=None,
+                    help="NPROBE,DELTA_D: skip the sweep and baselines; run W + K steps of that "
+                         "configuration inside the NVTX range 'dade_timed' (for ncu captures)")
     return ap.parse_args()
 
 
@@ -163,7 +166,7 @@ class Runner:
         if stats:
             self.stats.zero_()
         self.G.dade_search(self.idx, self.q, self.k, self.np, delta_d, self.ids, self.d, max_K=self.K,
-                           max_nprobe=self.max_nprobe, mode=mode, status=self.status,
+                           max_nprobe=nprobe, mode=mode, status=self.status,
                            stats=self.stats if stats else None, workspace=self.ws)
 
     def result(self):
@@ -320,13 +323,28 @@ def main():
     mean, R, _ = G.dade_train_rotation(X, sample_n=min(len(X), 1_000_000), seed=1)
     idx = G.ivf_build(X, mean, R, nlist, kmeans_iters=10, seed=1, dtype="f32")
     fit_nprobe = min(64, nlist)
-    for dd in DELTAS:
+    fit_deltas = DELTAS if not args.profile else [int(args.profile.split(",")[1])]
+    for dd in fit_deltas:
         G.dade_fit_correction(idx, T, K, fit_nprobe, dd, target_recall=0.995, seed=1)
     gt = ground_truth(X, Q, 10)
     setup_s = time.perf_counter() - t_setup
 
     maxp = min(max(NPROBES), nlist)
     run = Runner(G, idx, Q, K, maxp)
+    if args.profile:
+        npb, dd = (int(x) for x in args.profile.split(","))
+        for _ in range(args.warmup):
+            run.run(npb, dd, "prune")
+        run.result()
+        torch.cuda.nvtx.range_push("dade_timed")
+        for _ in range(args.steps):
+            run.run(npb, dd, "prune")
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        ids = run.result()
+        print(json.dumps({"profile": args.profile, "recall@10": recall_at(ids, gt), "steps": args.steps,
+                          "launches_per_step": 11 + 2 * n_waves(npb), "setup_s": time.perf_counter() - t_setup}))
+        return
     # --- sweep: recall per (mode, delta_d, nprobe); short timing of each
     sweep = []
     for mode, dds in (("full", [0]), ("prune", DELTAS)):
@@ -409,8 +427,8 @@ def main():
         run.q.copy_(q_h, non_blocking=True)
         run.k.copy_(k_h, non_blocking=True)
         run.np.copy_(n_h, non_blocking=True)
-        G.dade_search(idx, run.q, run.k, run.np, bd["delta_d"], run.ids, run.d, max_K=K, max_nprobe=maxp,
-                      status=run.status, workspace=run.ws)
+        G.dade_search(idx, run.q, run.k, run.np, bd["delta_d"], run.ids, run.d, max_K=K,
+                      max_nprobe=bd["nprobe"], status=run.status, workspace=run.ws)
         ids_h.copy_(run.ids, non_blocking=True)
         d_h.copy_(run.d, non_blocking=True)
 

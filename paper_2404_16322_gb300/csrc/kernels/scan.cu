@@ -21,6 +21,8 @@
 // not depend on which path computed it): per 8-dim block b,
 // s_b = sum_j fma((q_j - x_j)^2) from 0 in j order; the distance adds s_b in
 // block order.  This bounds the FP32 rounding by (8 + D/8) ulp-terms.
+#include <climits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -71,7 +73,7 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 // Bounded wait: gives up after ~2 s, records DADE_ETIMEOUT and returns false.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* status) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* status) {
     if (mbar_try_wait(bar, parity)) return true;
     uint64_t t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
@@ -162,7 +164,7 @@ struct Unit {
     int l, t, nq, nt, item;
 };
 
-__device__ Unit decode_unit(const IndexView& ix, const WaveView& wv, int w, int u) {
+__device__ __forceinline__ Unit decode_unit(const IndexView& ix, const WaveView& wv, int w, int u) {
     const int32_t* uo = wv.unit_off + (int64_t)w * (ix.nlist + 1);
     int lo = 0, hi = ix.nlist;
     while (hi - lo > 1) {
@@ -205,16 +207,64 @@ __device__ __forceinline__ void append(const WaveView& wv, int w, int q, bool ap
     }
 }
 
+// ------------------------------------------------------------ exact distance
+// Exact distance of one candidate per SEG-lane segment of the warp (SEG = the
+// smallest power of two >= nb, at most 32).  Lane j of a segment forms the
+// block sums s_b of blocks j, j + SEG, ...; every lane of the segment then
+// adds the segment's s_b in block order with shuffles, so the result is the
+// same as the staged path's d += s_b (block order) and every lane holds it.
+__device__ __forceinline__ int seg_lanes(int nb) {
+    int s = 1;
+    while (s < nb && s < 32) s <<= 1;
+    return s;
+}
+
+__device__ __forceinline__ float exact_coop(const float* xo, int64_t npad, const float* qp, bool valid, int nb,
+                            int lane, int seg) {
+    const int j = lane & (seg - 1), segbase = lane & ~(seg - 1);
+    float d = 0.f;
+    for (int r = 0; r < nb; r += seg) {
+        float mine = 0.f;
+        const int b = r + j;
+        if (valid && b < nb) {
+            float x[8], q[8];
+            load8(xo + (int64_t)b * npad * kBlock, nullptr, x);
+            load_q8(qp + b * kBlock, q);
+            mine = block_sq(q, x);
+        }
+        const int nr = min(seg, nb - r);
+        for (int jj = 0; jj < nr; ++jj) d += __shfl_sync(0xffffffffu, mine, segbase + jj);
+    }
+    return d;
+}
+
 // ------------------------------------------------------------ step pipeline
+// A unit's live candidates are kept per (query, segment) pair: when the unit
+// has fewer queries than warps, ws = kWarps / nq (a power of two) warps share
+// a query, each owning the fixed segment [j * kT / ws, (j + 1) * kT / ws) of
+// the tile with its own compacted list, so every warp has work.  Pair
+// p = g * ws + j; warp w handles pairs w, w + kWarps, ...  (nq * ws <= kG).
+constexpr int kQs = 4 * kBlock;  // widest step (Delta_d = 32) in floats
+
 struct StepShared {
-    unsigned char* buf[2];
+    unsigned char* buf0;        // two slab buffers at buf0 and buf0 + buf_bytes
+    int buf_bytes;
     uint64_t* bar;
-    uint16_t* alive;  // kG x kT candidate indices (compacted)
-    float* part;      // kG x kT partial distances
-    int* n;           // kG live counts
-    const int* q;     // kG query ids
-    const float* tau; // kG
+    uint8_t* alive;             // kG x kT candidate indices (compacted per pair)
+    float* part;                // kG x kT partial distances
+    int* n;                     // live count per pair
+    unsigned long long* st;     // per pair: candidates, pruned, exact, dims
+    float* qs;                  // kG x kQs: the step's query values
+    float* sc;                  // kQs: the step's FP8 scales
+    const int* q;               // kG query ids
+    const float* tau;           // kG
+    int ws;                     // warps (segments) per query
 };
+
+__device__ __forceinline__ int pair_base(const StepShared& sh, int p) {
+    const int g = p / sh.ws, j = p - g * sh.ws;
+    return g * kT + j * (kT / sh.ws);
+}
 
 // Runs `nsteps` slab steps over the tile: slab k covers blocks
 // [k*NBLK, min((k+1)*NBLK, nb)) of the source (rotated slabs in PRUNE mode,
@@ -223,22 +273,23 @@ struct StepShared {
 // +inf are skipped in PRUNE mode (they cannot be pruned).  Returns false if
 // a bounded wait gave up.
 template <class E, int NBLK, bool PRUNE>
-__device__ bool run_steps(const E* src, int64_t npad, int t, int nt, int nq, int nsteps, int nb,
-                          int D, StepShared& sh, uint32_t (&ph)[2], const float* qsrc, int Dpad,
+__device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int nt, int nq, int nsteps, int nb,
+                          int D, const StepShared& sh, uint32_t& phase_bits, const float* qsrc, int Dpad,
                           const float* m1, const float* beta, const float* scale,
-                          int32_t* status, int64_t (&wstat)[2][4], unsigned long long* staged) {
+                          int32_t* status, unsigned long long* staged) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt_copy = (nt + 31) & ~31;
     const uint32_t blk_bytes = (uint32_t)nt_copy * kBlock * sizeof(E);
-    auto issue = [&](int k) {
+    // phase_bits bit b is the parity to wait for on buffer b
+    auto issue = [src, npad, t, nb, blk_bytes, staged, &sh](int k) {
         int b0 = k * NBLK, nbk = min(NBLK, nb - b0);
-        unsigned char* dst = sh.buf[k & 1];
+        unsigned char* dst = sh.buf0 + (k & 1) * sh.buf_bytes;
         fence_proxy_async();
-        mbar_expect_tx(&sh.bar[k & 1], blk_bytes * nbk);
+        mbar_expect_tx(sh.bar + (k & 1), blk_bytes * nbk);
         for (int bb = 0; bb < nbk; ++bb)
             bulk_g2s(dst + (size_t)bb * kT * kBlock * sizeof(E),
                      src + ((int64_t)(b0 + bb) * npad + (int64_t)t * kT) * kBlock, blk_bytes,
-                     &sh.bar[k & 1]);
+                     sh.bar + (k & 1));
         if (staged) atomicAdd(staged, (unsigned long long)blk_bytes * nbk);
     };
     if (nsteps <= 0) return true;
@@ -246,86 +297,91 @@ __device__ bool run_steps(const E* src, int64_t npad, int t, int nt, int nq, int
     int k = 0;
     bool pending_next = false;
     for (; k < nsteps; ++k) {
-        bool got = mbar_wait(&sh.bar[k & 1], ph[k & 1], status);
-        ph[k & 1] ^= 1u;
+        const int b0 = k * NBLK, nbk = min(NBLK, nb - b0), w8 = nbk * kBlock;
+        // the step's query values (and FP8 scales) for every query of the unit
+        for (int e = tid; e < nq * kQs; e += kScanThreads) {
+            const int g = e / kQs, j = e - g * kQs;
+            sh.qs[e] = j < w8 ? qsrc[(int64_t)sh.q[g] * Dpad + b0 * kBlock + j] : 0.f;
+        }
+        if (scale && tid < kQs) sh.sc[tid] = tid < w8 ? scale[b0 * kBlock + tid] : 0.f;
+        bool got = mbar_wait(sh.bar + (k & 1), (phase_bits >> (k & 1)) & 1u, status);
+        phase_bits ^= 1u << (k & 1);
         if (!__syncthreads_and(got)) return false;
         pending_next = k + 1 < nsteps;
         if (tid == 0 && pending_next) issue(k + 1);
-        const E* bk = reinterpret_cast<const E*>(sh.buf[k & 1]);
-        const int b0 = k * NBLK, nbk = min(NBLK, nb - b0);
+        const E* bk = reinterpret_cast<const E*>(sh.buf0 + (k & 1) * sh.buf_bytes);
         const int dims_k = min((k + 1) * NBLK * kBlock, D);
-        for (int g = warp; g < nq; g += kWarps) {
+        for (int p = warp; p < nq * sh.ws; p += kWarps) {
+            const int g = p / sh.ws;
+            const int base_e = pair_base(sh, p);
             const float tau = sh.tau[g];
             if (PRUNE && isinf(tau)) continue;
-            const float* qp = qsrc + (int64_t)sh.q[g] * Dpad + b0 * kBlock;
-            float qv[NBLK][8];
-            float sc[NBLK][8];
-#pragma unroll
-            for (int bb = 0; bb < NBLK; ++bb) {
-                if (bb < nbk) {
-                    load_q8(qp + bb * kBlock, qv[bb]);
-                    if (scale) load_q8(scale + (b0 + bb) * kBlock, sc[bb]);
-                }
-            }
+            const float* qg = sh.qs + g * kQs;
             const float mm = PRUNE ? m1[k] : 0.f, bt = PRUNE ? beta[k] : 0.f;
-            const int n = sh.n[g];
+            const int n = sh.n[p];
             int out = 0;
-            int64_t pruned = 0;
+            int pruned = 0;
             for (int base = 0; base < n; base += 32) {
                 const int i = base + lane;
                 const bool valid = i < n;
                 int c = 0;
-                float p = 0.f;
+                float pd = 0.f;
                 if (valid) {
-                    c = sh.alive[g * kT + i];
-                    p = sh.part[g * kT + i];
+                    c = sh.alive[base_e + i];
+                    pd = sh.part[base_e + i];
 #pragma unroll
                     for (int bb = 0; bb < NBLK; ++bb) {
                         if (bb < nbk) {
-                            float x[8];
-                            load8(bk + ((size_t)bb * kT + c) * kBlock, sc[bb], x);
-                            p += block_sq(qv[bb], x);
+                            float x[8], qv[8];
+                            load8(bk + ((size_t)bb * kT + c) * kBlock, sh.sc + bb * kBlock, x);
+                            load8(qg + bb * kBlock, nullptr, qv);
+                            pd += block_sq(qv, x);
                         }
                     }
                 }
-                const bool keep = valid && !(PRUNE && fmaf(mm, p, bt) > tau);
+                const bool keep = valid && !(PRUNE && fmaf(mm, pd, bt) > tau);
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
                 __syncwarp();
                 if (keep) {
                     const int pos = out + __popc(bal & lanemask_lt());
-                    sh.alive[g * kT + pos] = (uint16_t)c;
-                    sh.part[g * kT + pos] = p;
+                    sh.alive[base_e + pos] = (uint8_t)c;
+                    sh.part[base_e + pos] = pd;
                 }
                 out += __popc(bal);
                 if (PRUNE) pruned += __popc(__ballot_sync(0xffffffffu, valid && !keep));
             }
             __syncwarp();
             if (lane == 0) {
-                sh.n[g] = out;
+                sh.n[p] = out;
                 if (PRUNE) {
-                    wstat[g / kWarps][1] += pruned;
-                    wstat[g / kWarps][3] += pruned * dims_k;
+                    sh.st[p * 4 + 1] += (unsigned long long)pruned;
+                    sh.st[p * 4 + 3] += (unsigned long long)pruned * dims_k;
                 }
             }
         }
         __syncthreads();
         if (PRUNE) {
             int live = 0;
-            for (int g = 0; g < nq; ++g) live |= (!isinf(sh.tau[g]) && sh.n[g] > 0);
+            for (int p = 0; p < nq * sh.ws; ++p) live |= (!isinf(sh.tau[p / sh.ws]) && sh.n[p] > 0);
             if (!live) break;
         }
     }
     if (PRUNE && k < nsteps && pending_next) {
         // the loop left early with the next slab in flight: drain it
         int kn = k + 1;
-        bool got = mbar_wait(&sh.bar[kn & 1], ph[kn & 1], status);
-        ph[kn & 1] ^= 1u;
+        bool got = mbar_wait(sh.bar + (kn & 1), (phase_bits >> (kn & 1)) & 1u, status);
+        phase_bits ^= 1u << (kn & 1);
         if (!__syncthreads_and(got)) return false;
     }
     return true;
 }
 
 // ------------------------------------------------------------ wave scan
+template <int NBLK>
+constexpr int scan_smem_bytes() {
+    return 2 * NBLK * kT * kBlock * 4 + kG * kT * (int)(sizeof(uint8_t) + sizeof(float));
+}
+
 template <int DT, int NBLK, bool FULL>
 __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, WaveView wv, int w,
                                                                  const float* __restrict__ m1,
@@ -336,17 +392,23 @@ __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, W
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_unit, s_l, s_t, s_nq, s_nt, s_inf;
-    __shared__ int s_q[kG], s_n[kG];
+    __shared__ int s_q[kG], s_n[kG];  // s_n per (query, segment) pair
     __shared__ float s_tau[kG];
+    __shared__ unsigned long long s_st[kG * 4];
+    __shared__ __align__(16) float s_qs[kG * kQs];
+    __shared__ __align__(16) float s_sc[kQs];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     StepShared sh;
-    sh.buf[0] = smem;
-    sh.buf[1] = smem + BUF;
-    sh.alive = reinterpret_cast<uint16_t*>(smem + 2 * BUF);
-    sh.part = reinterpret_cast<float*>(smem + 2 * BUF + kG * kT * sizeof(uint16_t));
+    sh.buf0 = smem;
+    sh.buf_bytes = BUF;
+    sh.alive = reinterpret_cast<uint8_t*>(smem + 2 * BUF);
+    sh.part = reinterpret_cast<float*>(smem + 2 * BUF + kG * kT * sizeof(uint8_t));
     sh.bar = bar;
     sh.n = s_n;
+    sh.st = s_st;
+    sh.qs = s_qs;
+    sh.sc = s_sc;
     sh.q = s_q;
     sh.tau = s_tau;
     if (tid == 0) {
@@ -355,9 +417,10 @@ __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, W
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t ph[2] = {0u, 0u};
+    uint32_t ph = 0u;
     const int total = wv.unit_off[(int64_t)w * (ix.nlist + 1) + ix.nlist];
     const int nsteps_full = (ix.nb + NBLK - 1) / NBLK;
+    const int eseg = seg_lanes(ix.nb);
 
     for (;;) {
         if (tid == 0) s_unit = atomicAdd(&wv.work[w], 1);
@@ -375,15 +438,25 @@ __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, W
                 int q = wv.items[un.item + g];
                 s_q[g] = q;
                 s_tau[g] = wv.tau[q];
-                s_n[g] = un.nt;
                 all_inf &= isinf(s_tau[g]) ? 1 : 0;
             }
             s_inf = all_inf;
         }
         __syncthreads();
         const int l = s_l, t = s_t, nq = s_nq, nt = s_nt;
+        int ws = 1;
+        while (ws * 2 * nq <= kWarps) ws *= 2;
+        sh.ws = ws;
+        const int seg = kT / ws;
+        if (tid < nq * ws) {
+            const int j = tid % ws;
+            const int n0 = max(0, min(seg, nt - j * seg));
+            s_n[tid] = n0;
+            s_st[tid * 4 + 0] = (unsigned long long)n0;
+            s_st[tid * 4 + 1] = s_st[tid * 4 + 2] = s_st[tid * 4 + 3] = 0ull;
+        }
         for (int e = tid; e < nq * kT; e += kScanThreads) {
-            sh.alive[e] = (uint16_t)(e % kT);
+            sh.alive[e] = (uint8_t)(e % kT);
             sh.part[e] = 0.f;
         }
         __syncthreads();
@@ -391,28 +464,30 @@ __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, W
         const int64_t npad = ix.list_slot[l + 1] - slot_l;
         const int64_t ebase = slot_l * ix.Dpad;
         const int32_t slot0 = (int32_t)(slot_l + (int64_t)t * kT);
-        int64_t wstat[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
         bool ok;
         const bool exact_all = FULL || s_inf;
         if (exact_all) {
             // every candidate's exact distance through the staged pipeline
             ok = run_steps<float, NBLK, false>(ix.orig + ebase, npad, t, nt, nq, nsteps_full, ix.nb,
                                                ix.D, sh, ph, wv.qpad, ix.Dpad, nullptr, nullptr,
-                                               nullptr, wv.status, wstat, wv.staged_bytes);
+                                               nullptr, wv.status, wv.staged_bytes);
             if (!ok) break;
-            for (int g = warp; g < nq; g += kWarps) {
+            for (int p = warp; p < nq * ws; p += kWarps) {
+                const int g = p / ws;
                 const int q = s_q[g];
                 const float tau = s_tau[g];
-                for (int base = 0; base < nt; base += 32) {
+                const int be = pair_base(sh, p);
+                const int n = s_n[p];
+                for (int base = 0; base < n; base += 32) {
                     const int i = base + lane;
-                    const bool valid = i < nt;
-                    const float d = valid ? sh.part[g * kT + i] : 0.f;
-                    append(wv, w, q, valid && d <= tau, d, slot0 + i, lane);
+                    const bool valid = i < n;
+                    const float d = valid ? sh.part[be + i] : 0.f;
+                    const int c = valid ? sh.alive[be + i] : 0;
+                    append(wv, w, q, valid && d <= tau, d, slot0 + c, lane);
                 }
                 if (lane == 0) {
-                    wstat[g / kWarps][0] += nt;
-                    wstat[g / kWarps][2] += nt;
-                    wstat[g / kWarps][3] += (int64_t)nt * ix.D;
+                    s_st[p * 4 + 2] += (unsigned long long)n;
+                    s_st[p * 4 + 3] += (unsigned long long)n * ix.D;
                 }
             }
         } else {
@@ -420,114 +495,162 @@ __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, W
             ok = run_steps<E, NBLK, true>(slab, npad, t, nt, nq, S - 1, ix.nb, ix.D, sh, ph, wv.qrot,
                                           ix.Dpad, m1, beta,
                                           DT == DADE_SLAB_FP8E4M3 ? ix.scale : nullptr, wv.status,
-                                          wstat, wv.staged_bytes);
+                                          wv.staged_bytes);
             if (!ok) break;
-            for (int g = warp; g < nq; g += kWarps) {
+            // survivors: exact distance from the original vector, eseg lanes each
+            const int per = 32 / eseg;
+            for (int p = warp; p < nq * ws; p += kWarps) {
+                const int g = p / ws;
                 const int q = s_q[g];
                 const float tau = s_tau[g];
-                const int n = s_n[g];
+                const int n = s_n[p];
+                const int be = pair_base(sh, p);
                 const float* qp = wv.qpad + (int64_t)q * ix.Dpad;
-                for (int base = 0; base < n; base += 32) {
-                    const int i = base + lane;
+                for (int base = 0; base < n; base += per) {
+                    const int i = base + lane / eseg;
                     const bool valid = i < n;
-                    float d = 0.f;
-                    int c = 0;
-                    if (valid) {
-                        c = sh.alive[g * kT + i];
-                        d = exact_distance(ix.orig + ebase + ((int64_t)t * kT + c) * kBlock, npad, qp,
-                                           ix.nb);
-                    }
-                    append(wv, w, q, valid && d <= tau, d, slot0 + c, lane);
+                    const int c = valid ? sh.alive[be + i] : 0;
+                    const float d = exact_coop(ix.orig + ebase + ((int64_t)t * kT + c) * kBlock, npad, qp,
+                                               valid, ix.nb, lane, eseg);
+                    const bool lead = (lane & (eseg - 1)) == 0;
+                    append(wv, w, q, valid && lead && d <= tau, d, slot0 + c, lane);
                 }
                 if (lane == 0) {
-                    wstat[g / kWarps][0] += nt;
-                    wstat[g / kWarps][2] += n;
-                    wstat[g / kWarps][3] += (int64_t)n * ix.D;
+                    s_st[p * 4 + 2] += (unsigned long long)n;
+                    s_st[p * 4 + 3] += (unsigned long long)n * ix.D;
                     if (wv.staged_bytes && n)
                         atomicAdd(wv.staged_bytes, (unsigned long long)n * ix.nb * kBlock * sizeof(float));
                 }
             }
         }
-        if (wv.stats && lane == 0) {
-            for (int g = warp, j = 0; g < nq; g += kWarps, ++j)
-                for (int f = 0; f < 4; ++f)
-                    if (wstat[j][f]) atomicAdd((unsigned long long*)&wv.stats[(int64_t)s_q[g] * 4 + f],
-                                               (unsigned long long)wstat[j][f]);
+        __syncthreads();
+        if (wv.stats && tid < nq * ws * 4) {
+            const int p = tid / 4, f = tid % 4;
+            if (s_st[tid]) atomicAdd((unsigned long long*)&wv.stats[(int64_t)s_q[p / ws] * 4 + f], s_st[tid]);
         }
         __syncthreads();
     }
 }
 
 // ------------------------------------------------------------ merge
-__device__ __forceinline__ bool pair_less(float da, int64_t ia, float db, int64_t ib) {
+// One warp per query: the wave's candidates are sorted in chunks of
+// kMergeChunk (warp bitonic sort in shared memory) and merged with the sorted
+// top-K by rank: an element's place is its index plus the number of elements
+// of the other list that precede it in (distance, id) order.
+constexpr int kMergeWarps = 8;
+constexpr int kMergeChunk = 256;
+
+__device__ __forceinline__ bool pair_less(float da, long long ia, float db, long long ib) {
     return da < db || (da == db && ia < ib);
 }
 
-__global__ void __launch_bounds__(256) merge_kernel(IndexView ix, WaveView wv, int w) {
-    __shared__ float sd[kMergeCap];
-    __shared__ int64_t sid[kMergeCap];
-    const int q = blockIdx.x, tid = threadIdx.x;
+// number of entries of the sorted list (d, id)[0, n) that precede (x, xi)
+__device__ __forceinline__ int count_before(const float* d, const long long* id, int n, float x, long long xi) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (pair_less(d[mid], id[mid], x, xi)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(IndexView ix, WaveView wv, int w) {
+    extern __shared__ __align__(16) unsigned char msmem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * kMergeWarps + warp;
+    if (q >= wv.B) return;
+    const int cap_k = wv.Kmax;
+    const int region = 2 * cap_k + kMergeChunk;  // top list, chunk, output
+    float* rd = reinterpret_cast<float*>(msmem) + (size_t)warp * region;
+    long long* ri = reinterpret_cast<long long*>(msmem + sizeof(float) * (size_t)kMergeWarps * region) +
+                    (size_t)warp * region;
+    float* ad = rd;
+    long long* ai = ri;
+    float* bd = rd + cap_k;
+    long long* bi = ri + cap_k;
+    float* od = rd + cap_k + kMergeChunk;
+    long long* oi = ri + cap_k + kMergeChunk;
+
     const int64_t* co = wv.cand_off + (int64_t)w * (wv.B + 1);
     const int64_t off = co[q], cap = co[q + 1] - off;
     const int cnt = (int)((int64_t)wv.cand_cnt[q] < cap ? (int64_t)wv.cand_cnt[q] : cap);
     const int K = wv.K[q];
     if (cnt == 0 || K < 1 || K > wv.Kmax) {
-        __syncthreads();
-        if (tid == 0) wv.cand_cnt[q] = 0;
+        if (lane == 0) wv.cand_cnt[q] = 0;
         return;
     }
+    float* td = wv.top_d + q * wv.Kmax;
+    int64_t* ti = wv.top_id + q * wv.Kmax;
     int cur = wv.top_n[q];
-    float* td = wv.top_d + (int64_t)q * wv.Kmax;
-    int64_t* ti = wv.top_id + (int64_t)q * wv.Kmax;
-    for (int i = tid; i < cur; i += 256) {
-        sd[i] = td[i];
-        sid[i] = ti[i];
+    for (int i = lane; i < cur; i += 32) {
+        ad[i] = td[i];
+        ai[i] = ti[i];
     }
-    int done = 0;
-    while (done < cnt) {
-        const int chunk = min(cnt - done, kMergeCap - cur);
-        for (int i = tid; i < chunk; i += 256) {
-            sd[cur + i] = wv.cand_d[off + done + i];
-            sid[cur + i] = ix.ids[wv.cand_pos[off + done + i]];
-        }
+    for (int done = 0; done < cnt; done += kMergeChunk) {
+        const int m = min(kMergeChunk, cnt - done);
         int M = 1;
-        while (M < cur + chunk) M <<= 1;
-        for (int i = cur + chunk + tid; i < M; i += 256) {
-            sd[i] = INFINITY;
-            sid[i] = INT64_MAX;
+        while (M < m) M <<= 1;
+        for (int i = lane; i < M; i += 32) {
+            if (i < m) {
+                bd[i] = wv.cand_d[off + done + i];
+                bi[i] = ix.ids[wv.cand_pos[off + done + i]];
+            } else {
+                bd[i] = INFINITY;
+                bi[i] = LLONG_MAX;
+            }
         }
-        __syncthreads();
+        __syncwarp();
         for (int size = 2; size <= M; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < M; i += 256) {
-                    int j = i ^ stride;
+                for (int i = lane; i < M; i += 32) {
+                    const int j = i ^ stride;
                     if (j > i) {
-                        bool up = (i & size) == 0;
-                        bool sw = up ? pair_less(sd[j], sid[j], sd[i], sid[i])
-                                     : pair_less(sd[i], sid[i], sd[j], sid[j]);
+                        const bool up = (i & size) == 0;
+                        const bool sw = up ? pair_less(bd[j], bi[j], bd[i], bi[i])
+                                           : pair_less(bd[i], bi[i], bd[j], bi[j]);
                         if (sw) {
-                            float a = sd[i];
-                            sd[i] = sd[j];
-                            sd[j] = a;
-                            int64_t b = sid[i];
-                            sid[i] = sid[j];
-                            sid[j] = b;
+                            float x = bd[i];
+                            bd[i] = bd[j];
+                            bd[j] = x;
+                            long long y = bi[i];
+                            bi[i] = bi[j];
+                            bi[j] = y;
                         }
                     }
                 }
-                __syncthreads();
+                __syncwarp();
             }
         }
-        cur = min(K, cur + chunk);
-        done += chunk;
+        const int nout = min(K, cur + m);
+        for (int i = lane; i < cur; i += 32) {
+            const int r = i + count_before(bd, bi, m, ad[i], ai[i]);
+            if (r < nout) {
+                od[r] = ad[i];
+                oi[r] = ai[i];
+            }
+        }
+        for (int i = lane; i < m; i += 32) {
+            const int r = i + count_before(ad, ai, cur, bd[i], bi[i]);
+            if (r < nout) {
+                od[r] = bd[i];
+                oi[r] = bi[i];
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < nout; i += 32) {
+            ad[i] = od[i];
+            ai[i] = oi[i];
+        }
+        __syncwarp();
+        cur = nout;
     }
-    for (int i = tid; i < cur; i += 256) {
-        td[i] = sd[i];
-        ti[i] = sid[i];
+    for (int i = lane; i < cur; i += 32) {
+        td[i] = ad[i];
+        ti[i] = ai[i];
     }
-    if (tid == 0) {
+    if (lane == 0) {
         wv.top_n[q] = cur;
-        wv.tau[q] = cur == K ? sd[K - 1] : INFINITY;
+        wv.tau[q] = cur == K ? ad[K - 1] : INFINITY;
         wv.cand_cnt[q] = 0;
     }
 }
@@ -762,8 +885,7 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
 template <int DT, int NBLK, bool FULL>
 cudaError_t launch_scan_t(const IndexView& ix, const WaveView& wv, int w, const float* m1,
                           const float* beta, int S, cudaStream_t st) {
-    constexpr int BUF = NBLK * kT * kBlock * 4;
-    constexpr int SMEM = 2 * BUF + kG * kT * (int)(sizeof(uint16_t) + sizeof(float));
+    constexpr int SMEM = scan_smem_bytes<NBLK>();
     static int grid = 0;
     auto kern = wave_scan_kernel<DT, NBLK, FULL>;
     if (grid == 0) {
@@ -832,7 +954,14 @@ cudaError_t launch_wave_scan(const IndexView& ix, const WaveView& wv, int w, boo
 
 cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStream_t st) {
     if (wv.B == 0) return cudaSuccess;
-    merge_kernel<<<(unsigned)wv.B, 256, 0, st>>>(ix, wv, w);
+    const int smem = kMergeWarps * (2 * wv.Kmax + kMergeChunk) * (int)(sizeof(float) + sizeof(long long));
+    static int configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    merge_kernel<<<(unsigned)ceil_div(wv.B, kMergeWarps), kMergeWarps * 32, smem, st>>>(ix, wv, w);
     return cudaGetLastError();
 }
 

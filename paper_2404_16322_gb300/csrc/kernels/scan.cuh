@@ -9,7 +9,6 @@ namespace dade {
 constexpr int kG = 16;             // queries per work unit
 constexpr int kT = 256;            // candidates per tile of a bucket
 constexpr int kScanThreads = 256;  // 8 warps, each owns kG / 8 queries
-constexpr int kMergeCap = 4096;    // (distance, id) pairs sorted at once by the merge
 
 struct IndexView {
     const void* slab;          // rotated vectors, blocked, slab dtype
