@@ -207,6 +207,34 @@ dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,
                         const dade_search_opts* opts, int64_t* ids_dev, float* dists_dev,
                         const int64_t* out_offsets_dev, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * dade_search_noalloc -- dade_search for callers that cannot allocate.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory at search time, such as an application whose
+ * own allocator has reserved all of the GPU's memory, or a latency-critical
+ * path that cannot afford the implicit synchronisation of cudaMalloc.  It
+ * runs the same kernels as dade_search, with the same arguments and results,
+ * but its scratch is a fixed 64 MiB device array compiled into the library
+ * (every GPU that loads the library holds it until the process exits); the
+ * call itself performs no cudaMalloc, cudaFree or other allocation.
+ *  - opts->workspace must be NULL; a search whose scratch would exceed
+ *    64 MiB (dade_search_workspace_size) is rejected with DADE_EINVAL and a
+ *    message, before any work is enqueued (e.g. 256 queries of K 100 and
+ *    nprobe 64 fit on a 1M-vector index with 4096 buckets).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) once for that device; make that first call
+ *    before any stream capture.
+ *  - Every call uses the same array, which keeps the previous call's
+ *    contents; each call clears what must start at zero.  Calls whose work
+ *    overlaps on the GPU race on the array: serialise them (one stream, or
+ *    events between streams).
+ * ---------------------------------------------------------------------- */
+dade_status dade_search_noalloc(const dade_index* idx, const float* Q_dev, int64_t B,
+                                const int32_t* K_dev, const int32_t* nprobe_dev, int32_t delta_d,
+                                const dade_search_opts* opts, int64_t* ids_dev, float* dists_dev,
+                                const int64_t* out_offsets_dev, void* cuda_stream);
+
 /* Device scratch bytes dade_search needs for B queries with these bounds
  * (the same opts fields as dade_search reads).  0 on invalid arguments. */
 size_t dade_search_workspace_size(const dade_index* idx, int64_t B, int32_t delta_d,

@@ -15,7 +15,8 @@ import numpy as np
 from . import _lib as L
 
 __all__ = ["dade_train_rotation", "ivf_build", "dade_fit_correction", "dade_fit_samples",
-           "dade_set_correction", "dade_get_correction", "dade_search", "dade_search_workspace_size",
+           "dade_set_correction", "dade_get_correction", "dade_search", "dade_search_noalloc",
+           "dade_search_workspace_size",
            "dade_index_info_get", "dade_index_centroids", "dade_index_assignment",
            "dade_index_list_sizes", "dade_index_save", "dade_index_load", "dade_index_free",
            "dade_stage_timing", "dade_stage_timing_read", "dade_last_error", "Index", "library",
@@ -187,6 +188,21 @@ def dade_search(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: in
     _check(library().dade_search(idx.ptr, _ptr(Q), int(Q.shape[0]), _ptr(K), _ptr(nprobe), int(delta_d),
                                  ctypes.byref(o), _ptr(ids), _ptr(dists), _ptr(offsets),
                                  ctypes.c_void_p(s.cuda_stream)))
+
+
+def dade_search_noalloc(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: int,
+                        max_nprobe: int, mode: str = "prune", first_wave: int = 0, tau=None,
+                        probe_in=None, probe_out=None, qrot_out=None, stats=None, status=None,
+                        offsets=None, stream=None) -> None:
+    """dade_search whose scratch is the library's fixed device array: for
+    callers that cannot allocate device memory.  Same arguments and results
+    as dade_search except that no workspace is passed."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    o = _opts(mode, max_K, max_nprobe, first_wave, tau, probe_in, probe_out, qrot_out, stats, status, None)
+    _check(library().dade_search_noalloc(idx.ptr, _ptr(Q), int(Q.shape[0]), _ptr(K), _ptr(nprobe),
+                                         int(delta_d), ctypes.byref(o), _ptr(ids), _ptr(dists), _ptr(offsets),
+                                         ctypes.c_void_p(s.cuda_stream)))
 
 
 def dade_index_info_get(idx: Index) -> dict:

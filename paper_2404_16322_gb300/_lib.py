@@ -50,6 +50,8 @@ SIGNATURES = {
     "dade_get_correction": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),
     "dade_search": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i32, ctypes.POINTER(SearchOpts),
                                    c_vp, c_vp, c_vp, c_vp]),
+    "dade_search_noalloc": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i32, ctypes.POINTER(SearchOpts),
+                                           c_vp, c_vp, c_vp, c_vp]),
     "dade_search_workspace_size": (c_sz, [c_vp, c_i64, c_i32, ctypes.POINTER(SearchOpts)]),
     "dade_index_info_get": (ctypes.c_int, [c_vp, ctypes.POINTER(IndexInfo)]),
     "dade_index_centroids": (ctypes.c_int, [c_vp, c_vp]),
