@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 TARGET_RECALL = 0.95
 NPROBES = [8, 16, 24, 32, 48, 64, 96, 128, 192, 256]
 DELTAS = [8, 16, 32]
+FIRST_WAVES = [1, 4]
 METRIC = "QPS at recall@10>=0.95 (estimate-and-prune IVF search, SIFT-shaped 1M x 128, nlist 4096, K 100)"
 
 
@@ -49,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-queries", type=int, default=400)
     ap.add_argument("--profile", default=None,
-                    help="NPROBE,DELTA_D: skip the sweep and baselines; run W + K steps of that "
+                    help="NPROBE,DELTA_D[,FIRST_WAVE]: skip the sweep and baselines; run W + K steps of that "
                          "configuration inside the NVTX range 'dade_timed' (for ncu captures)")
     return ap.parse_args()
 
@@ -161,12 +162,12 @@ class Runner:
         self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
         self.max_nprobe = max_nprobe
 
-    def run(self, nprobe, delta_d, mode, stats=False):
+    def run(self, nprobe, delta_d, mode, stats=False, first_wave=1):
         self.np.fill_(nprobe)
         if stats:
             self.stats.zero_()
         self.G.dade_search(self.idx, self.q, self.k, self.np, delta_d, self.ids, self.d, max_K=self.K,
-                           max_nprobe=nprobe, mode=mode, status=self.status,
+                           max_nprobe=nprobe, mode=mode, status=self.status, first_wave=first_wave,
                            stats=self.stats if stats else None, workspace=self.ws)
 
     def result(self):
@@ -174,10 +175,10 @@ class Runner:
         assert int(self.status.item()) == 0, f"device status {int(self.status.item())}"
         return self.ids.view(self.B, self.K).cpu().numpy()
 
-    def time(self, nprobe, delta_d, mode, steps, warmup):
+    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1):
         torch = self.torch
         for _ in range(warmup):
-            self.run(nprobe, delta_d, mode)
+            self.run(nprobe, delta_d, mode, first_wave=first_wave)
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         t0 = torch.cuda.Event(enable_timing=True)
@@ -185,7 +186,7 @@ class Runner:
         t0.record()
         for e0, e1 in evs:
             e0.record()
-            self.run(nprobe, delta_d, mode)
+            self.run(nprobe, delta_d, mode, first_wave=first_wave)
             e1.record()
         t1.record()
         torch.cuda.synchronize()
@@ -332,30 +333,34 @@ def main():
     maxp = min(max(NPROBES), nlist)
     run = Runner(G, idx, Q, K, maxp)
     if args.profile:
-        npb, dd = (int(x) for x in args.profile.split(","))
+        vals = [int(x) for x in args.profile.split(",")]
+        npb, dd = vals[0], vals[1]
+        fw = vals[2] if len(vals) > 2 else 1
         for _ in range(args.warmup):
-            run.run(npb, dd, "prune")
+            run.run(npb, dd, "prune", first_wave=fw)
         run.result()
         torch.cuda.nvtx.range_push("dade_timed")
         for _ in range(args.steps):
-            run.run(npb, dd, "prune")
+            run.run(npb, dd, "prune", first_wave=fw)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         ids = run.result()
         print(json.dumps({"profile": args.profile, "recall@10": recall_at(ids, gt), "steps": args.steps,
-                          "launches_per_step": 11 + 2 * n_waves(npb), "setup_s": time.perf_counter() - t_setup}))
+                          "launches_per_step": 12 + 2 * n_waves(npb, fw), "setup_s": time.perf_counter() - t_setup}))
         return
     # --- sweep: recall per (mode, delta_d, nprobe); short timing of each
     sweep = []
     for mode, dds in (("full", [0]), ("prune", DELTAS)):
         for dd in dds:
-            for npb in [p for p in NPROBES if p <= maxp]:
-                run.run(npb, dd, mode)
-                rec = recall_at(run.result(), gt)
-                total, per = run.time(npb, dd, mode, 5, 2)
-                sweep.append(dict(mode=mode, delta_d=dd, nprobe=npb, recall=rec, ms=float(np.median(per))))
-                if rec >= TARGET_RECALL + 0.02:
-                    break
+            for fw in FIRST_WAVES:
+                for npb in [p for p in NPROBES if p <= maxp]:
+                    run.run(npb, dd, mode, first_wave=fw)
+                    rec = recall_at(run.result(), gt)
+                    total, per = run.time(npb, dd, mode, 5, 2, first_wave=fw)
+                    sweep.append(dict(mode=mode, delta_d=dd, first_wave=fw, nprobe=npb, recall=rec,
+                                      ms=float(np.median(per))))
+                    if rec >= TARGET_RECALL + 0.02:
+                        break
 
     def best(mode):
         ok = [s for s in sweep if s["mode"] == mode and s["recall"] >= TARGET_RECALL]
@@ -370,12 +375,12 @@ def main():
         dist.barrier()
     sampler = ClockSampler(local)
     for _ in range(args.warmup):
-        run.run(bd["nprobe"], bd["delta_d"], "prune")
+        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"])
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms, per = run.time(bd["nprobe"], bd["delta_d"], "prune", args.steps, 0)
+    total_ms, per = run.time(bd["nprobe"], bd["delta_d"], "prune", args.steps, 0, first_wave=bd["first_wave"])
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:
@@ -386,14 +391,14 @@ def main():
     value = world * run.B / (ms_step / 1000.0)
 
     # --- full-scan reference point on the same GPU, same timing
-    f_total, f_per = run.time(bf["nprobe"], 0, "full", args.steps, args.warmup)
+    f_total, f_per = run.time(bf["nprobe"], 0, "full", args.steps, args.warmup, first_wave=bf["first_wave"])
     full_qps = run.B / (f_total / args.steps / 1000.0)
 
     # --- stage timing of the dominant kernel (the refinement scan)
     G.dade_stage_timing(True)
     G.dade_stage_timing_read()
     for _ in range(args.steps):
-        run.run(bd["nprobe"], bd["delta_d"], "prune")
+        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"])
     scan_ms, scan_launches, scan_bytes = G.dade_stage_timing_read()
     G.dade_stage_timing(False)
     per_launch_ms = scan_ms / max(1, scan_launches)
@@ -404,13 +409,13 @@ def main():
     traffic = traffic_from_profiles(khash)
 
     # --- work accounting (bytes per query) for both modes
-    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True)
+    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True, first_wave=bd["first_wave"])
     run.result()
     st = run.stats.cpu().numpy()
     S = G.n_steps(128, bd["delta_d"])
     pruned_dims = st[:, 3] - st[:, 2] * 128
     dade_bytes = (pruned_dims * 4 + st[:, 2] * ((S - 1) * bd["delta_d"] * 4 + 128 * 4)).sum() / run.B
-    run.run(bf["nprobe"], 0, "full", stats=True)
+    run.run(bf["nprobe"], 0, "full", stats=True, first_wave=bf["first_wave"])
     run.result()
     stf = run.stats.cpu().numpy()
     full_bytes = (stf[:, 0] * 128 * 4).sum() / run.B
@@ -428,7 +433,8 @@ def main():
         run.k.copy_(k_h, non_blocking=True)
         run.np.copy_(n_h, non_blocking=True)
         G.dade_search(idx, run.q, run.k, run.np, bd["delta_d"], run.ids, run.d, max_K=K,
-                      max_nprobe=bd["nprobe"], status=run.status, workspace=run.ws)
+                      max_nprobe=bd["nprobe"], status=run.status, workspace=run.ws,
+                      first_wave=bd["first_wave"])
         ids_h.copy_(run.ids, non_blocking=True)
         d_h.copy_(run.d, non_blocking=True)
 
@@ -451,14 +457,15 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K, args.cpu_sample_queries)
 
-    launches = 11 + 2 * n_waves(bd["nprobe"])
+    launches = 12 + 2 * n_waves(bd["nprobe"], bd["first_wave"])
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"sift1m-shaped: N={len(X)}, D=128 integer [0,255], 256-comp mixture lambda~i^-0.8; "
                                f"B={run.B} queries; nlist={nlist}, K={K}",
-                   "nprobe": bd["nprobe"], "delta_d": bd["delta_d"], "slabs": "f32", "recall@10": bd["recall"],
+                   "nprobe": bd["nprobe"], "delta_d": bd["delta_d"], "first_wave": bd["first_wave"],
+                   "slabs": "f32", "recall@10": bd["recall"],
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (index 1.0 GB > 129 MB L2)"},
         "full_scan": {"value": full_qps, "unit": "queries/s", "nprobe": bf["nprobe"], "recall@10": bf["recall"]},
         "speedup_vs_full_scan": value / world / full_qps,

@@ -160,51 +160,20 @@ __device__ float exact_distance(const float* xo, int64_t npad, const float* qp, 
 }
 
 // ------------------------------------------------------------ unit decode
+// A work unit is (bucket l, tile t of up to kT candidates, group of up to kG
+// queries probing l in the wave); its descriptor is built by expand_units.
 struct Unit {
     int l, t, nq, nt, item;
 };
 
-__device__ __forceinline__ Unit decode_unit(const IndexView& ix, const WaveView& wv, int w, int u) {
-    const int32_t* uo = wv.unit_off + (int64_t)w * (ix.nlist + 1);
-    int lo = 0, hi = ix.nlist;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (uo[mid] <= u) lo = mid; else hi = mid;
-    }
+__device__ __forceinline__ Unit unpack_unit(int4 d) {
     Unit r;
-    r.l = lo;
-    int local = u - uo[lo];
-    int nl = ix.list_size[lo];
-    int ntile = (nl + kT - 1) / kT;
-    int g = local / ntile;
-    r.t = local - g * ntile;
-    int key = w * ix.nlist + lo;
-    int cnt = wv.cnt_wl[key];
-    r.nq = min(kG, cnt - g * kG);
-    r.nt = min(kT, nl - r.t * kT);
-    r.item = wv.off_wl[key] + g * kG;
+    r.l = d.x;
+    r.t = d.y;
+    r.item = d.z;
+    r.nq = d.w >> 16;
+    r.nt = d.w & 0xffff;
     return r;
-}
-
-// Append (d, slot) to query q's candidate buffer of wave w when app is set.
-__device__ __forceinline__ void append(const WaveView& wv, int w, int q, bool app, float d,
-                                       int32_t slot, int lane) {
-    unsigned bal = __ballot_sync(0xffffffffu, app);
-    if (!bal) return;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&wv.cand_cnt[q], __popc(bal));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (app) {
-        const int64_t* co = wv.cand_off + (int64_t)w * (wv.B + 1);
-        int64_t off = co[q], cap = co[q + 1] - off;
-        int s = base + __popc(bal & lanemask_lt());
-        if (s < cap) {
-            wv.cand_d[off + s] = d;
-            wv.cand_pos[off + s] = slot;
-        } else {
-            atomicCAS(wv.status, 0, (int)DADE_EINVAL);
-        }
-    }
 }
 
 // ------------------------------------------------------------ exact distance
@@ -239,44 +208,43 @@ __device__ __forceinline__ float exact_coop(const float* xo, int64_t npad, const
 }
 
 // ------------------------------------------------------------ step pipeline
-// A unit's live candidates are kept per (query, segment) pair: when the unit
-// has fewer queries than warps, ws = kWarps / nq (a power of two) warps share
-// a query, each owning the fixed segment [j * kT / ws, (j + 1) * kT / ws) of
-// the tile with its own compacted list, so every warp has work.  Pair
-// p = g * ws + j; warp w handles pairs w, w + kWarps, ...  (nq * ws <= kG).
-constexpr int kQs = 4 * kBlock;  // widest step (Delta_d = 32) in floats
+// A unit's (query, candidate) pairs are split over the warps in one flat list
+// per warp: pair e = g * nt + c (query g of the unit, candidate c of the tile)
+// belongs to the 32-pair chunk e / 32, and chunk h goes to warp h % kWarps.
+// Each warp compacts its own list after every test, so its 32-lane chunks
+// stay full whichever queries the live pairs belong to; interleaving whole
+// chunks keeps the warps' lists about equally long while the lanes of a
+// chunk read consecutive candidates (no shared-memory bank conflicts).  A
+// pair is stored as the key g << 8 | c (kT = 256) and its partial distance.
+constexpr int kQs = 4 * kBlock;     // widest step (Delta_d = 32) in floats
+constexpr int kQsPad = kQs + 4;     // query rows 16 B apart in bank terms
+constexpr int kWarpCap = kG * kT / kWarps;
 
 struct StepShared {
     unsigned char* buf0;        // two slab buffers at buf0 and buf0 + buf_bytes
     int buf_bytes;
     uint64_t* bar;
-    uint8_t* alive;             // kG x kT candidate indices (compacted per pair)
-    float* part;                // kG x kT partial distances
-    int* n;                     // live count per pair
-    unsigned long long* st;     // per pair: candidates, pruned, exact, dims
-    float* qs;                  // kG x kQs: the step's query values
+    uint16_t* key;              // kWarps x kWarpCap pair keys
+    float* part;                // kWarps x kWarpCap partial distances
+    int* n;                     // live pairs per warp
+    unsigned long long* st;     // per query: candidates, pruned, exact, dims
+    float* qs;                  // kG x kQsPad: the step's query values
     float* sc;                  // kQs: the step's FP8 scales
     const int* q;               // kG query ids
     const float* tau;           // kG
-    int ws;                     // warps (segments) per query
 };
-
-__device__ __forceinline__ int pair_base(const StepShared& sh, int p) {
-    const int g = p / sh.ws, j = p - g * sh.ws;
-    return g * kT + j * (kT / sh.ws);
-}
 
 // Runs `nsteps` slab steps over the tile: slab k covers blocks
 // [k*NBLK, min((k+1)*NBLK, nb)) of the source (rotated slabs in PRUNE mode,
 // original vectors otherwise).  PRUNE tests after each slab and compacts;
-// otherwise every candidate accumulates every slab.  Queries whose tau is
-// +inf are skipped in PRUNE mode (they cannot be pruned).  Returns false if
-// a bounded wait gave up.
+// otherwise every pair accumulates every slab.  A pair whose query has
+// tau = +inf is never pruned.  Returns false if a bounded wait gave up.
 template <class E, int NBLK, bool PRUNE>
-__device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int nt, int nq, int nsteps, int nb,
-                          int D, const StepShared& sh, uint32_t& phase_bits, const float* qsrc, int Dpad,
-                          const float* m1, const float* beta, const float* scale,
-                          int32_t* status, unsigned long long* staged) {
+__device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int nt, int nq, int nsteps,
+                                          int nb, int D, const StepShared& sh, uint32_t& phase_bits,
+                                          const float* qsrc, int Dpad, const float* m1,
+                                          const float* beta, const float* scale, int32_t* status,
+                                          unsigned long long* staged, bool want_stats) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt_copy = (nt + 31) & ~31;
     const uint32_t blk_bytes = (uint32_t)nt_copy * kBlock * sizeof(E);
@@ -296,12 +264,14 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
     if (tid == 0) issue(0);
     int k = 0;
     bool pending_next = false;
+    uint16_t* key = sh.key + warp * kWarpCap;
+    float* part = sh.part + warp * kWarpCap;
     for (; k < nsteps; ++k) {
         const int b0 = k * NBLK, nbk = min(NBLK, nb - b0), w8 = nbk * kBlock;
         // the step's query values (and FP8 scales) for every query of the unit
         for (int e = tid; e < nq * kQs; e += kScanThreads) {
             const int g = e / kQs, j = e - g * kQs;
-            sh.qs[e] = j < w8 ? qsrc[(int64_t)sh.q[g] * Dpad + b0 * kBlock + j] : 0.f;
+            sh.qs[g * kQsPad + j] = j < w8 ? qsrc[(int64_t)sh.q[g] * Dpad + b0 * kBlock + j] : 0.f;
         }
         if (scale && tid < kQs) sh.sc[tid] = tid < w8 ? scale[b0 * kBlock + tid] : 0.f;
         bool got = mbar_wait(sh.bar + (k & 1), (phase_bits >> (k & 1)) & 1u, status);
@@ -311,58 +281,50 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
         if (tid == 0 && pending_next) issue(k + 1);
         const E* bk = reinterpret_cast<const E*>(sh.buf0 + (k & 1) * sh.buf_bytes);
         const int dims_k = min((k + 1) * NBLK * kBlock, D);
-        for (int p = warp; p < nq * sh.ws; p += kWarps) {
-            const int g = p / sh.ws;
-            const int base_e = pair_base(sh, p);
-            const float tau = sh.tau[g];
-            if (PRUNE && isinf(tau)) continue;
-            const float* qg = sh.qs + g * kQs;
-            const float mm = PRUNE ? m1[k] : 0.f, bt = PRUNE ? beta[k] : 0.f;
-            const int n = sh.n[p];
-            int out = 0;
-            int pruned = 0;
-            for (int base = 0; base < n; base += 32) {
-                const int i = base + lane;
-                const bool valid = i < n;
-                int c = 0;
-                float pd = 0.f;
-                if (valid) {
-                    c = sh.alive[base_e + i];
-                    pd = sh.part[base_e + i];
+        const float mm = PRUNE ? m1[k] : 0.f, bt = PRUNE ? beta[k] : 0.f;
+        const int n = sh.n[warp];
+        int out = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + lane;
+            const bool valid = i < n;
+            int kk = 0, g = 0;
+            float pd = 0.f;
+            if (valid) {
+                kk = key[i];
+                g = kk >> 8;
+                const int c = kk & 255;
+                pd = part[i];
+                const float* qg = sh.qs + g * kQsPad;
 #pragma unroll
-                    for (int bb = 0; bb < NBLK; ++bb) {
-                        if (bb < nbk) {
-                            float x[8], qv[8];
-                            load8(bk + ((size_t)bb * kT + c) * kBlock, sh.sc + bb * kBlock, x);
-                            load8(qg + bb * kBlock, nullptr, qv);
-                            pd += block_sq(qv, x);
-                        }
+                for (int bb = 0; bb < NBLK; ++bb) {
+                    if (bb < nbk) {
+                        float x[8], qv[8];
+                        load8(bk + ((size_t)bb * kT + c) * kBlock, sh.sc + bb * kBlock, x);
+                        load8(qg + bb * kBlock, nullptr, qv);
+                        pd += block_sq(qv, x);
                     }
                 }
-                const bool keep = valid && !(PRUNE && fmaf(mm, pd, bt) > tau);
-                const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                __syncwarp();
-                if (keep) {
-                    const int pos = out + __popc(bal & lanemask_lt());
-                    sh.alive[base_e + pos] = (uint8_t)c;
-                    sh.part[base_e + pos] = pd;
-                }
-                out += __popc(bal);
-                if (PRUNE) pruned += __popc(__ballot_sync(0xffffffffu, valid && !keep));
             }
+            const bool keep = valid && !(PRUNE && fmaf(mm, pd, bt) > sh.tau[g]);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
             __syncwarp();
-            if (lane == 0) {
-                sh.n[p] = out;
-                if (PRUNE) {
-                    sh.st[p * 4 + 1] += (unsigned long long)pruned;
-                    sh.st[p * 4 + 3] += (unsigned long long)pruned * dims_k;
-                }
+            if (keep) {
+                const int pos = out + __popc(bal & lanemask_lt());
+                key[pos] = (uint16_t)kk;
+                part[pos] = pd;
+            }
+            out += __popc(bal);
+            if (PRUNE && want_stats && valid && !keep) {
+                atomicAdd(&sh.st[g * 4 + 1], 1ull);
+                atomicAdd(&sh.st[g * 4 + 3], (unsigned long long)dims_k);
             }
         }
+        __syncwarp();
+        if (lane == 0) sh.n[warp] = out;
         __syncthreads();
         if (PRUNE) {
             int live = 0;
-            for (int p = 0; p < nq * sh.ws; ++p) live |= (!isinf(sh.tau[p / sh.ws]) && sh.n[p] > 0);
+            for (int w = 0; w < kWarps; ++w) live |= sh.n[w];
             if (!live) break;
         }
     }
@@ -376,10 +338,32 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
     return true;
 }
 
+// Append (d, slot) to query q's candidate buffer for every lane with app set;
+// lanes of the same query share one atomic.
+__device__ __forceinline__ void append_any(const WaveView& wv, int w, int q, bool app, float d,
+                                           int32_t slot, int lane) {
+    if (!__ballot_sync(0xffffffffu, app)) return;
+    const unsigned peers = __match_any_sync(0xffffffffu, app ? q : -1);
+    if (!app) return;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&wv.cand_cnt[q], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int64_t* co = wv.cand_off + (int64_t)w * (wv.B + 1);
+    const int64_t off = co[q], cap = co[q + 1] - off;
+    const int s = base + __popc(peers & lanemask_lt());
+    if (s < cap) {
+        wv.cand_d[off + s] = d;
+        wv.cand_pos[off + s] = slot;
+    } else {
+        atomicCAS(wv.status, 0, (int)DADE_EINVAL);
+    }
+}
+
 // ------------------------------------------------------------ wave scan
 template <int NBLK>
 constexpr int scan_smem_bytes() {
-    return 2 * NBLK * kT * kBlock * 4 + kG * kT * (int)(sizeof(uint8_t) + sizeof(float));
+    return 2 * NBLK * kT * kBlock * 4 + kWarps * kWarpCap * (int)(sizeof(uint16_t) + sizeof(float));
 }
 
 template <int DT, int NBLK, bool FULL>
@@ -391,19 +375,20 @@ __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, W
     constexpr int BUF = NBLK * kT * kBlock * 4;  // sized for FP32 (original vectors)
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_unit, s_l, s_t, s_nq, s_nt, s_inf;
-    __shared__ int s_q[kG], s_n[kG];  // s_n per (query, segment) pair
+    __shared__ int s_unit;
+    __shared__ int4 s_desc;
+    __shared__ int s_q[kG], s_n[kWarps];
     __shared__ float s_tau[kG];
     __shared__ unsigned long long s_st[kG * 4];
-    __shared__ __align__(16) float s_qs[kG * kQs];
+    __shared__ __align__(16) float s_qs[kG * kQsPad];
     __shared__ __align__(16) float s_sc[kQs];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     StepShared sh;
     sh.buf0 = smem;
     sh.buf_bytes = BUF;
-    sh.alive = reinterpret_cast<uint8_t*>(smem + 2 * BUF);
-    sh.part = reinterpret_cast<float*>(smem + 2 * BUF + kG * kT * sizeof(uint8_t));
+    sh.key = reinterpret_cast<uint16_t*>(smem + 2 * BUF);
+    sh.part = reinterpret_cast<float*>(smem + 2 * BUF + kWarps * kWarpCap * sizeof(uint16_t));
     sh.bar = bar;
     sh.n = s_n;
     sh.st = s_st;
@@ -419,75 +404,79 @@ __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, W
     __syncthreads();
     uint32_t ph = 0u;
     const int total = wv.unit_off[(int64_t)w * (ix.nlist + 1) + ix.nlist];
+    const int4* units = wv.units + wv.ubase[w];
     const int nsteps_full = (ix.nb + NBLK - 1) / NBLK;
     const int eseg = seg_lanes(ix.nb);
+    const bool want_stats = wv.stats != nullptr;
+    // thread 0 claims the next unit and loads its descriptor one unit ahead
+    int next_u = 0;
+    int4 next_d = make_int4(0, 0, 0, 0);
+    if (tid == 0) {
+        next_u = atomicAdd(&wv.work[w], 1);
+        if (next_u < total) next_d = units[next_u];
+    }
 
     for (;;) {
-        if (tid == 0) s_unit = atomicAdd(&wv.work[w], 1);
-        __syncthreads();
-        const int u = s_unit;
-        if (u >= total) break;
         if (tid == 0) {
-            Unit un = decode_unit(ix, wv, w, u);
-            s_l = un.l;
-            s_t = un.t;
-            s_nq = un.nq;
-            s_nt = un.nt;
-            int all_inf = 1;
-            for (int g = 0; g < un.nq; ++g) {
-                int q = wv.items[un.item + g];
-                s_q[g] = q;
-                s_tau[g] = wv.tau[q];
-                all_inf &= isinf(s_tau[g]) ? 1 : 0;
+            s_unit = next_u;
+            s_desc = next_d;
+            if (next_u < total) {
+                next_u = atomicAdd(&wv.work[w], 1);
+                if (next_u < total) next_d = units[next_u];
             }
-            s_inf = all_inf;
         }
         __syncthreads();
-        const int l = s_l, t = s_t, nq = s_nq, nt = s_nt;
-        int ws = 1;
-        while (ws * 2 * nq <= kWarps) ws *= 2;
-        sh.ws = ws;
-        const int seg = kT / ws;
-        if (tid < nq * ws) {
-            const int j = tid % ws;
-            const int n0 = max(0, min(seg, nt - j * seg));
-            s_n[tid] = n0;
-            s_st[tid * 4 + 0] = (unsigned long long)n0;
+        if (s_unit >= total) break;
+        const Unit un = unpack_unit(s_desc);
+        const int l = un.l, t = un.t, nq = un.nq, nt = un.nt;
+        bool my_inf = true;
+        if (tid < nq) {
+            const int q = wv.items[un.item + tid];
+            const float tq = wv.tau[q];
+            s_q[tid] = q;
+            s_tau[tid] = tq;
+            my_inf = isinf(tq);
+            s_st[tid * 4 + 0] = (unsigned long long)nt;
             s_st[tid * 4 + 1] = s_st[tid * 4 + 2] = s_st[tid * 4 + 3] = 0ull;
         }
-        for (int e = tid; e < nq * kT; e += kScanThreads) {
-            sh.alive[e] = (uint8_t)(e % kT);
-            sh.part[e] = 0.f;
+        const int npairs = nq * nt;
+        if (tid < kWarps) {
+            int cnt = 0;
+            for (int h = tid; h * 32 < npairs; h += kWarps) cnt += min(32, npairs - h * 32);
+            s_n[tid] = cnt;
         }
-        __syncthreads();
+        for (int e = tid; e < npairs; e += kScanThreads) {
+            const int g = e / nt, c = e - g * nt;
+            const int h = e >> 5;
+            const int wi = h % kWarps, pos = (h / kWarps) * 32 + (e & 31);
+            sh.key[wi * kWarpCap + pos] = (uint16_t)((g << 8) | c);
+            sh.part[wi * kWarpCap + pos] = 0.f;
+        }
+        const bool all_inf = __syncthreads_and(my_inf);
         const int64_t slot_l = ix.list_slot[l];
         const int64_t npad = ix.list_slot[l + 1] - slot_l;
         const int64_t ebase = slot_l * ix.Dpad;
         const int32_t slot0 = (int32_t)(slot_l + (int64_t)t * kT);
+        uint16_t* key = sh.key + warp * kWarpCap;
+        float* part = sh.part + warp * kWarpCap;
         bool ok;
-        const bool exact_all = FULL || s_inf;
-        if (exact_all) {
-            // every candidate's exact distance through the staged pipeline
+        if (FULL || all_inf) {
+            // every pair's exact distance through the staged pipeline
             ok = run_steps<float, NBLK, false>(ix.orig + ebase, npad, t, nt, nq, nsteps_full, ix.nb,
                                                ix.D, sh, ph, wv.qpad, ix.Dpad, nullptr, nullptr,
-                                               nullptr, wv.status, wv.staged_bytes);
+                                               nullptr, wv.status, wv.staged_bytes, want_stats);
             if (!ok) break;
-            for (int p = warp; p < nq * ws; p += kWarps) {
-                const int g = p / ws;
-                const int q = s_q[g];
-                const float tau = s_tau[g];
-                const int be = pair_base(sh, p);
-                const int n = s_n[p];
-                for (int base = 0; base < n; base += 32) {
-                    const int i = base + lane;
-                    const bool valid = i < n;
-                    const float d = valid ? sh.part[be + i] : 0.f;
-                    const int c = valid ? sh.alive[be + i] : 0;
-                    append(wv, w, q, valid && d <= tau, d, slot0 + c, lane);
-                }
-                if (lane == 0) {
-                    s_st[p * 4 + 2] += (unsigned long long)n;
-                    s_st[p * 4 + 3] += (unsigned long long)n * ix.D;
+            const int n = s_n[warp];
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                const bool valid = i < n;
+                const int kk = valid ? key[i] : 0;
+                const int g = kk >> 8;
+                const float d = valid ? part[i] : 0.f;
+                append_any(wv, w, s_q[g], valid && d <= s_tau[g], d, slot0 + (kk & 255), lane);
+                if (want_stats && valid) {
+                    atomicAdd(&s_st[g * 4 + 2], 1ull);
+                    atomicAdd(&s_st[g * 4 + 3], (unsigned long long)ix.D);
                 }
             }
         } else {
@@ -495,48 +484,46 @@ __global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, W
             ok = run_steps<E, NBLK, true>(slab, npad, t, nt, nq, S - 1, ix.nb, ix.D, sh, ph, wv.qrot,
                                           ix.Dpad, m1, beta,
                                           DT == DADE_SLAB_FP8E4M3 ? ix.scale : nullptr, wv.status,
-                                          wv.staged_bytes);
+                                          wv.staged_bytes, want_stats);
             if (!ok) break;
             // survivors: exact distance from the original vector, eseg lanes each
             const int per = 32 / eseg;
-            for (int p = warp; p < nq * ws; p += kWarps) {
-                const int g = p / ws;
+            const int n = s_n[warp];
+            for (int base = 0; base < n; base += per) {
+                const int i = base + lane / eseg;
+                const bool valid = i < n;
+                const int kk = valid ? key[i] : 0;
+                const int g = kk >> 8, c = kk & 255;
                 const int q = s_q[g];
-                const float tau = s_tau[g];
-                const int n = s_n[p];
-                const int be = pair_base(sh, p);
-                const float* qp = wv.qpad + (int64_t)q * ix.Dpad;
-                for (int base = 0; base < n; base += per) {
-                    const int i = base + lane / eseg;
-                    const bool valid = i < n;
-                    const int c = valid ? sh.alive[be + i] : 0;
-                    const float d = exact_coop(ix.orig + ebase + ((int64_t)t * kT + c) * kBlock, npad, qp,
-                                               valid, ix.nb, lane, eseg);
-                    const bool lead = (lane & (eseg - 1)) == 0;
-                    append(wv, w, q, valid && lead && d <= tau, d, slot0 + c, lane);
-                }
-                if (lane == 0) {
-                    s_st[p * 4 + 2] += (unsigned long long)n;
-                    s_st[p * 4 + 3] += (unsigned long long)n * ix.D;
-                    if (wv.staged_bytes && n)
-                        atomicAdd(wv.staged_bytes, (unsigned long long)n * ix.nb * kBlock * sizeof(float));
+                const float d = exact_coop(ix.orig + ebase + ((int64_t)t * kT + c) * kBlock, npad,
+                                           wv.qpad + (int64_t)q * ix.Dpad, valid, ix.nb, lane, eseg);
+                const bool lead = valid && (lane & (eseg - 1)) == 0;
+                append_any(wv, w, q, lead && d <= s_tau[g], d, slot0 + c, lane);
+                if (want_stats && lead) {
+                    atomicAdd(&s_st[g * 4 + 2], 1ull);
+                    atomicAdd(&s_st[g * 4 + 3], (unsigned long long)ix.D);
                 }
             }
+            if (wv.staged_bytes && lane == 0 && n)
+                atomicAdd(wv.staged_bytes, (unsigned long long)n * ix.nb * kBlock * sizeof(float));
         }
         __syncthreads();
-        if (wv.stats && tid < nq * ws * 4) {
-            const int p = tid / 4, f = tid % 4;
-            if (s_st[tid]) atomicAdd((unsigned long long*)&wv.stats[(int64_t)s_q[p / ws] * 4 + f], s_st[tid]);
+        if (want_stats && tid < nq * 4) {
+            if (s_st[tid]) atomicAdd((unsigned long long*)&wv.stats[(int64_t)s_q[tid / 4] * 4 + (tid % 4)], s_st[tid]);
         }
         __syncthreads();
     }
 }
 
 // ------------------------------------------------------------ merge
-// One warp per query: the wave's candidates are sorted in chunks of
-// kMergeChunk (warp bitonic sort in shared memory) and merged with the sorted
-// top-K by rank: an element's place is its index plus the number of elements
-// of the other list that precede it in (distance, id) order.
+// One warp per query.  The wave's candidates are streamed in chunks of up to
+// kMergeChunk, each chunk sorted (warp bitonic sort in shared memory) and
+// merged with the sorted top-K by rank: an element's place is its index plus
+// the number of elements of the other list that precede it in (distance, id)
+// order.  When there are many candidates (a wave whose tau was +inf appends
+// all of them), a warp radix select first finds the K-th smallest distance v
+// among them and only candidates with distance <= v are merged: at least K of
+// the candidates are <= v, so no other candidate can enter the top-K.
 constexpr int kMergeWarps = 8;
 constexpr int kMergeChunk = 256;
 
@@ -554,8 +541,120 @@ __device__ __forceinline__ int count_before(const float* d, const long long* id,
     return lo;
 }
 
+// The k-th smallest (1-based) 32-bit pattern of the non-negative floats
+// v[0, n), by an MSD radix select over 8-bit digits (warp-wide).
+__device__ uint32_t warp_kth_bits(const float* v, int n, int k, int* hist, int lane) {
+    uint32_t prefix = 0, mask = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = lane; b < 256; b += 32) hist[b] = 0;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const uint32_t key = __float_as_uint(v[i]);
+            if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
+        }
+        __syncwarp();
+        // lane j owns bins [8j, 8j + 8): find the bin where the count reaches k
+        int h[8], s = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            h[u] = hist[lane * 8 + u];
+            s += h[u];
+        }
+        int incl = s;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        const int excl = incl - s;
+        const unsigned hit = __ballot_sync(0xffffffffu, excl < k && incl >= k);
+        const int src = __ffs(hit) - 1;
+        int digit = 0, below = 0;
+        if (lane == src) {
+            int cum = excl;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (cum + h[u] >= k) {
+                    digit = lane * 8 + u;
+                    break;
+                }
+                cum += h[u];
+            }
+            below = cum;
+        }
+        digit = __shfl_sync(0xffffffffu, digit, src);
+        below = __shfl_sync(0xffffffffu, below, src);
+        k -= below;
+        prefix |= (uint32_t)digit << shift;
+        mask |= 255u << shift;
+        __syncwarp();
+    }
+    return prefix;
+}
+
+__device__ __forceinline__ void warp_sort(float* bd, long long* bi, int M, int lane) {
+    for (int size = 2; size <= M; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < M; i += 32) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const bool sw = up ? pair_less(bd[j], bi[j], bd[i], bi[i])
+                                       : pair_less(bd[i], bi[i], bd[j], bi[j]);
+                    if (sw) {
+                        float x = bd[i];
+                        bd[i] = bd[j];
+                        bd[j] = x;
+                        long long y = bi[i];
+                        bi[i] = bi[j];
+                        bi[j] = y;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Sort the chunk b[0, m) and merge it into a[0, cur) keeping the best
+// min(K, cur + m); returns the new count (result in a).
+__device__ int merge_chunk(float* ad, long long* ai, int cur, float* bd, long long* bi, int m, float* od,
+                           long long* oi, int K, int lane) {
+    int M = 1;
+    while (M < m) M <<= 1;
+    for (int i = m + lane; i < M; i += 32) {
+        bd[i] = INFINITY;
+        bi[i] = LLONG_MAX;
+    }
+    __syncwarp();
+    warp_sort(bd, bi, M, lane);
+    const int nout = min(K, cur + m);
+    for (int i = lane; i < cur; i += 32) {
+        const int r = i + count_before(bd, bi, m, ad[i], ai[i]);
+        if (r < nout) {
+            od[r] = ad[i];
+            oi[r] = ai[i];
+        }
+    }
+    for (int i = lane; i < m; i += 32) {
+        const int r = i + count_before(ad, ai, cur, bd[i], bi[i]);
+        if (r < nout) {
+            od[r] = bd[i];
+            oi[r] = bi[i];
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < nout; i += 32) {
+        ad[i] = od[i];
+        ai[i] = oi[i];
+    }
+    __syncwarp();
+    return nout;
+}
+
 __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(IndexView ix, WaveView wv, int w) {
     extern __shared__ __align__(16) unsigned char msmem[];
+    __shared__ int s_hist[kMergeWarps][256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * kMergeWarps + warp;
     if (q >= wv.B) return;
@@ -579,6 +678,8 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(IndexView ix, W
         if (lane == 0) wv.cand_cnt[q] = 0;
         return;
     }
+    const float* cd = wv.cand_d + off;
+    const int32_t* cp = wv.cand_pos + off;
     float* td = wv.top_d + q * wv.Kmax;
     int64_t* ti = wv.top_id + q * wv.Kmax;
     int cur = wv.top_n[q];
@@ -586,64 +687,26 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(IndexView ix, W
         ad[i] = td[i];
         ai[i] = ti[i];
     }
-    for (int done = 0; done < cnt; done += kMergeChunk) {
-        const int m = min(kMergeChunk, cnt - done);
-        int M = 1;
-        while (M < m) M <<= 1;
-        for (int i = lane; i < M; i += 32) {
-            if (i < m) {
-                bd[i] = wv.cand_d[off + done + i];
-                bi[i] = ix.ids[wv.cand_pos[off + done + i]];
-            } else {
-                bd[i] = INFINITY;
-                bi[i] = LLONG_MAX;
-            }
+    // candidates above the K-th smallest of this wave cannot enter the top-K
+    const uint32_t thr = cnt > max(K, kMergeChunk) ? warp_kth_bits(cd, cnt, K, s_hist[warp], lane) : 0xffffffffu;
+    int m = 0;  // filled part of the chunk
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        const bool keep = i < cnt && __float_as_uint(cd[i]) <= thr;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int pos = m + __popc(bal & lanemask_lt());
+            bd[pos] = cd[i];
+            bi[pos] = ix.ids[cp[i]];
         }
+        m += __popc(bal);
         __syncwarp();
-        for (int size = 2; size <= M; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = lane; i < M; i += 32) {
-                    const int j = i ^ stride;
-                    if (j > i) {
-                        const bool up = (i & size) == 0;
-                        const bool sw = up ? pair_less(bd[j], bi[j], bd[i], bi[i])
-                                           : pair_less(bd[i], bi[i], bd[j], bi[j]);
-                        if (sw) {
-                            float x = bd[i];
-                            bd[i] = bd[j];
-                            bd[j] = x;
-                            long long y = bi[i];
-                            bi[i] = bi[j];
-                            bi[j] = y;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
+        if (m > kMergeChunk - 32) {
+            cur = merge_chunk(ad, ai, cur, bd, bi, m, od, oi, K, lane);
+            m = 0;
         }
-        const int nout = min(K, cur + m);
-        for (int i = lane; i < cur; i += 32) {
-            const int r = i + count_before(bd, bi, m, ad[i], ai[i]);
-            if (r < nout) {
-                od[r] = ad[i];
-                oi[r] = ai[i];
-            }
-        }
-        for (int i = lane; i < m; i += 32) {
-            const int r = i + count_before(ad, ai, cur, bd[i], bi[i]);
-            if (r < nout) {
-                od[r] = bd[i];
-                oi[r] = bi[i];
-            }
-        }
-        __syncwarp();
-        for (int i = lane; i < nout; i += 32) {
-            ad[i] = od[i];
-            ai[i] = oi[i];
-        }
-        __syncwarp();
-        cur = nout;
     }
+    if (m > 0) cur = merge_chunk(ad, ai, cur, bd, bi, m, od, oi, K, lane);
     for (int i = lane; i < cur; i += 32) {
         td[i] = ad[i];
         ti[i] = ai[i];
@@ -782,6 +845,28 @@ struct LoadCap {
     __device__ int64_t operator()(int seg, int64_t i) const { return p[seg * stride + i]; }
 };
 
+// One thread per (wave, bucket): write the descriptors of the bucket's units
+// in this wave, in the order of unit_off (group-major, then tile).
+__global__ void expand_units_kernel(IndexView ix, WaveView wv) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)wv.n_waves * ix.nlist) return;
+    const int w = (int)(e / ix.nlist), l = (int)(e % ix.nlist);
+    const int cnt = wv.cnt_wl[e];
+    if (cnt == 0) return;
+    const int nl = ix.list_size[l];
+    const int ntile = (nl + kT - 1) / kT;
+    const int ng = (cnt + kG - 1) / kG;
+    int4* out = wv.units + wv.ubase[w] + wv.unit_off[(int64_t)w * (ix.nlist + 1) + l];
+    const int item0 = wv.off_wl[e];
+    for (int g = 0; g < ng; ++g) {
+        const int nq = min(kG, cnt - g * kG);
+        for (int t = 0; t < ntile; ++t) {
+            const int nt = min(kT, nl - t * kT);
+            out[g * ntile + t] = make_int4(l, t, item0 + g * kG, (nq << 16) | nt);
+        }
+    }
+}
+
 __global__ void prepare_queries_kernel(const float* Q, int64_t B, int32_t D, int32_t Dpad, float* qpad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * Dpad) return;
@@ -802,7 +887,6 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
                                                                int S, CollectArgs ca, int64_t qoff) {
     using E = typename Elem<DT>::T;
     __shared__ int s_unit;
-    __shared__ Unit s_un;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int total = wv.unit_off[(int64_t)w * (ix.nlist + 1) + ix.nlist];
     const int nblk = dd / kBlock;
@@ -811,9 +895,7 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
         __syncthreads();
         const int u = s_unit;
         if (u >= total) break;
-        if (tid == 0) s_un = decode_unit(ix, wv, w, u);
-        __syncthreads();
-        const Unit un = s_un;
+        const Unit un = unpack_unit(wv.units[wv.ubase[w] + u]);
         const int64_t slot_l = ix.list_slot[un.l];
         const int64_t npad = ix.list_slot[un.l + 1] - slot_l;
         const int64_t ebase = slot_l * ix.Dpad;
@@ -929,6 +1011,7 @@ cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStre
     seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(LoadCap{wv.cand_off, wv.B + 1}, wv.cand_off, wv.B,
                                                  wv.B + 1);
     scatter_kernel<<<gb, 128, 0, st>>>(ix, wv);
+    expand_units_kernel<<<(unsigned)ceil_div(nwl, 128), 128, 0, st>>>(ix, wv);
     return cudaGetLastError();
 }
 

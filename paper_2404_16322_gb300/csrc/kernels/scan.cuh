@@ -33,6 +33,8 @@ struct WaveView {
     int32_t* fill_wl;         // n_waves x nlist: scatter cursors
     int32_t* items;           // B x P query ids grouped by (wave, bucket)
     int32_t* unit_off;        // n_waves x (nlist + 1): work units per wave, prefix
+    int4* units;              // unit descriptors {bucket, tile, first item, nq << 16 | nt}
+    int64_t ubase[16];        // first descriptor of each wave in `units`
     int64_t* cand_off;        // n_waves x (B + 1): candidate capacity per query, prefix
     int32_t* cand_cnt;        // B: candidates appended in the current wave
     float* cand_d;            // candidate buffer (capacity of the largest wave)

@@ -78,6 +78,16 @@ size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* 
     v.off_wl = c.take<int32_t>((size_t)nw * nl + 1);
     v.items = c.take<int32_t>((size_t)B * P);
     v.unit_off = c.take<int32_t>((size_t)nw * (nl + 1));
+    // unit descriptors: a wave has at most (items / kG + buckets touched) groups,
+    // each with ceil(largest bucket / kT) tiles
+    const int64_t ntile_max = std::max<int64_t>(1, ceil_div(idx->max_list, kT));
+    int64_t ucap = 0;
+    for (int w = 0; w < nw; ++w) {
+        const int64_t width = std::max(0, std::min(P, wave_begin(w + 1, f)) - wave_begin(w, f));
+        v.ubase[w] = ucap;
+        ucap += (ceil_div(B * width, kG) + std::min<int64_t>(nl, B * width)) * ntile_max;
+    }
+    v.units = c.take<int4>((size_t)std::max<int64_t>(1, ucap));
     pl->cand_cap = B * cap_per_q;
     v.cand_d = c.take<float>((size_t)std::max<int64_t>(1, pl->cand_cap));
     v.cand_pos = c.take<int32_t>((size_t)std::max<int64_t>(1, pl->cand_cap));
