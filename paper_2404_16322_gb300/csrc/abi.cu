@@ -353,6 +353,9 @@ extern "C" dade_status dade_index_load(const char* path, dade_index** out) {
     DADE_CUDA_TRY(cudaMemcpy(idx->R_dev.p, Rf.data(), sizeof(float) * Rf.size(), cudaMemcpyHostToDevice));
     DADE_CUDA_TRY(cudaMemcpy(idx->mean_dev.p, mf.data(), sizeof(float) * mf.size(), cudaMemcpyHostToDevice));
     DADE_CUDA_TRY(cudaMemcpy(idx->cent_dev.p, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice));
+    DADE_TRY(idx->cnorm_dev.alloc(sizeof(float) * nl));
+    DADE_CUDA_TRY(launch_row_norms(idx->cent_dev.as<float>(), Dp, nl, Dp, idx->cnorm_dev.as<float>(), 0));
+    DADE_CUDA_TRY(cudaDeviceSynchronize());
     if (idx->dtype == DADE_SLAB_FP8E4M3) {
         DADE_TRY(idx->scale_dev.alloc(sizeof(float) * Dp));
         DADE_CUDA_TRY(cudaMemcpy(idx->scale_dev.p, idx->fp8_scale.data(), sizeof(float) * Dp, cudaMemcpyHostToDevice));

@@ -130,8 +130,8 @@ extern "C" dade_status ivf_build(const float* X, int64_t N, int32_t D, const dou
     DADE_TRY(xr_dev.alloc(sizeof(float) * N * Dp));
     DADE_TRY(amin.alloc(sizeof(unsigned long long) * N));
     DADE_CUDA_TRY(cudaMemcpyAsync(x_dev.p, X, sizeof(float) * N * D, cudaMemcpyHostToDevice, st));
-    DADE_CUDA_TRY(launch_gemm_store(GEMM_DOT, x_dev.as<float>(), D, idx->mean_dev.as<float>(),
-                                    idx->R_dev.as<float>(), Dp, xr_dev.as<float>(), Dp, N, Dp, D, st));
+    DADE_CUDA_TRY(launch_tc_dot(x_dev.as<float>(), D, idx->mean_dev.as<float>(), idx->R_dev.as<float>(), Dp,
+                                xr_dev.as<float>(), Dp, N, Dp, D, nullptr, st));
 
     // centroids (rotated space)
     std::vector<float> cent((size_t)nl * Dp, 0.f);
@@ -160,6 +160,8 @@ extern "C" dade_status ivf_build(const float* X, int64_t N, int32_t D, const dou
     }
     DADE_CUDA_TRY(cudaMemcpyAsync(idx->cent_dev.p, cent.data(), sizeof(float) * cent.size(),
                                   cudaMemcpyHostToDevice, st));
+    DADE_TRY(idx->cnorm_dev.alloc(sizeof(float) * nl));
+    DADE_CUDA_TRY(launch_row_norms(idx->cent_dev.as<float>(), Dp, nl, Dp, idx->cnorm_dev.as<float>(), st));
     if (p->assign) {
         memcpy(assign.data(), p->assign, sizeof(int32_t) * N);
     } else {

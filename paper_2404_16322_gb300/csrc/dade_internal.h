@@ -88,6 +88,7 @@ struct dade_index {
     dade::DevBuf R_dev;        // Dpad x Dpad FP32 (zero beyond D)
     dade::DevBuf mean_dev;     // Dpad FP32
     dade::DevBuf cent_dev;     // nlist x Dpad FP32
+    dade::DevBuf cnorm_dev;    // nlist FP32: ||c||^2
     dade::DevBuf list_size_dev;  // nlist int32
     dade::DevBuf list_slot_dev;  // nlist + 1 int64
     dade::DevBuf slab_dev;     // total_slots x Dpad elements of dtype, blocked
@@ -122,6 +123,15 @@ cudaError_t launch_gemm_store(int op, const float* A, int64_t lda, const float* 
 cudaError_t launch_gemm_argmin(const float* A, int64_t lda, const float* B, int64_t ldb,
                                unsigned long long* out, int64_t M, int64_t N, int Kd,
                                cudaStream_t st);
+// Tensor-core (tcgen05, 3xTF32) GEMMs: C = (A - sub) B^T, and
+// C = max(0, an + bn - 2 A B^T) (squared distances from norms).
+cudaError_t launch_tc_dot(const float* A, int64_t lda, const float* sub, const float* B, int64_t ldb,
+                          float* C, int64_t ldc, int64_t M, int64_t N, int Kd, int32_t* status,
+                          cudaStream_t st);
+cudaError_t launch_tc_l2(const float* A, int64_t lda, const float* an, const float* B, int64_t ldb,
+                         const float* bn, float* C, int64_t ldc, int64_t M, int64_t N, int Kd,
+                         int32_t* status, cudaStream_t st);
+cudaError_t launch_row_norms(const float* X, int64_t ld, int64_t M, int n, float* out, cudaStream_t st);
 // Per row b: the nprobe[b] smallest of scores[b, 0:n] ordered by (score, column).
 cudaError_t launch_select_probes(const float* scores, int64_t B, int n, const int32_t* nprobe,
                                  int P, int32_t* probes, int32_t* status, cudaStream_t st);

@@ -41,6 +41,7 @@ struct Carve {
 struct Plan {
     WaveView wv{};
     float* scores = nullptr;
+    float* qnorm = nullptr;
     char* zero_begin = nullptr;
     size_t zero_bytes = 0;
     int32_t* status_internal = nullptr;
@@ -74,6 +75,7 @@ size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* 
     v.qrot = c.take<float>((size_t)B * idx->Dpad);
     v.qpad = c.take<float>((size_t)B * idx->Dpad);
     pl->scores = o.probe_in_dev ? nullptr : c.take<float>((size_t)B * nl);
+    pl->qnorm = o.probe_in_dev ? nullptr : c.take<float>((size_t)B);
     v.probes = c.take<int32_t>((size_t)B * P);
     v.off_wl = c.take<int32_t>((size_t)nw * nl + 1);
     v.items = c.take<int32_t>((size_t)B * P);
@@ -197,9 +199,8 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
         DADE_CUDA_TRY(launch_fill(v.tau, B, INFINITY, st));
 
     // 1. q' = R (q - mean); the original query zero-padded to Dpad
-    DADE_CUDA_TRY(launch_gemm_store(GEMM_DOT, Q, idx->D, idx->mean_dev.as<float>(),
-                                    idx->R_dev.as<float>(), idx->Dpad, const_cast<float*>(v.qrot),
-                                    idx->Dpad, B, idx->Dpad, idx->D, st));
+    DADE_CUDA_TRY(launch_tc_dot(Q, idx->D, idx->mean_dev.as<float>(), idx->R_dev.as<float>(), idx->Dpad,
+                                const_cast<float*>(v.qrot), idx->Dpad, B, idx->Dpad, idx->D, v.status, st));
     DADE_CUDA_TRY(launch_prepare_queries(Q, B, idx->D, idx->Dpad, const_cast<float*>(v.qpad), st));
     if (o.qrot_out_dev) {
         DADE_CUDA_TRY(cudaMemcpy2DAsync(o.qrot_out_dev, sizeof(float) * idx->D, v.qrot,
@@ -211,8 +212,10 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
         DADE_CUDA_TRY(cudaMemcpyAsync(const_cast<int32_t*>(v.probes), o.probe_in_dev,
                                       sizeof(int32_t) * B * v.P, cudaMemcpyDeviceToDevice, st));
     } else {
-        DADE_CUDA_TRY(launch_gemm_store(GEMM_L2, v.qrot, idx->Dpad, nullptr, idx->cent_dev.as<float>(),
-                                        idx->Dpad, pl.scores, idx->nlist, B, idx->nlist, idx->Dpad, st));
+        DADE_CUDA_TRY(launch_row_norms(v.qrot, idx->Dpad, B, idx->Dpad, pl.qnorm, st));
+        DADE_CUDA_TRY(launch_tc_l2(v.qrot, idx->Dpad, pl.qnorm, idx->cent_dev.as<float>(), idx->Dpad,
+                                   idx->cnorm_dev.as<float>(), pl.scores, idx->nlist, B, idx->nlist, idx->Dpad,
+                                   v.status, st));
         DADE_CUDA_TRY(launch_select_probes(pl.scores, B, idx->nlist, nprobe_dev, v.P,
                                            const_cast<int32_t*>(v.probes), v.status, st));
     }
