@@ -35,19 +35,29 @@ __device__ int block_excl_scan(int flag, int* warp_sums, int* total) {
     return base + pre;
 }
 
+// STAGED: the row is first copied to shared memory (n <= kStageMax).
+constexpr int kStageMax = 16384;
+
+template <bool STAGED>
 __global__ void __launch_bounds__(NT) select_kernel(const float* __restrict__ scores, int n,
                                                     const int32_t* __restrict__ nprobe, int P,
                                                     int32_t* __restrict__ probes,
                                                     int32_t* __restrict__ status) {
+    extern __shared__ float srow[];
     __shared__ int hist[256];
     __shared__ int warp_sums[NT / 32];
     __shared__ uint32_t sel_key[PMAX];
     __shared__ int sel_id[PMAX];
     __shared__ int s_digit, s_below;
     const int64_t b = blockIdx.x;
-    const float* row = scores + b * (int64_t)n;
+    const float* grow = scores + b * (int64_t)n;
     int32_t* out = probes + b * (int64_t)P;
     const int tid = threadIdx.x;
+    if (STAGED) {
+        for (int i = tid; i < n; i += NT) srow[i] = grow[i];
+        __syncthreads();
+    }
+    const float* row = STAGED ? srow : grow;
     int np = nprobe[b];
     if (np < 1 || np > P || np > n) {
         if (tid == 0 && status) atomicCAS(status, 0, (int)DADE_EINVAL);
@@ -141,7 +151,18 @@ cudaError_t launch_select_probes(const float* scores, int64_t B, int n, const in
                                  int P, int32_t* probes, int32_t* status, cudaStream_t st) {
     if (B <= 0) return cudaSuccess;
     if (P > PMAX) return cudaErrorInvalidValue;
-    select_kernel<<<(unsigned)B, NT, 0, st>>>(scores, n, nprobe, P, probes, status);
+    if (n <= kStageMax) {
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kStageMax * (int)sizeof(float));
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        select_kernel<true><<<(unsigned)B, NT, n * sizeof(float), st>>>(scores, n, nprobe, P, probes, status);
+    } else {
+        select_kernel<false><<<(unsigned)B, NT, 0, st>>>(scores, n, nprobe, P, probes, status);
+    }
     return cudaGetLastError();
 }
 

@@ -86,9 +86,59 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, int32_t
 
 enum Epi { EPI_STORE = 0, EPI_L2 = 1 };
 
+// Loads the 128 x 32 K-block at (row0, k0) of a row-major operand and stores
+// its TF32 hi and lo parts.  VEC: float4 loads (rows 16-byte aligned, K a
+// multiple of 4); element f of the 1024 float4s of the block maps to row
+// (f / 64) * 8 + f % 8 and float4 column (f / 8) % 8, so the 8 lanes of a
+// quarter warp store to 8 different rows of one core-matrix column (distinct
+// banks) and each row is read in 64-byte runs.
+template <bool VEC>
+__device__ __forceinline__ void load_split(const float* __restrict__ X, int64_t ld, const float* __restrict__ sub,
+                                           int64_t row0, int64_t nrows, int k0, int Kd,
+                                           unsigned char* hi, unsigned char* lo, int tid) {
+    if (VEC) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int f = tid + 128 * i;
+            const int r = (f >> 6) * 8 + (f & 7), c4 = (f >> 3) & 7;
+            const int64_t gr = row0 + r;
+            const int gk = k0 + c4 * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gr < nrows && gk < Kd) {
+                v = __ldg(reinterpret_cast<const float4*>(X + gr * ld + gk));
+                if (sub) {
+                    const float4 m = __ldg(reinterpret_cast<const float4*>(sub + gk));
+                    v.x -= m.x; v.y -= m.y; v.z -= m.z; v.w -= m.w;
+                }
+            }
+            float4 h, l;
+            h.x = to_tf32(v.x); h.y = to_tf32(v.y); h.z = to_tf32(v.z); h.w = to_tf32(v.w);
+            l.x = to_tf32(v.x - h.x); l.y = to_tf32(v.y - h.y); l.z = to_tf32(v.z - h.z); l.w = to_tf32(v.w - h.w);
+            const uint32_t o = tile_off(r, c4 * 4);
+            *reinterpret_cast<float4*>(hi + o) = h;
+            *reinterpret_cast<float4*>(lo + o) = l;
+        }
+    } else {
+        for (int e = tid; e < TM * TKB; e += 128) {
+            const int r = e / TKB, j = e % TKB;
+            const int64_t gr = row0 + r;
+            const int gk = k0 + j;
+            float v = 0.f;
+            if (gr < nrows && gk < Kd) {
+                v = X[gr * ld + gk];
+                if (sub) v -= sub[gk];
+            }
+            const float h = to_tf32(v);
+            const uint32_t o = tile_off(r, j);
+            *reinterpret_cast<float*>(hi + o) = h;
+            *reinterpret_cast<float*>(lo + o) = to_tf32(v - h);
+        }
+    }
+}
+
 // A: M x Kd (lda), optionally minus sub[k]; B: N x Kd (ldb).
 // EPI_STORE: C = dot.  EPI_L2: C = max(0, an[m] + bn[n] - 2 dot).
-template <int EPI>
+template <int EPI, bool VA, bool VB>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict__ A, int64_t lda,
                                                          const float* __restrict__ sub,
                                                          const float* __restrict__ Bm, int64_t ldb,
@@ -128,27 +178,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
     const int nkb = (Kd + TKB - 1) / TKB;
     for (int kb = 0; kb < nkb; ++kb) {
         const int k0 = kb * TKB;
-        // 128 rows x 32 columns per operand: thread tid loads row tid
-        {
-            const int r = tid;
-            const int64_t gm = m0 + r, gn = n0 + r;
-#pragma unroll 4
-            for (int j = 0; j < TKB; ++j) {
-                const int gk = k0 + j;
-                float a = 0.f, b = 0.f;
-                if (gm < M && gk < Kd) {
-                    a = A[gm * lda + gk];
-                    if (sub) a -= sub[gk];
-                }
-                if (gn < N && gk < Kd) b = Bm[gn * ldb + gk];
-                const float ah = to_tf32(a), bh = to_tf32(b);
-                const uint32_t o = tile_off(r, j);
-                *reinterpret_cast<float*>(a_hi + o) = ah;
-                *reinterpret_cast<float*>(a_lo + o) = to_tf32(a - ah);
-                *reinterpret_cast<float*>(b_hi + o) = bh;
-                *reinterpret_cast<float*>(b_lo + o) = to_tf32(b - bh);
-            }
-        }
+        load_split<VA>(A, lda, sub, m0, M, k0, Kd, a_hi, a_lo, tid);
+        load_split<VB>(Bm, ldb, nullptr, n0, N, k0, Kd, b_hi, b_lo, tid);
         // make the generic-proxy stores visible to the tensor core
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -176,7 +207,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
     }
 
     if (s_ok) {
-        // epilogue: warp w owns accumulator lanes (rows) [32w, 32w + 32)
+        // epilogue: warp w owns accumulator lanes (rows) [32w, 32w + 32); a
+        // 32 x 16 block goes through shared memory (the operand area, free
+        // now) so that global stores run along rows
+        float* stage = reinterpret_cast<float*>(base) + warp * 32 * 17;
         const int r = warp * 32 + lane;
         const int64_t gm = m0 + r;
         const float arow = (EPI == EPI_L2 && gm < M) ? an[gm] : 0.f;
@@ -192,19 +226,22 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
                   "=r"(v[14]), "=r"(v[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (gm < M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int64_t gn = n0 + c0 + j;
-                    if (gn < N) {
-                        const float dot = __uint_as_float(v[j]);
-                        float out;
-                        if (EPI == EPI_L2) out = fmaxf(0.f, arow + bn[gn] - 2.f * dot);
-                        else out = dot;
-                        C[gm * ldc + gn] = out;
-                    }
-                }
+            for (int j = 0; j < 16; ++j) {
+                const float dot = __uint_as_float(v[j]);
+                float out;
+                if (EPI == EPI_L2) out = fmaxf(0.f, arow + (n0 + c0 + j < N ? bn[n0 + c0 + j] : 0.f) - 2.f * dot);
+                else out = dot;
+                stage[lane * 17 + j] = out;
             }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int e = i * 32 + lane, rr = e >> 4, cc = e & 15;
+                const int64_t grow = m0 + warp * 32 + rr, gcol = n0 + c0 + cc;
+                if (grow < M && gcol < N) C[grow * ldc + gcol] = stage[rr * 17 + cc];
+            }
+            __syncwarp();
         }
     }
     if (!s_ok) {
@@ -235,20 +272,38 @@ __global__ void row_norms_kernel(const float* __restrict__ X, int64_t ld, int64_
 
 constexpr int kSmem = 4 * TILE_BYTES + 1024;  // four operand parts + alignment slack
 
+template <int EPI, bool VA, bool VB>
+cudaError_t launch_v(const float* A, int64_t lda, const float* sub, const float* B, int64_t ldb,
+                     const float* an, const float* bn, float* C, int64_t ldc, int64_t M, int64_t N, int Kd,
+                     int32_t* status, cudaStream_t st) {
+    static bool configured = false;
+    auto kern = tc_gemm_kernel<EPI, VA, VB>;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((unsigned)ceil_div(M, TM), (unsigned)ceil_div(N, TN));
+    kern<<<grid, 128, kSmem, st>>>(A, lda, sub, B, ldb, an, bn, C, ldc, M, N, Kd, status);
+    return cudaGetLastError();
+}
+
+// float4 loads need 16-byte aligned rows and K (and the subtrahend) in
+// whole float4s
+bool vec_ok(const float* X, int64_t ld, int Kd) {
+    return (reinterpret_cast<uintptr_t>(X) & 15) == 0 && ld % 4 == 0 && Kd % 4 == 0;
+}
+
 template <int EPI>
 cudaError_t launch_t(const float* A, int64_t lda, const float* sub, const float* B, int64_t ldb,
                      const float* an, const float* bn, float* C, int64_t ldc, int64_t M, int64_t N, int Kd,
                      int32_t* status, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     if (M <= 0 || N <= 0) return cudaSuccess;
-    dim3 grid((unsigned)ceil_div(M, TM), (unsigned)ceil_div(N, TN));
-    tc_gemm_kernel<EPI><<<grid, 128, kSmem, st>>>(A, lda, sub, B, ldb, an, bn, C, ldc, M, N, Kd, status);
-    return cudaGetLastError();
+    const bool va = vec_ok(A, lda, Kd) && (!sub || (reinterpret_cast<uintptr_t>(sub) & 15) == 0);
+    const bool vb = vec_ok(B, ldb, Kd);
+    if (va && vb) return launch_v<EPI, true, true>(A, lda, sub, B, ldb, an, bn, C, ldc, M, N, Kd, status, st);
+    if (vb) return launch_v<EPI, false, true>(A, lda, sub, B, ldb, an, bn, C, ldc, M, N, Kd, status, st);
+    return launch_v<EPI, false, false>(A, lda, sub, B, ldb, an, bn, C, ldc, M, N, Kd, status, st);
 }
 
 }  // namespace
