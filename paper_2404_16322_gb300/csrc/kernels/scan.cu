@@ -129,15 +129,50 @@ __device__ __forceinline__ void load8(const __nv_fp8_storage_t* p, const float* 
     }
 }
 
-// s_b = sum over the block's 8 dims of (q - x)^2, FMA in dim order from 0.
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// s_b = sum over the block's 8 dims of (q - x)^2 with packed FP32 pairs:
+// the even and the odd dims each form an FMA chain in dim order (the first
+// term a product), and s_b = even + odd.  Every path uses this function, so
+// a pair's distance does not depend on the path that computed it.
 __device__ __forceinline__ float block_sq(const float (&q)[8], const float (&x)[8]) {
-    float s = 0.f;
+    unsigned long long acc, t;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(pack2(q[0], q[1])), "l"(pack2(x[0], x[1])));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(acc) : "l"(t));
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        float t = q[j] - x[j];
-        s = fmaf(t, t, s);
+    for (int j = 2; j < 8; j += 2) {
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(pack2(q[j], q[j + 1])), "l"(pack2(x[j], x[j + 1])));
+        asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(acc) : "l"(t), "l"(acc));
     }
-    return s;
+    float e, o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(e), "=f"(o) : "l"(acc));
+    return e + o;
+}
+
+// 8 FP32 values of one block from the shared-memory slab buffer.  A block
+// is 32 bytes; lanes whose bit 2 is set read its second half first, so each
+// 16-byte load of a quarter warp touches all 32 banks once.
+__device__ __forceinline__ void load8_staged(const float* p, const float*, float (&x)[8]) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    const int sw = (threadIdx.x >> 2) & 1;
+    float4 a = p4[sw], b = p4[sw ^ 1];
+    if (sw) {
+        const float4 t = a;
+        a = b;
+        b = t;
+    }
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void load8_staged(const __nv_bfloat16* p, const float* sc, float (&x)[8]) {
+    load8(p, sc, x);
+}
+__device__ __forceinline__ void load8_staged(const __nv_fp8_storage_t* p, const float* sc, float (&x)[8]) {
+    load8(p, sc, x);
 }
 
 __device__ __forceinline__ void load_q8(const float* p, float (&q)[8]) {
@@ -299,7 +334,7 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
                 for (int bb = 0; bb < NBLK; ++bb) {
                     if (bb < nbk) {
                         float x[8], qv[8];
-                        load8(bk + ((size_t)bb * kT + c) * kBlock, sh.sc + bb * kBlock, x);
+                        load8_staged(bk + ((size_t)bb * kT + c) * kBlock, sh.sc + bb * kBlock, x);
                         load8(qg + bb * kBlock, nullptr, qv);
                         pd += block_sq(qv, x);
                     }
@@ -367,7 +402,7 @@ constexpr int scan_smem_bytes() {
 }
 
 template <int DT, int NBLK, bool FULL>
-__global__ void __launch_bounds__(kScanThreads) wave_scan_kernel(IndexView ix, WaveView wv, int w,
+__global__ void __launch_bounds__(kScanThreads, 3) wave_scan_kernel(IndexView ix, WaveView wv, int w,
                                                                  const float* __restrict__ m1,
                                                                  const float* __restrict__ beta,
                                                                  int S) {
