@@ -36,6 +36,7 @@ TARGET_RECALL = 0.95
 NPROBES = [8, 16, 24, 32, 48, 64, 96, 128, 192, 256]
 DELTAS = [8, 16, 32]
 FIRST_WAVES = [1, 4]
+SERVING_RATES = [200_000, 1_000_000, 3_000_000]
 METRIC = "QPS at recall@10>=0.95 (estimate-and-prune IVF search, SIFT-shaped 1M x 128, nlist 4096, K 100)"
 
 
@@ -48,6 +49,7 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="database size override (debug)")
     ap.add_argument("--queries", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-sample-queries", type=int, default=400)
     ap.add_argument("--profile", default=None,
                     help="NPROBE,DELTA_D[,FIRST_WAVE]: skip the sweep and baselines; run W + K steps of that "
@@ -133,65 +135,6 @@ def ground_truth(X, Q, k=10, chunk=1024):
     del Xt
     torch.cuda.empty_cache()
     return out
-
-
-def recall_at(ids, gt, k=10):
-    hit = 0
-    for b in range(len(gt)):
-        hit += len(set(ids[b, :k].tolist()) & set(gt[b, :k].tolist()))
-    return hit / (k * len(gt))
-
-
-class Runner:
-    """Device-resident batch and outputs for repeated dade_search calls."""
-
-    def __init__(self, G, idx, Q, K, max_nprobe):
-        import torch
-        self.G, self.idx, self.torch = G, idx, torch
-        dev = torch.device("cuda")
-        self.B = len(Q)
-        self.K = K
-        self.q = torch.from_numpy(Q).to(dev)
-        self.k = torch.full((self.B,), K, dtype=torch.int32, device=dev)
-        self.np = torch.zeros(self.B, dtype=torch.int32, device=dev)
-        self.ids = torch.empty(self.B * K, dtype=torch.int64, device=dev)
-        self.d = torch.empty(self.B * K, dtype=torch.float32, device=dev)
-        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.stats = torch.zeros((self.B, 4), dtype=torch.int64, device=dev)
-        ws = max(G.dade_search_workspace_size(idx, self.B, 16, K, max_nprobe, mode=m) for m in ("prune", "full"))
-        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
-        self.max_nprobe = max_nprobe
-
-    def run(self, nprobe, delta_d, mode, stats=False, first_wave=1):
-        self.np.fill_(nprobe)
-        if stats:
-            self.stats.zero_()
-        self.G.dade_search(self.idx, self.q, self.k, self.np, delta_d, self.ids, self.d, max_K=self.K,
-                           max_nprobe=nprobe, mode=mode, status=self.status, first_wave=first_wave,
-                           stats=self.stats if stats else None, workspace=self.ws)
-
-    def result(self):
-        self.torch.cuda.synchronize()
-        assert int(self.status.item()) == 0, f"device status {int(self.status.item())}"
-        return self.ids.view(self.B, self.K).cpu().numpy()
-
-    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1):
-        torch = self.torch
-        for _ in range(warmup):
-            self.run(nprobe, delta_d, mode, first_wave=first_wave)
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        for e0, e1 in evs:
-            e0.record()
-            self.run(nprobe, delta_d, mode, first_wave=first_wave)
-            e1.record()
-        t1.record()
-        torch.cuda.synchronize()
-        per = [a.elapsed_time(b) for a, b in evs]
-        return t0.elapsed_time(t1), per
 
 
 def n_waves(nprobe, first_wave=1):
@@ -330,8 +273,9 @@ def main():
     gt = ground_truth(X, Q, 10)
     setup_s = time.perf_counter() - t_setup
 
+    from paper_2404_16322_gb300 import autotune, serving
     maxp = min(max(NPROBES), nlist)
-    run = Runner(G, idx, Q, K, maxp)
+    run = autotune.Bench(G, idx, Q, K, maxp, DELTAS)
     if args.profile:
         vals = [int(x) for x in args.profile.split(",")]
         npb, dd = vals[0], vals[1]
@@ -345,29 +289,13 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         ids = run.result()
-        print(json.dumps({"profile": args.profile, "recall@10": recall_at(ids, gt), "steps": args.steps,
+        print(json.dumps({"profile": args.profile, "recall@10": autotune.recall_at(ids, gt, 10), "steps": args.steps,
                           "launches_per_step": 12 + 2 * n_waves(npb, fw), "setup_s": time.perf_counter() - t_setup}))
         return
-    # --- sweep: recall per (mode, delta_d, nprobe); short timing of each
-    sweep = []
-    for mode, dds in (("full", [0]), ("prune", DELTAS)):
-        for dd in dds:
-            for fw in FIRST_WAVES:
-                for npb in [p for p in NPROBES if p <= maxp]:
-                    run.run(npb, dd, mode, first_wave=fw)
-                    rec = recall_at(run.result(), gt)
-                    total, per = run.time(npb, dd, mode, 5, 2, first_wave=fw)
-                    sweep.append(dict(mode=mode, delta_d=dd, first_wave=fw, nprobe=npb, recall=rec,
-                                      ms=float(np.median(per))))
-                    if rec >= TARGET_RECALL + 0.02:
-                        break
-
-    def best(mode):
-        ok = [s for s in sweep if s["mode"] == mode and s["recall"] >= TARGET_RECALL]
-        return min(ok, key=lambda s: s["ms"]) if ok else max((s for s in sweep if s["mode"] == mode),
-                                                              key=lambda s: s["recall"])
-
-    bd, bf = best("prune"), best("full")
+    nps = [p for p in NPROBES if p <= maxp]
+    bd, tried_p = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, FIRST_WAVES, nps, mode="prune")
+    bf, tried_f = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, FIRST_WAVES, nps, mode="full")
+    sweep = tried_f + tried_p
 
     # --- timed region: exactly K steps of the chosen configuration
     if world > 1:
@@ -453,6 +381,22 @@ def main():
     d2h = run.B * K * (8 + 4)
     assert np.array_equal(ids_h.view(run.B, K).numpy()[:, :10], run.result()[:, :10])
 
+    # --- serving: Poisson arrivals of single-query requests (K in {1, 10, 100})
+    serve_out = []
+    if not args.no_serving:
+        srv = serving.Server(G, idx, bd["delta_d"], max_K=K, max_nprobe=bd["nprobe"],
+                             buckets=(64, 256, 1024, 4096), slots=3, first_wave=bd["first_wave"])
+        rng = np.random.default_rng(6)
+        for rate in SERVING_RATES:
+            n_req = int(min(200_000, max(20_000, rate * 0.25)))
+            arr = serving.poisson_arrivals(n_req, rate, seed=6)
+            ks = rng.choice([1, 10, 100], n_req)
+            qi = np.arange(n_req) % len(Q)
+            _, _, _, o = srv.serve_arrays(Q[qi], ks, np.full(n_req, bd["nprobe"]), arr, max_batch=4096)
+            o["offered_rate"] = rate
+            serve_out.append(o)
+        del srv
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K, args.cpu_sample_queries)
@@ -472,6 +416,7 @@ def main():
         "bytes_per_query": {"prune": dade_bytes, "full_scan": full_bytes, "ratio": dade_bytes / full_bytes},
         "scanned_dims_ratio": scan_ratio,
         "latency_ms": {"batch_p50": float(np.percentile(per, 50)), "batch_p99": float(np.percentile(per, 99))},
+        "serving": serve_out,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "wave_scan_kernel", "per_launch_ms": per_launch_ms,

@@ -155,7 +155,9 @@ dade_status dade_get_correction(const dade_index* idx, int32_t delta_d, float* m
  * dade_search -- batched AKNN search on one stream.
  *
  * Q_dev: B x D FP32 queries.  K_dev[B], nprobe_dev[B]: per-query K
- * (1..opts->max_K) and nprobe (1..min(opts->max_nprobe, nlist)).
+ * (1..opts->max_K) and nprobe (1..min(opts->max_nprobe, nlist)); a query
+ * with K = 0 or nprobe = 0 is an inactive slot (no work, padded output), so
+ * a fixed-capacity batch can carry fewer live queries.
  * Pipeline, all on cuda_stream (a cudaStream_t; NULL = legacy default):
  *  1. q' = R (q - mean) for every query (Section IV-A x_D = R x).
  *  2. squared distance of q' to every centroid; the nprobe nearest, ordered

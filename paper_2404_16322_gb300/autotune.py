@@ -1,0 +1,123 @@
+"""Autotuner for dade_search: picks the step width Delta_d, the first wave
+size and nprobe that give the highest throughput at a recall target.
+
+For every (Delta_d, first wave) it raises nprobe until recall@k against the
+given ground truth reaches the target, times that configuration (CUDA
+events, median of `reps` batches after `warmup`), and keeps the fastest.
+The full-dimension scan (mode "full") is tuned the same way as a reference.
+Results can be cached in a JSON file keyed by the index shape and the GPU.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+
+
+def recall_at(ids: np.ndarray, gt: np.ndarray, k: int) -> float:
+    hit = 0
+    for b in range(len(gt)):
+        hit += len(set(ids[b, :k].tolist()) & set(gt[b, :k].tolist()))
+    return hit / (k * len(gt))
+
+
+class Bench:
+    """Device-resident batch for repeated dade_search calls."""
+
+    def __init__(self, G, idx, Q, K: int, max_nprobe: int, deltas=(8, 16, 32)):
+        import torch
+        self.G, self.idx, self.torch = G, idx, torch
+        dev = torch.device("cuda")
+        self.B, self.K = len(Q), K
+        self.q = torch.from_numpy(np.ascontiguousarray(Q, np.float32)).to(dev)
+        self.k = torch.full((self.B,), K, dtype=torch.int32, device=dev)
+        self.np = torch.zeros(self.B, dtype=torch.int32, device=dev)
+        self.ids = torch.empty(self.B * K, dtype=torch.int64, device=dev)
+        self.d = torch.empty(self.B * K, dtype=torch.float32, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.stats = torch.zeros((self.B, 4), dtype=torch.int64, device=dev)
+        ws = max(G.dade_search_workspace_size(idx, self.B, dd, K, max_nprobe, mode=m, first_wave=1)
+                 for m in ("prune", "full") for dd in deltas)
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+
+    def run(self, nprobe, delta_d, mode, first_wave=1, stats=False):
+        self.np.fill_(nprobe)
+        if stats:
+            self.stats.zero_()
+        self.G.dade_search(self.idx, self.q, self.k, self.np, delta_d, self.ids, self.d, max_K=self.K,
+                           max_nprobe=nprobe, mode=mode, status=self.status, first_wave=first_wave,
+                           stats=self.stats if stats else None, workspace=self.ws)
+
+    def result(self) -> np.ndarray:
+        self.torch.cuda.synchronize()
+        st = int(self.status.item())
+        if st:
+            raise RuntimeError(f"device status {st}")
+        return self.ids.view(self.B, self.K).cpu().numpy()
+
+    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1):
+        """Returns (total ms, per-step ms list), CUDA events on the stream."""
+        torch = self.torch
+        for _ in range(warmup):
+            self.run(nprobe, delta_d, mode, first_wave)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for e0, e1 in evs:
+            e0.record()
+            self.run(nprobe, delta_d, mode, first_wave)
+            e1.record()
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in evs]
+
+
+def cache_key(G, idx, K: int, target: float, mode: str) -> str:
+    import torch
+    info = G.dade_index_info_get(idx)
+    sizes = G.dade_index_list_sizes(idx)
+    h = hashlib.sha256(sizes.tobytes()).hexdigest()[:12]
+    return (f"{torch.cuda.get_device_name()}|N{info['N']}|D{info['D']}|nl{info['nlist']}|dt{info['dtype']}"
+            f"|{h}|K{K}|r{target}|{mode}")
+
+
+def autotune(bench: Bench, gt: np.ndarray, target: float = 0.95, k_recall: int = 10,
+             deltas=(8, 16, 32), first_waves=(1, 4), nprobes=(8, 16, 24, 32, 48, 64, 96, 128, 192, 256),
+             reps: int = 5, warmup: int = 2, mode: str = "prune", margin: float = 0.02):
+    """Returns (best configuration, every configuration tried)."""
+    tried = []
+    dds = deltas if mode == "prune" else (0,)
+    for dd in dds:
+        for fw in first_waves:
+            for npb in nprobes:
+                bench.run(npb, dd, mode, fw)
+                rec = recall_at(bench.result(), gt, k_recall)
+                _, per = bench.time(npb, dd, mode, reps, warmup, fw)
+                tried.append(dict(mode=mode, delta_d=dd, first_wave=fw, nprobe=npb, recall=rec,
+                                  ms=float(np.median(per))))
+                if rec >= target + margin:
+                    break
+    ok = [t for t in tried if t["recall"] >= target]
+    best = min(ok, key=lambda t: t["ms"]) if ok else max(tried, key=lambda t: t["recall"])
+    return best, tried
+
+
+def autotune_cached(G, idx, bench: Bench, gt, cache_path: str | None = None, **kw):
+    """autotune() with a JSON cache of the chosen configuration."""
+    key = cache_key(G, idx, bench.K, kw.get("target", 0.95), kw.get("mode", "prune"))
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    if key in cache:
+        return cache[key], []
+    best, tried = autotune(bench, gt, **kw)
+    if cache_path:
+        cache[key] = best
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return best, tried

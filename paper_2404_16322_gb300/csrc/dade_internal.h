@@ -123,7 +123,7 @@ cudaError_t launch_gemm_store(int op, const float* A, int64_t lda, const float* 
 cudaError_t launch_gemm_argmin(const float* A, int64_t lda, const float* B, int64_t ldb,
                                unsigned long long* out, int64_t M, int64_t N, int Kd,
                                cudaStream_t st);
-// Tensor-core (tcgen05, 3xTF32) GEMMs: C = (A - sub) B^T, and
+// Tensor-core (tcgen05, split-TF32) GEMMs: C = (A - sub) B^T, and
 // C = max(0, an + bn - 2 A B^T) (squared distances from norms).
 cudaError_t launch_tc_dot(const float* A, int64_t lda, const float* sub, const float* B, int64_t ldb,
                           float* C, int64_t ldc, int64_t M, int64_t N, int Kd, int32_t* status,

@@ -773,7 +773,10 @@ __global__ void count_kernel(IndexView ix, WaveView wv) {
     int np = wv.nprobe[b];
     const int K = wv.K[b];
     if (np < 1 || np > wv.P || K < 1 || K > wv.Kmax) {
-        atomicCAS(wv.status, 0, (int)DADE_EINVAL);
+        // nprobe = 0 or K = 0 marks an inactive query slot (no work, padded
+        // output); anything else out of range is an error
+        if (!((np == 0 && K >= 0 && K <= wv.Kmax) || (K == 0 && np >= 0 && np <= wv.P)))
+            atomicCAS(wv.status, 0, (int)DADE_EINVAL);
         return;
     }
     for (int r = 0; r < np; ++r) {

@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(NT) select_kernel(const float* __restrict__ sc
     const float* row = STAGED ? srow : grow;
     int np = nprobe[b];
     if (np < 1 || np > P || np > n) {
-        if (tid == 0 && status) atomicCAS(status, 0, (int)DADE_EINVAL);
+        // nprobe = 0 marks an inactive query slot; other values are errors
+        if (tid == 0 && status && np != 0) atomicCAS(status, 0, (int)DADE_EINVAL);
         for (int r = tid; r < P; r += NT) out[r] = -1;
         return;
     }

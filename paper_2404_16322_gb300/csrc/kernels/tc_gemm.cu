@@ -5,15 +5,18 @@
 //
 // C[M x N] = A[M x K] . B[N x K]^T with both operands K-major (rows of A and
 // of B are contiguous in K).  One CTA of 128 threads computes a 128 x 128 tile:
-//  - K is consumed in blocks of 32; the threads load a block of A and B,
-//    split every value into two TF32 parts (hi = RNE to TF32, lo = RNE of the
-//    remainder) and store them in shared memory in the canonical K-major
+//  - K is consumed in blocks of 32; the threads load a block of A and B and
+//    split every value into TF32 parts (round to nearest): A into three,
+//    a = hi + mid + lo exactly (11 + 11 + the last <= 3 bits), B into two,
+//    b ~ hi + mid; the parts go to shared memory in the canonical K-major
 //    layout without swizzle: 8-row x 16-byte core matrices, core matrices
 //    adjacent in K 128 bytes apart (LBO), 8-row groups 1024 bytes apart (SBO);
-//  - one thread issues, per K = 8 step, three tcgen05.mma kind::tf32
-//    (hi.hi + hi.lo + lo.hi, "3xTF32": about 21 bits of the product) into an
-//    FP32 accumulator of 128 lanes x 128 columns in tensor memory, then
-//    tcgen05.commit to an mbarrier that the threads wait on (bounded);
+//  - one thread issues, per K = 8 step, four tcgen05.mma kind::tf32
+//    (Ah.Bh + Ah.Bm + Am.Bh + Al.Bh) into an FP32 accumulator of 128 lanes
+//    x 128 columns in tensor memory -- every product of B's parts with A is
+//    kept except terms below 2^-22 of the result, and a product by an exact
+//    TF32 b (such as a permutation matrix) is exact -- then tcgen05.commit
+//    to an mbarrier that the threads wait on (bounded);
 //  - the 4 warps read their 32 accumulator lanes (rows) with
 //    tcgen05.ld.32x32b and apply the epilogue.
 #include "../dade_internal.h"
@@ -87,7 +90,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, int32_t
 enum Epi { EPI_STORE = 0, EPI_L2 = 1 };
 
 // Loads the 128 x 32 K-block at (row0, k0) of a row-major operand and stores
-// its TF32 hi and lo parts.  VEC: float4 loads (rows 16-byte aligned, K a
+// its TF32 parts: hi, mid and (when lo != nullptr) lo = the exact rest.  VEC: float4 loads (rows 16-byte aligned, K a
 // multiple of 4); element f of the 1024 float4s of the block maps to row
 // (f / 64) * 8 + f % 8 and float4 column (f / 8) % 8, so the 8 lanes of a
 // quarter warp store to 8 different rows of one core-matrix column (distinct
@@ -95,7 +98,7 @@ enum Epi { EPI_STORE = 0, EPI_L2 = 1 };
 template <bool VEC>
 __device__ __forceinline__ void load_split(const float* __restrict__ X, int64_t ld, const float* __restrict__ sub,
                                            int64_t row0, int64_t nrows, int k0, int Kd,
-                                           unsigned char* hi, unsigned char* lo, int tid) {
+                                           unsigned char* hi, unsigned char* mid, unsigned char* lo, int tid) {
     if (VEC) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -111,12 +114,17 @@ __device__ __forceinline__ void load_split(const float* __restrict__ X, int64_t 
                     v.x -= m.x; v.y -= m.y; v.z -= m.z; v.w -= m.w;
                 }
             }
-            float4 h, l;
+            float4 h, m;
             h.x = to_tf32(v.x); h.y = to_tf32(v.y); h.z = to_tf32(v.z); h.w = to_tf32(v.w);
-            l.x = to_tf32(v.x - h.x); l.y = to_tf32(v.y - h.y); l.z = to_tf32(v.z - h.z); l.w = to_tf32(v.w - h.w);
+            m.x = to_tf32(v.x - h.x); m.y = to_tf32(v.y - h.y); m.z = to_tf32(v.z - h.z); m.w = to_tf32(v.w - h.w);
             const uint32_t o = tile_off(r, c4 * 4);
             *reinterpret_cast<float4*>(hi + o) = h;
-            *reinterpret_cast<float4*>(lo + o) = l;
+            *reinterpret_cast<float4*>(mid + o) = m;
+            if (lo) {
+                float4 l;
+                l.x = (v.x - h.x) - m.x; l.y = (v.y - h.y) - m.y; l.z = (v.z - h.z) - m.z; l.w = (v.w - h.w) - m.w;
+                *reinterpret_cast<float4*>(lo + o) = l;
+            }
         }
     } else {
         for (int e = tid; e < TM * TKB; e += 128) {
@@ -129,9 +137,11 @@ __device__ __forceinline__ void load_split(const float* __restrict__ X, int64_t 
                 if (sub) v -= sub[gk];
             }
             const float h = to_tf32(v);
+            const float m = to_tf32(v - h);
             const uint32_t o = tile_off(r, j);
             *reinterpret_cast<float*>(hi + o) = h;
-            *reinterpret_cast<float*>(lo + o) = to_tf32(v - h);
+            *reinterpret_cast<float*>(mid + o) = m;
+            if (lo) *reinterpret_cast<float*>(lo + o) = (v - h) - m;
         }
     }
 }
@@ -152,9 +162,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
     __shared__ int s_ok;
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~uintptr_t(1023));
     unsigned char* a_hi = base;
-    unsigned char* a_lo = base + TILE_BYTES;
-    unsigned char* b_hi = base + 2 * TILE_BYTES;
-    unsigned char* b_lo = base + 3 * TILE_BYTES;
+    unsigned char* a_md = base + TILE_BYTES;
+    unsigned char* a_lo = base + 2 * TILE_BYTES;
+    unsigned char* b_hi = base + 3 * TILE_BYTES;
+    unsigned char* b_md = base + 4 * TILE_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t m0 = (int64_t)blockIdx.x * TM, n0 = (int64_t)blockIdx.y * TN;
 
@@ -178,20 +189,22 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
     const int nkb = (Kd + TKB - 1) / TKB;
     for (int kb = 0; kb < nkb; ++kb) {
         const int k0 = kb * TKB;
-        load_split<VA>(A, lda, sub, m0, M, k0, Kd, a_hi, a_lo, tid);
-        load_split<VB>(Bm, ldb, nullptr, n0, N, k0, Kd, b_hi, b_lo, tid);
+        load_split<VA>(A, lda, sub, m0, M, k0, Kd, a_hi, a_md, a_lo, tid);
+        load_split<VB>(Bm, ldb, nullptr, n0, N, k0, Kd, b_hi, b_md, nullptr, tid);
         // make the generic-proxy stores visible to the tensor core
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+            const uint32_t ah = smem_u32(a_hi), am = smem_u32(a_md), al = smem_u32(a_lo);
+            const uint32_t bh = smem_u32(b_hi), bm = smem_u32(b_md);
 #pragma unroll
             for (int s = 0; s < TKB / 8; ++s) {
                 const uint32_t step = (uint32_t)s * 2 * LBO;  // K = 8 = two core matrices
                 const uint32_t first = (kb == 0 && s == 0) ? 0u : 1u;
                 mma_tf32(tmem, smem_desc(ah + step), smem_desc(bh + step), first);
-                mma_tf32(tmem, smem_desc(ah + step), smem_desc(bl + step), 1u);
+                mma_tf32(tmem, smem_desc(ah + step), smem_desc(bm + step), 1u);
+                mma_tf32(tmem, smem_desc(am + step), smem_desc(bh + step), 1u);
                 mma_tf32(tmem, smem_desc(al + step), smem_desc(bh + step), 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -270,7 +283,7 @@ __global__ void row_norms_kernel(const float* __restrict__ X, int64_t ld, int64_
     out[r] = s;
 }
 
-constexpr int kSmem = 4 * TILE_BYTES + 1024;  // four operand parts + alignment slack
+constexpr int kSmem = 5 * TILE_BYTES + 1024;  // five operand parts + alignment slack
 
 template <int EPI, bool VA, bool VB>
 cudaError_t launch_v(const float* A, int64_t lda, const float* sub, const float* B, int64_t ldb,

@@ -1,0 +1,113 @@
+"""GPU parity on the shapes of the other workloads, and the full-size SIFT
+-shaped workload in the benchmark's launch configuration.
+
+* GIST-shaped (D = 960, strong spectral decay, BF16 slabs, Delta_d = 32) and
+  vMF-shaped (D = 96, L2-normalised, FP8 slabs, uneven K and nprobe) at
+  sizes the oracle finishes in seconds, with the oracle's rotation, buckets
+  and tables on both sides (pre-rotated: strict id parity).
+* SIFT-shaped 1M x 128, 10k queries, nprobe 64, K 100, Delta_d 16, first
+  wave 4 -- the configuration bench.py times -- checked on sampled queries
+  through properties that hold at any size: returned distances are the exact
+  distances of the returned ids (integer data: bit-exact in FP32), results
+  are sorted and unique, the pruned search returns every candidate of the
+  full scan that beats the full scan's K-th, and recall@10 against brute
+  force on the sample."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import search
+
+from . import gpu_helpers as H
+from . import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2404_16322_gb300 import build
+    build.build()
+    import paper_2404_16322_gb300 as G
+    return G
+
+
+def _oracle_search(inp, Q, K, nprobe, delta_d, amb="exact"):
+    oidx = inp["oidx"]
+    P = int(np.max(nprobe))
+    pr = oidx.probe(oidx.rotate_queries(Q), P)
+    ids, d, st = search.search(oidx, Q, pr, nprobe, K, delta_d, inp["m1"].astype(np.float64),
+                               inp["beta"].astype(np.float64), amb=H.AMB[amb])
+    return ids, d, st, pr
+
+
+def test_gist_shaped_bf16_slabs(G):
+    spec = synth.MixtureSpec(D=960, n_comp=32, alpha=1.3)
+    X, Q, T = spec.sample(20_000, 1), spec.sample(60, 2), spec.sample(300, 3)
+    inp = H.oracle_inputs(X, T, 64, iters=4, K=100, nprobe=8, delta_d=32, dtype="bf16", n_train=300,
+                          prerotate=True)
+    idx = H.build_gpu(G, None, inp, 64, dtype="bf16", delta_d=32)
+    Qr = inp["rot"](Q)
+    ids, d, st, pr = _oracle_search(inp, Qr, 100, 8, 32)
+    out = H.gpu_search(G, idx, Qr, 100, 8, 32, probe_in=pr, want=("stats",))
+    parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, 100, amb=st[:, 4], min_strict=0.9)
+    un = st[:, 4] == 0
+    assert np.array_equal(out["stats"][un], st[un, :4])
+    assert st[:, 1].sum() > 0
+    idx.close()
+
+
+def test_vmf_shaped_fp8_slabs_uneven_requests(G):
+    spec = synth.VmfSpec(D=96, n_comp=64)
+    X, Q, T = spec.sample(20_000, 1), spec.sample(120, 2), spec.sample(400, 3)
+    inp = H.oracle_inputs(X, T, 64, iters=4, K=50, nprobe=12, delta_d=16, dtype="fp8", n_train=400,
+                          prerotate=True)
+    idx = H.build_gpu(G, None, inp, 64, dtype="fp8", delta_d=16)
+    Qr = inp["rot"](Q)
+    rng = np.random.default_rng(9)
+    K = rng.integers(1, 101, len(Q)).astype(np.int32)
+    npb = rng.integers(8, 17, len(Q)).astype(np.int32)
+    ids, d, st, pr = _oracle_search(inp, Qr, K, npb, 16)
+    out = H.gpu_search(G, idx, Qr, K, npb, 16, probe_in=pr, max_K=100, max_nprobe=16)
+    parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, K, amb=st[:, 4], min_strict=0.9)
+    idx.close()
+
+
+@pytest.fixture(scope="module")
+def sift_full(G):
+    X, Q, T, cfg = synth.workload("sift1m")
+    mean, R, _ = G.dade_train_rotation(X, sample_n=1_000_000, seed=1)
+    idx = G.ivf_build(X, mean, R, cfg["nlist"], kmeans_iters=10, seed=1, dtype="f32")
+    G.dade_fit_correction(idx, T, 100, 64, 16, target_recall=0.995, seed=1)
+    yield dict(X=X, Q=Q, idx=idx)
+    idx.close()
+
+
+def test_sift_full_size_in_the_benchmark_configuration(G, sift_full):
+    X, Q, idx = sift_full["X"], sift_full["Q"], sift_full["idx"]
+    pr = H.gpu_search(G, idx, Q, 100, 64, 16, first_wave=4, want=("stats",))
+    fu = H.gpu_search(G, idx, Q, 100, 64, 0, mode="full", first_wave=4)
+    assert pr["status"] == 0 and fu["status"] == 0
+    sample = np.random.default_rng(5).choice(len(Q), 24, replace=False)
+    Xd = X.astype(np.float64)
+    hits = []
+    for b in sample:
+        q = Q[b].astype(np.float64)
+        for out in (pr, fu):
+            ids, dd = out["ids"][b], out["dists"][b]
+            assert np.all(ids >= 0) and len(set(ids.tolist())) == 100
+            ex = ((Xd[ids] - q) ** 2).sum(1)
+            assert np.array_equal(dd.astype(np.float64), ex)  # integer data: exact
+            assert np.all(np.diff(dd) >= 0)
+        # pruning removes candidates only: whatever the full scan keeps below
+        # its own K-th entry is found by the pruned search too, unless pruned
+        kth = (fu["dists"][b][-1], fu["ids"][b][-1])
+        better_p = {i for i, x in zip(pr["ids"][b], pr["dists"][b]) if (x, i) < kth}
+        assert better_p <= set(fu["ids"][b].tolist())
+        # brute-force recall@10 of the pruned search on the sample
+        dall = ((Xd - q) ** 2).sum(1)
+        gt = np.lexsort((np.arange(len(X)), dall))[:10]
+        hits.append(len(set(gt.tolist()) & set(pr["ids"][b][:10].tolist())) / 10)
+    assert np.mean(hits) >= 0.9
+    st = pr["stats"]
+    assert st[:, 1].sum() > 0.5 * st[:, 0].sum()  # most candidates are pruned
