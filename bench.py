@@ -175,7 +175,7 @@ def peaks():
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, seed_queries=None, steps=1):
+def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave=1):
     """The oracle (plain FP64 C loop, all host threads) on a bounded sample of
     the workload: a 100k-vector instance of the same mixture with the same
     bucket size (nlist 410, ~244 vectors per bucket), the same nprobe, K and
@@ -207,12 +207,12 @@ def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, seed_queries=None, 
         q = Q[s * n_queries:(s + 1) * n_queries]
         t0 = time.perf_counter()
         pr = oidx.probe(oidx.rotate_queries(q), nprobe)  # probing is part of the query
-        search.search(oidx, q, pr, nprobe, K, delta_d, m1, beta)
+        search.search(oidx, q, pr, nprobe, K, delta_d, m1, beta, first_wave=first_wave)
         times.append(time.perf_counter() - t0)
     qps = n_queries / float(np.median(times))
     sample = (f"oracle FP64 C loop on {n_queries} queries per step against a {N}-vector SIFT-shaped instance "
               f"(nlist {nlist}, ~{N // nlist}/bucket like the full 1M/4096), nprobe {nprobe}, K {K}, "
-              f"delta_d {delta_d}; probing included")
+              f"delta_d {delta_d}, first wave {first_wave}; probing included")
     return dict(value=qps, unit="queries/s", cores=threads, kind="oracle", sample=sample), times
 
 
@@ -224,17 +224,17 @@ def reference_arm(args):
     cfg = dict(synth.WORKLOADS["sift1m"])
     n_q = 40
     t0 = time.perf_counter()
-    cb, times = oracle_baseline(cfg, 64, 16, 100, n_q, steps=args.steps + args.warmup)
+    cb, times = oracle_baseline(cfg, 64, 16, 100, n_q, steps=args.steps + args.warmup, first_wave=4)
     wall = time.perf_counter() - t0
     timed = times[args.warmup:] or times
     ms = 1000.0 * float(np.mean(timed))
     value = n_q / (ms / 1000.0)
     cb["value"] = value
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "sift1m-shaped sample (see cpu_baseline.sample)", "nprobe": 64, "K": 100,
-                       "delta_d": 16},
+                       "delta_d": 16, "first_wave": 4},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
@@ -399,7 +399,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K, args.cpu_sample_queries)
+        cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K, args.cpu_sample_queries,
+                                 first_wave=bd["first_wave"])
 
     launches = 12 + 2 * n_waves(bd["nprobe"], bd["first_wave"])
     line = {
