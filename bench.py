@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 TARGET_RECALL = 0.95
 NPROBES = [8, 16, 24, 32, 48, 64, 96, 128, 192, 256]
 DELTAS = [8, 16, 32]
-FIRST_WAVES = [1, 4]
+FIRST_WAVES = [1, 2, 4, 8]
 SERVING_RATES = [200_000, 1_000_000, 3_000_000]
 METRIC = "QPS at recall@10>=0.95 (estimate-and-prune IVF search, SIFT-shaped 1M x 128, nlist 4096, K 100)"
 

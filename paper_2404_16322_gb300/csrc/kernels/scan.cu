@@ -27,6 +27,7 @@
 #include <cuda_fp8.h>
 
 #include "scan.cuh"
+#include "warp_select.cuh"
 
 namespace dade {
 namespace {
@@ -576,56 +577,10 @@ __device__ __forceinline__ int count_before(const float* d, const long long* id,
     return lo;
 }
 
-// The k-th smallest (1-based) 32-bit pattern of the non-negative floats
-// v[0, n), by an MSD radix select over 8-bit digits (warp-wide).
-__device__ uint32_t warp_kth_bits(const float* v, int n, int k, int* hist, int lane) {
-    uint32_t prefix = 0, mask = 0;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int b = lane; b < 256; b += 32) hist[b] = 0;
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-            const uint32_t key = __float_as_uint(v[i]);
-            if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
-        }
-        __syncwarp();
-        // lane j owns bins [8j, 8j + 8): find the bin where the count reaches k
-        int h[8], s = 0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            h[u] = hist[lane * 8 + u];
-            s += h[u];
-        }
-        int incl = s;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int o = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += o;
-        }
-        const int excl = incl - s;
-        const unsigned hit = __ballot_sync(0xffffffffu, excl < k && incl >= k);
-        const int src = __ffs(hit) - 1;
-        int digit = 0, below = 0;
-        if (lane == src) {
-            int cum = excl;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (cum + h[u] >= k) {
-                    digit = lane * 8 + u;
-                    break;
-                }
-                cum += h[u];
-            }
-            below = cum;
-        }
-        digit = __shfl_sync(0xffffffffu, digit, src);
-        below = __shfl_sync(0xffffffffu, below, src);
-        k -= below;
-        prefix |= (uint32_t)digit << shift;
-        mask |= 255u << shift;
-        __syncwarp();
-    }
-    return prefix;
-}
+struct CandKeys {
+    const float* d;
+    __device__ uint32_t operator()(int i) const { return __float_as_uint(d[i]); }
+};
 
 __device__ __forceinline__ void warp_sort(float* bd, long long* bi, int M, int lane) {
     for (int size = 2; size <= M; size <<= 1) {
@@ -723,7 +678,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(IndexView ix, W
         ai[i] = ti[i];
     }
     // candidates above the K-th smallest of this wave cannot enter the top-K
-    const uint32_t thr = cnt > max(K, kMergeChunk) ? warp_kth_bits(cd, cnt, K, s_hist[warp], lane) : 0xffffffffu;
+    const uint32_t thr = cnt > max(K, kMergeChunk) ? warp_kth_key(CandKeys{cd}, cnt, K, s_hist[warp], lane) : 0xffffffffu;
     int m = 0;  // filled part of the chunk
     for (int base = 0; base < cnt; base += 32) {
         const int i = base + lane;
