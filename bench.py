@@ -35,7 +35,6 @@ sys.path.insert(0, ROOT)
 TARGET_RECALL = 0.95
 NPROBES = [8, 16, 24, 32, 48, 64, 96, 128, 192, 256]
 DELTAS = [8, 16, 32]
-FIRST_WAVES = [1, 2, 4, 8]
 SERVING_RATES = [200_000, 1_000_000, 3_000_000]
 METRIC = "QPS at recall@10>=0.95 (estimate-and-prune IVF search, SIFT-shaped 1M x 128, nlist 4096, K 100)"
 
@@ -52,7 +51,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-sample-queries", type=int, default=400)
     ap.add_argument("--profile", default=None,
-                    help="NPROBE,DELTA_D[,FIRST_WAVE]: skip the sweep and baselines; run W + K steps of that "
+                    help="NPROBE,DELTA_D[,FIRST_WAVE[,GROWTH]]: skip the sweep and baselines; run W + K steps of that "
                          "configuration inside the NVTX range 'dade_timed' (for ncu captures)")
     return ap.parse_args()
 
@@ -137,10 +136,10 @@ def ground_truth(X, Q, k=10, chunk=1024):
     return out
 
 
-def n_waves(nprobe, first_wave=1):
+def n_waves(nprobe, first_wave=1, growth=1):
     b, w = 0, 0
     while b < nprobe:
-        b = first_wave if b == 0 else 2 * b
+        b = first_wave if b == 0 else b << min(max(growth, 1), 40)
         w += 1
     return w
 
@@ -175,7 +174,7 @@ def peaks():
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave=1):
+def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave=1, growth=1):
     """The oracle (plain FP64 C loop, all host threads) on a bounded sample of
     the workload: a 100k-vector instance of the same mixture with the same
     bucket size (nlist 410, ~244 vectors per bucket), the same nprobe, K and
@@ -207,12 +206,12 @@ def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave
         q = Q[s * n_queries:(s + 1) * n_queries]
         t0 = time.perf_counter()
         pr = oidx.probe(oidx.rotate_queries(q), nprobe)  # probing is part of the query
-        search.search(oidx, q, pr, nprobe, K, delta_d, m1, beta, first_wave=first_wave)
+        search.search(oidx, q, pr, nprobe, K, delta_d, m1, beta, first_wave=first_wave, growth=growth)
         times.append(time.perf_counter() - t0)
     qps = n_queries / float(np.median(times))
     sample = (f"oracle FP64 C loop on {n_queries} queries per step against a {N}-vector SIFT-shaped instance "
               f"(nlist {nlist}, ~{N // nlist}/bucket like the full 1M/4096), nprobe {nprobe}, K {K}, "
-              f"delta_d {delta_d}, first wave {first_wave}; probing included")
+              f"delta_d {delta_d}, first wave {first_wave}, growth 2^{growth}; probing included")
     return dict(value=qps, unit="queries/s", cores=threads, kind="oracle", sample=sample), times
 
 
@@ -280,21 +279,22 @@ def main():
         vals = [int(x) for x in args.profile.split(",")]
         npb, dd = vals[0], vals[1]
         fw = vals[2] if len(vals) > 2 else 1
+        gw = vals[3] if len(vals) > 3 else 1
         for _ in range(args.warmup):
-            run.run(npb, dd, "prune", first_wave=fw)
+            run.run(npb, dd, "prune", first_wave=fw, growth=gw)
         run.result()
         torch.cuda.nvtx.range_push("dade_timed")
         for _ in range(args.steps):
-            run.run(npb, dd, "prune", first_wave=fw)
+            run.run(npb, dd, "prune", first_wave=fw, growth=gw)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         ids = run.result()
         print(json.dumps({"profile": args.profile, "recall@10": autotune.recall_at(ids, gt, 10), "steps": args.steps,
-                          "launches_per_step": 12 + 2 * n_waves(npb, fw), "setup_s": time.perf_counter() - t_setup}))
+                          "launches_per_step": 12 + 2 * n_waves(npb, fw, gw), "setup_s": time.perf_counter() - t_setup}))
         return
     nps = [p for p in NPROBES if p <= maxp]
-    bd, tried_p = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, FIRST_WAVES, nps, mode="prune")
-    bf, tried_f = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, FIRST_WAVES, nps, mode="full")
+    bd, tried_p = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, nprobes=nps, mode="prune")
+    bf, tried_f = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, nprobes=nps, mode="full")
     sweep = tried_f + tried_p
 
     # --- timed region: exactly K steps of the chosen configuration
@@ -303,12 +303,13 @@ def main():
         dist.barrier()
     sampler = ClockSampler(local)
     for _ in range(args.warmup):
-        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"])
+        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"])
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms, per = run.time(bd["nprobe"], bd["delta_d"], "prune", args.steps, 0, first_wave=bd["first_wave"])
+    total_ms, per = run.time(bd["nprobe"], bd["delta_d"], "prune", args.steps, 0, first_wave=bd["first_wave"],
+                             growth=bd["growth"])
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:
@@ -319,14 +320,15 @@ def main():
     value = world * run.B / (ms_step / 1000.0)
 
     # --- full-scan reference point on the same GPU, same timing
-    f_total, f_per = run.time(bf["nprobe"], 0, "full", args.steps, args.warmup, first_wave=bf["first_wave"])
+    f_total, f_per = run.time(bf["nprobe"], 0, "full", args.steps, args.warmup, first_wave=bf["first_wave"],
+                              growth=bf["growth"])
     full_qps = run.B / (f_total / args.steps / 1000.0)
 
     # --- stage timing of the dominant kernel (the refinement scan)
     G.dade_stage_timing(True)
     G.dade_stage_timing_read()
     for _ in range(args.steps):
-        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"])
+        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"])
     scan_ms, scan_launches, scan_bytes = G.dade_stage_timing_read()
     G.dade_stage_timing(False)
     per_launch_ms = scan_ms / max(1, scan_launches)
@@ -337,13 +339,13 @@ def main():
     traffic = traffic_from_profiles(khash)
 
     # --- work accounting (bytes per query) for both modes
-    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True, first_wave=bd["first_wave"])
+    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True, first_wave=bd["first_wave"], growth=bd["growth"])
     run.result()
     st = run.stats.cpu().numpy()
     S = G.n_steps(128, bd["delta_d"])
     pruned_dims = st[:, 3] - st[:, 2] * 128
     dade_bytes = (pruned_dims * 4 + st[:, 2] * ((S - 1) * bd["delta_d"] * 4 + 128 * 4)).sum() / run.B
-    run.run(bf["nprobe"], 0, "full", stats=True, first_wave=bf["first_wave"])
+    run.run(bf["nprobe"], 0, "full", stats=True, first_wave=bf["first_wave"], growth=bf["growth"])
     run.result()
     stf = run.stats.cpu().numpy()
     full_bytes = (stf[:, 0] * 128 * 4).sum() / run.B
@@ -362,7 +364,7 @@ def main():
         run.np.copy_(n_h, non_blocking=True)
         G.dade_search(idx, run.q, run.k, run.np, bd["delta_d"], run.ids, run.d, max_K=K,
                       max_nprobe=bd["nprobe"], status=run.status, workspace=run.ws,
-                      first_wave=bd["first_wave"])
+                      first_wave=bd["first_wave"], wave_growth_log2=bd["growth"])
         ids_h.copy_(run.ids, non_blocking=True)
         d_h.copy_(run.d, non_blocking=True)
 
@@ -385,7 +387,8 @@ def main():
     serve_out = []
     if not args.no_serving:
         srv = serving.Server(G, idx, bd["delta_d"], max_K=K, max_nprobe=bd["nprobe"],
-                             buckets=(64, 256, 1024, 4096), slots=3, first_wave=bd["first_wave"])
+                             buckets=(64, 256, 1024, 4096), slots=3, first_wave=bd["first_wave"],
+                             wave_growth_log2=bd["growth"])
         rng = np.random.default_rng(6)
         for rate in SERVING_RATES:
             n_req = int(min(200_000, max(20_000, rate * 0.25)))
@@ -400,9 +403,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K, args.cpu_sample_queries,
-                                 first_wave=bd["first_wave"])
+                                 first_wave=bd["first_wave"], growth=max(1, bd["growth"]))
 
-    launches = 12 + 2 * n_waves(bd["nprobe"], bd["first_wave"])
+    launches = 12 + 2 * n_waves(bd["nprobe"], bd["first_wave"], bd["growth"])
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -410,6 +413,7 @@ def main():
         "config": {"workload": f"sift1m-shaped: N={len(X)}, D=128 integer [0,255], 256-comp mixture lambda~i^-0.8; "
                                f"B={run.B} queries; nlist={nlist}, K={K}",
                    "nprobe": bd["nprobe"], "delta_d": bd["delta_d"], "first_wave": bd["first_wave"],
+                   "wave_growth_log2": bd["growth"],
                    "slabs": "f32", "recall@10": bd["recall"],
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (index 1.0 GB > 129 MB L2)"},
         "full_scan": {"value": full_qps, "unit": "queries/s", "nprobe": bf["nprobe"], "recall@10": bf["recall"]},

@@ -163,7 +163,8 @@ dade_status dade_get_correction(const dade_index* idx, int32_t delta_d, float* m
  *  2. squared distance of q' to every centroid; the nprobe nearest, ordered
  *     by (distance, list id), are the query's buckets (Section II-A).
  *  3. probe ranks are cut into waves [b_w, b_{w+1}): b_0 = 0,
- *     b_1 = first_wave, b_{w+1} = 2 b_w.  Every candidate of wave w is tested
+ *     b_1 = first_wave, b_{w+1} = 2^g b_w (g = opts->wave_growth_log2).
+ *     Every candidate of wave w is tested
  *     against the query's tau at the end of wave w - 1 (tau = +inf before the
  *     queue holds K entries), in parallel over (bucket, query) work units.
  *  4. mode DADE_SCAN_PRUNE: the candidate's partial distance over the rotated
@@ -202,6 +203,9 @@ typedef struct {
     int32_t* status_dev;     /* optional int32 device status word                 */
     void* workspace;         /* optional device scratch of workspace_bytes        */
     size_t workspace_bytes;
+    int32_t wave_growth_log2;  /* g: each wave after the first is 2^g times the */
+                               /* previous one (0 means 1: doubling); 30 puts   */
+                               /* every rank after the first wave in one wave   */
 } dade_search_opts;
 
 dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,

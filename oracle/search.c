@@ -24,8 +24,9 @@
  * on parallel order):
  *  - SEQUENTIAL: tau is re-read before every candidate (Section I heap loop).
  *  - WAVES: probe ranks are cut into waves [b_w, b_{w+1}) with b_0 = 0,
- *    b_1 = first_wave, b_{w+1} = 2 b_w; every candidate of a wave is tested
- *    against the tau left by the previous waves; survivors are then merged.
+ *    b_1 = first_wave, b_{w+1} = 2^g b_w (g >= 1); every candidate of a wave
+ *    is tested against the tau left by the previous waves; survivors are
+ *    then merged.
  *  - FROZEN: every candidate is tested against a given tau_q; survivors with
  *    exact distance <= tau_q form the result (top-K by (distance, id)).
  */
@@ -107,10 +108,14 @@ static int estimate_and_test(const double* qr, const double* xs, int D, int dd, 
     return S - 1;
 }
 
-static int64_t wave_end(int64_t b, int first_wave) { return b == 0 ? first_wave : 2 * b; }
+static int64_t wave_end(int64_t b, int first_wave, int g)
+{
+    if (b == 0) return first_wave;
+    return g >= 30 ? ((int64_t)1 << 40) : b << g;
+}
 
 typedef struct {
-    int32_t D, dd, S, P, Kmax, mode, first_wave;
+    int32_t D, dd, S, P, Kmax, mode, first_wave, growth;
     double amb;
     const double* Qr;
     const float* Q;
@@ -174,7 +179,7 @@ static void search_one(const oracle_args* a, int64_t b)
     } else {
         int64_t b0 = 0;
         while (b0 < np) {
-            int64_t b1 = a->mode == MODE_FROZEN ? np : wave_end(b0, a->first_wave);
+            int64_t b1 = a->mode == MODE_FROZEN ? np : wave_end(b0, a->first_wave, a->growth);
             if (b1 > np) b1 = np;
             double tau = a->mode == MODE_FROZEN ? a->tau_in[b] : queue_tau(&q);
             int64_t cap = 0;
@@ -200,14 +205,14 @@ static void search_one(const oracle_args* a, int64_t b)
 }
 
 int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t Kmax,
-                  int32_t mode, int32_t first_wave, double amb, const double* Qr, const float* Q,
+                  int32_t mode, int32_t first_wave, int32_t growth, double amb, const double* Qr, const float* Q,
                   const double* Xs, const float* X, const int64_t* ids, const int64_t* list_off,
                   const int64_t* members, const int32_t* probes, const int32_t* nprobe,
                   const int32_t* K, const double* m1, const double* beta, const double* tau_in,
                   int64_t* out_ids, double* out_d, int64_t* stats)
 {
-    if (delta_d <= 0 || S < 1 || first_wave < 1 || mode < 0 || mode > 2) return 1;
-    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, amb, Qr, Q, Xs, X, ids, list_off,
+    if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1 || mode < 0 || mode > 2) return 1;
+    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, Qr, Q, Xs, X, ids, list_off,
                      members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < B; b++) search_one(&a, b);
@@ -218,14 +223,14 @@ int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, i
  * candidate, its partial distances dis'_1..dis'_{S-1}, the tau it would be
  * tested against, its exact distance, query index and id.  Row offsets per
  * query are given by the caller (row_off[b] = first row of query b). */
-int oracle_collect(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t first_wave,
+int oracle_collect(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t first_wave, int32_t growth,
                    const double* Qr, const float* Q, const double* Xs, const float* X,
                    const int64_t* ids, const int64_t* list_off, const int64_t* members,
                    const int32_t* probes, const int32_t* nprobe, const int32_t* K,
                    const int64_t* row_off, double* partials, double* tau_out, double* dis_out,
                    int64_t* id_out)
 {
-    if (delta_d <= 0 || S < 1 || first_wave < 1) return 1;
+    if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1) return 1;
     double* never = (double*)malloc(sizeof(double) * (size_t)(S > 1 ? S - 1 : 1));
     for (int s = 0; s < S - 1; s++) never[s] = 0.0;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -241,7 +246,7 @@ int oracle_collect(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, 
         double* neg_inf = (double*)malloc(sizeof(double) * (size_t)(S > 1 ? S - 1 : 1));
         for (int s = 0; s < S - 1; s++) neg_inf[s] = -INFINITY;
         while (b0 < np) {
-            int64_t b1 = wave_end(b0, first_wave);
+            int64_t b1 = wave_end(b0, first_wave, growth);
             if (b1 > np) b1 = np;
             double tau = queue_tau(&q);
             int64_t row0 = row;

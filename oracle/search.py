@@ -80,7 +80,7 @@ class OracleIndex:
 
 
 def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode="waves",
-           first_wave: int = 1, tau=None, amb: float = 0.0):
+           first_wave: int = 1, tau=None, amb: float = 0.0, growth: int = 1):
     """Returns (ids[B, Kmax], dists[B, Kmax], stats[B, 5]) where stats holds
     candidates visited, candidates pruned, exact distances taken, dims
     scanned, and tests whose left side m1 dis' + beta lay within amb * tau
@@ -105,7 +105,8 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
     rc = lib.oracle_search(
         ctypes.c_int64(B), ctypes.c_int32(idx.D), ctypes.c_int32(delta_d), ctypes.c_int32(S),
         ctypes.c_int32(P), ctypes.c_int32(Kmax), ctypes.c_int32(MODES[mode]),
-        ctypes.c_int32(first_wave), ctypes.c_double(amb), _p(Qr), _p(Q), _p(idx.Xs), _p(idx.X),
+        ctypes.c_int32(first_wave), ctypes.c_int32(growth), ctypes.c_double(amb), _p(Qr), _p(Q), _p(idx.Xs),
+        _p(idx.X),
         _p(idx.ids),
         _p(idx.list_off), _p(idx.members), _p(probes), _p(nprobe), _p(K), _p(m1), _p(beta),
         _p(tau_in), _p(out_ids), _p(out_d), _p(stats))
@@ -114,7 +115,7 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
     return out_ids, out_d, stats
 
 
-def collect(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, first_wave: int = 1):
+def collect(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, first_wave: int = 1, growth: int = 1):
     """Replay with pruning off; returns a dict of per-candidate rows:
     partials[n, S-1], tau[n], dis[n], id[n], query[n]."""
     lib = _load()
@@ -137,7 +138,8 @@ def collect(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, first_wave: in
     ids = np.empty(n, dtype=np.int64)
     rc = lib.oracle_collect(
         ctypes.c_int64(B), ctypes.c_int32(idx.D), ctypes.c_int32(delta_d), ctypes.c_int32(S),
-        ctypes.c_int32(P), ctypes.c_int32(first_wave), _p(Qr), _p(Q), _p(idx.Xs), _p(idx.X),
+        ctypes.c_int32(P), ctypes.c_int32(first_wave), ctypes.c_int32(growth), _p(Qr), _p(Q), _p(idx.Xs),
+        _p(idx.X),
         _p(idx.ids), _p(idx.list_off), _p(idx.members), _p(probes), _p(nprobe), _p(K),
         _p(row_off), _p(partials), _p(tau), _p(dis), _p(ids))
     if rc != 0:
@@ -146,11 +148,11 @@ def collect(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, first_wave: in
     return dict(partials=partials, tau=tau, dis=dis, id=ids, query=query, S=S)
 
 
-def wave_bounds(nprobe: int, first_wave: int = 1):
-    """Probe-rank boundaries of the WAVES schedule: 0, f, 2f, 4f, ... capped."""
+def wave_bounds(nprobe: int, first_wave: int = 1, growth: int = 1):
+    """Probe-rank boundaries of the WAVES schedule: 0, f, f 2^g, f 2^2g, ... capped."""
     b = [0]
     while b[-1] < nprobe:
-        nxt = first_wave if b[-1] == 0 else 2 * b[-1]
+        nxt = first_wave if b[-1] == 0 else b[-1] << min(growth, 40)
         b.append(min(nxt, nprobe))
     return b
 

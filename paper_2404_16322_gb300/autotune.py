@@ -42,13 +42,13 @@ class Bench:
                  for m in ("prune", "full") for dd in deltas)
         self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
 
-    def run(self, nprobe, delta_d, mode, first_wave=1, stats=False):
+    def run(self, nprobe, delta_d, mode, first_wave=1, stats=False, growth=0):
         self.np.fill_(nprobe)
         if stats:
             self.stats.zero_()
         self.G.dade_search(self.idx, self.q, self.k, self.np, delta_d, self.ids, self.d, max_K=self.K,
                            max_nprobe=nprobe, mode=mode, status=self.status, first_wave=first_wave,
-                           stats=self.stats if stats else None, workspace=self.ws)
+                           stats=self.stats if stats else None, workspace=self.ws, wave_growth_log2=growth)
 
     def result(self) -> np.ndarray:
         self.torch.cuda.synchronize()
@@ -57,11 +57,11 @@ class Bench:
             raise RuntimeError(f"device status {st}")
         return self.ids.view(self.B, self.K).cpu().numpy()
 
-    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1):
+    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1, growth=0):
         """Returns (total ms, per-step ms list), CUDA events on the stream."""
         torch = self.torch
         for _ in range(warmup):
-            self.run(nprobe, delta_d, mode, first_wave)
+            self.run(nprobe, delta_d, mode, first_wave, growth=growth)
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         t0 = torch.cuda.Event(enable_timing=True)
@@ -69,7 +69,7 @@ class Bench:
         t0.record()
         for e0, e1 in evs:
             e0.record()
-            self.run(nprobe, delta_d, mode, first_wave)
+            self.run(nprobe, delta_d, mode, first_wave, growth=growth)
             e1.record()
         t1.record()
         torch.cuda.synchronize()
@@ -85,21 +85,38 @@ def cache_key(G, idx, K: int, target: float, mode: str) -> str:
             f"|{h}|K{K}|r{target}|{mode}")
 
 
+SCHEDULES = ((1, 1), (4, 1), (8, 1), (8, 2), (8, 30), (16, 30))
+
+
 def autotune(bench: Bench, gt: np.ndarray, target: float = 0.95, k_recall: int = 10,
-             deltas=(8, 16, 32), first_waves=(1, 4), nprobes=(8, 16, 24, 32, 48, 64, 96, 128, 192, 256),
-             reps: int = 5, warmup: int = 2, mode: str = "prune", margin: float = 0.02):
-    """Returns (best configuration, every configuration tried)."""
+             deltas=(8, 16, 32), schedules=SCHEDULES,
+             nprobes=(8, 16, 24, 32, 48, 64, 96, 128, 192, 256), reps: int = 5, warmup: int = 2,
+             mode: str = "prune"):
+    """Returns (best configuration, every configuration tried).
+
+    The smallest nprobe whose full-dimension scan reaches the target is found
+    first (pruning can only lose recall); every (Delta_d, first wave, growth)
+    schedule is then timed from that nprobe up to the first that reaches the
+    target.  Mode "full" tunes the full-dimension scan's schedule the same way."""
     tried = []
+    start = 0
+    for i, npb in enumerate(nprobes):
+        bench.run(npb, 0, "full", 1)
+        if recall_at(bench.result(), gt, k_recall) >= target:
+            start = i
+            break
+    else:
+        start = len(nprobes) - 1
     dds = deltas if mode == "prune" else (0,)
     for dd in dds:
-        for fw in first_waves:
-            for npb in nprobes:
-                bench.run(npb, dd, mode, fw)
+        for fw, g in schedules:
+            for npb in nprobes[start:]:
+                bench.run(npb, dd, mode, fw, growth=g)
                 rec = recall_at(bench.result(), gt, k_recall)
-                _, per = bench.time(npb, dd, mode, reps, warmup, fw)
-                tried.append(dict(mode=mode, delta_d=dd, first_wave=fw, nprobe=npb, recall=rec,
+                _, per = bench.time(npb, dd, mode, reps, warmup, fw, growth=g)
+                tried.append(dict(mode=mode, delta_d=dd, first_wave=fw, growth=g, nprobe=npb, recall=rec,
                                   ms=float(np.median(per))))
-                if rec >= target + margin:
+                if rec >= target:
                     break
     ok = [t for t in tried if t["recall"] >= target]
     best = min(ok, key=lambda t: t["ms"]) if ok else max(tried, key=lambda t: t["recall"])

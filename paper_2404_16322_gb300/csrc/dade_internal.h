@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -38,15 +39,20 @@ constexpr int kMaxD = 4096;
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
-// Probe rank r belongs to wave w: [0, f) is wave 0, [f 2^(w-1), f 2^w) wave w.
-inline int wave_of_rank_host(int r, int f) {
+// Wave schedule with first wave f and growth 2^g: wave 0 holds probe ranks
+// [0, f), wave w >= 1 holds [f 2^(g(w-1)), f 2^(gw)).
+inline int wave_of_rank_host(int r, int f, int g) {
     if (r < f) return 0;
-    int q = r / f, w = 0;
-    while (q) { q >>= 1; ++w; }
-    return w;
+    int q = r / f, lg = -1;
+    while (q) { q >>= 1; ++lg; }
+    return 1 + lg / g;
 }
-inline int num_waves(int nprobe, int f) { return nprobe <= 0 ? 0 : wave_of_rank_host(nprobe - 1, f) + 1; }
-inline int wave_begin(int w, int f) { return w == 0 ? 0 : f << (w - 1); }
+inline int num_waves(int nprobe, int f, int g) { return nprobe <= 0 ? 0 : wave_of_rank_host(nprobe - 1, f, g) + 1; }
+inline int wave_begin(int w, int f, int g) {
+    if (w == 0) return 0;
+    const int64_t sh = (int64_t)g * (w - 1);
+    return sh >= 30 ? (1 << 30) : (int)std::min<int64_t>((int64_t)f << sh, 1 << 30);
+}
 
 struct CorrectionTable {
     int32_t S = 0;

@@ -740,11 +740,7 @@ __global__ void count_kernel(IndexView ix, WaveView wv) {
             atomicCAS(wv.status, 0, (int)DADE_EINVAL);
             continue;
         }
-        int wr = 0;
-        if (r >= wv.first_wave) {
-            int qq = r / wv.first_wave;
-            wr = 32 - __clz(qq);
-        }
+        const int wr = r < wv.first_wave ? 0 : 1 + (31 - __clz(r / wv.first_wave)) / wv.wave_shift;
         atomicAdd(&wv.cnt_wl[wr * ix.nlist + l], 1);
         wv.cand_off[(int64_t)wr * (wv.B + 1) + b] += ix.list_size[l];
     }
@@ -759,8 +755,7 @@ __global__ void scatter_kernel(IndexView ix, WaveView wv) {
     for (int r = 0; r < np; ++r) {
         const int l = wv.probes[b * wv.P + r];
         if (l < 0 || l >= ix.nlist) continue;
-        int wr = 0;
-        if (r >= wv.first_wave) wr = 32 - __clz(r / wv.first_wave);
+        const int wr = r < wv.first_wave ? 0 : 1 + (31 - __clz(r / wv.first_wave)) / wv.wave_shift;
         const int key = wr * ix.nlist + l;
         const int pos = atomicAdd(&wv.fill_wl[key], 1);
         wv.items[wv.off_wl[key] + pos] = (int32_t)b;

@@ -22,7 +22,7 @@ struct IndexView {
 
 struct WaveView {
     int64_t B;
-    int32_t P, Kmax, first_wave, n_waves;
+    int32_t P, Kmax, first_wave, n_waves, wave_shift;
     const float* qrot;        // B x Dpad rotated queries
     const float* qpad;        // B x Dpad original queries, zero padded
     const int32_t* probes;    // B x P

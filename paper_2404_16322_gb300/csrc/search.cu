@@ -50,8 +50,8 @@ struct Plan {
 
 // Upper bound of one wave's candidates for a query: the sum of the largest
 // (end - begin) bucket sizes.
-int64_t wave_bound(const dade_index* idx, int P, int f, int w) {
-    int b0 = wave_begin(w, f), b1 = std::min(P, wave_begin(w + 1, f));
+int64_t wave_bound(const dade_index* idx, int P, int f, int g, int w) {
+    int b0 = wave_begin(w, f, g), b1 = std::min(P, wave_begin(w + 1, f, g));
     int n = std::max(0, b1 - b0);
     n = std::min<int>(n, idx->nlist);
     return idx->sizes_desc_prefix[n];
@@ -61,16 +61,18 @@ size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* 
     const int P = o.max_nprobe, Kmax = o.max_K;
     const bool frozen = o.tau_dev != nullptr;
     const int f = frozen ? P : std::max(1, o.first_wave);
-    const int nw = num_waves(P, f);
+    const int g = std::max(1, o.wave_growth_log2);
+    const int nw = num_waves(P, f, g);
     const int64_t nl = idx->nlist;
     int64_t cap_per_q = 0;
-    for (int w = 0; w < nw; ++w) cap_per_q = std::max(cap_per_q, wave_bound(idx, P, f, w));
+    for (int w = 0; w < nw; ++w) cap_per_q = std::max(cap_per_q, wave_bound(idx, P, f, g, w));
     Carve c{base};
     WaveView& v = pl->wv;
     v.B = B;
     v.P = P;
     v.Kmax = Kmax;
     v.first_wave = f;
+    v.wave_shift = g;
     v.n_waves = nw;
     v.qrot = c.take<float>((size_t)B * idx->Dpad);
     v.qpad = c.take<float>((size_t)B * idx->Dpad);
@@ -85,7 +87,7 @@ size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* 
     const int64_t ntile_max = std::max<int64_t>(1, ceil_div(idx->max_list, kT));
     int64_t ucap = 0;
     for (int w = 0; w < nw; ++w) {
-        const int64_t width = std::max(0, std::min(P, wave_begin(w + 1, f)) - wave_begin(w, f));
+        const int64_t width = std::max(0, std::min(P, wave_begin(w + 1, f, g)) - wave_begin(w, f, g));
         v.ubase[w] = ucap;
         ucap += (ceil_div(B * width, kG) + std::min<int64_t>(nl, B * width)) * ntile_max;
     }
@@ -119,6 +121,7 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
         return fail(DADE_EINVAL, "max_nprobe must be in [1, min(nlist, 1024)]");
     if (o.mode != DADE_SCAN_PRUNE && o.mode != DADE_SCAN_FULL) return fail(DADE_EINVAL, "bad mode");
     if (o.first_wave < 0) return fail(DADE_EINVAL, "first_wave < 0");
+    if (o.wave_growth_log2 < 0 || o.wave_growth_log2 > 30) return fail(DADE_EINVAL, "wave_growth_log2 must be in [0, 30]");
     if (o.mode == DADE_SCAN_PRUNE) {
         if (delta_d != 8 && delta_d != 16 && delta_d != 32)
             return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32 (got %d)", delta_d);

@@ -139,6 +139,23 @@ def test_frozen_tau_matches_oracle(G, tiny_pre):
     parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb=st[:, 4], min_strict=s["strict"])
 
 
+@pytest.mark.parametrize("fw,g", [(2, 2), (2, 30)])
+def test_wave_growth_schedules(G, tiny_pre, fw, g):
+    """Waves [0,f), [f, f*2^g), ...: the oracle's waves mode with the same
+    schedule gives the same ids (strict up to the ambiguity band)."""
+    s = tiny_pre
+    oidx = s["inp"]["oidx"]
+    pr = oidx.probe(oidx.rotate_queries(s["Q"]), 8)
+    ids, d, st = search.search(oidx, s["Q"], pr, 8, 10, 16, s["inp"]["m1"].astype(np.float64),
+                               s["inp"]["beta"].astype(np.float64), first_wave=fw, growth=g,
+                               amb=H.AMB["exact"])
+    out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, first_wave=fw, growth=g, want=("stats",))
+    assert out["status"] == 0
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb=st[:, 4], min_strict=s["strict"])
+    un = st[:, 4] == 0
+    assert np.array_equal(out["stats"][un], st[un, :4])
+
+
 def test_ragged_K_and_nprobe(G, tiny_pre):
     s = tiny_pre
     rng = np.random.default_rng(5)

@@ -119,8 +119,9 @@ def test_exact_safe_tables_match_pruning_off_for_every_schedule(small):
     off = search.disabled_tables(S)
     safe = (np.ones(S - 1), np.zeros(S - 1))
     ref_ids, ref_d, _ = search.search(idx, Q, probes, 6, 10, 8, *off)
-    for mode, fw in [("sequential", 1), ("waves", 1), ("waves", 2), ("waves", 6)]:
-        ids, d, st = search.search(idx, Q, probes, 6, 10, 8, *safe, mode=mode, first_wave=fw)
+    for mode, fw, g in [("sequential", 1, 1), ("waves", 1, 1), ("waves", 2, 1), ("waves", 6, 1),
+                        ("waves", 1, 2), ("waves", 2, 30)]:
+        ids, d, st = search.search(idx, Q, probes, 6, 10, 8, *safe, mode=mode, first_wave=fw, growth=g)
         assert np.array_equal(ids, ref_ids) and np.array_equal(d, ref_d)
     ids, d, st = search.search(idx, Q, probes, 6, 10, 8, *safe, mode="frozen", tau=ref_d[:, -1])
     assert np.array_equal(ids, ref_ids) and np.array_equal(d, ref_d)
@@ -157,6 +158,13 @@ def test_partial_distances_monotone_lower_bounds(small):
     last = ((idx.Xs[np.searchsorted(idx.ids, rows["id"])][:, 16:] -
              idx.rotate_queries(Q[:10])[rows["query"]][:, 16:]) ** 2).sum(1)
     assert np.allclose(P[:, -1] + last, rows["dis"], rtol=1e-12, atol=1e-12)
+
+
+def test_wave_bounds_growth():
+    assert search.wave_bounds(64, 1, 1) == [0, 1, 2, 4, 8, 16, 32, 64]
+    assert search.wave_bounds(64, 8, 2) == [0, 8, 32, 64]
+    assert search.wave_bounds(64, 8, 30) == [0, 8, 64]
+    assert search.wave_bounds(5, 8, 1) == [0, 5]
 
 
 def test_collect_tau_is_the_waves_schedule_tau(small):
