@@ -174,7 +174,7 @@ def peaks():
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave=1, growth=1):
+def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave=1, growth=1, final_test=False):
     """The oracle (plain FP64 C loop, all host threads) on a bounded sample of
     the workload: a 100k-vector instance of the same mixture with the same
     bucket size (nlist 410, ~244 vectors per bucket), the same nprobe, K and
@@ -206,7 +206,8 @@ def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave
         q = Q[s * n_queries:(s + 1) * n_queries]
         t0 = time.perf_counter()
         pr = oidx.probe(oidx.rotate_queries(q), nprobe)  # probing is part of the query
-        search.search(oidx, q, pr, nprobe, K, delta_d, m1, beta, first_wave=first_wave, growth=growth)
+        search.search(oidx, q, pr, nprobe, K, delta_d, m1, beta, first_wave=first_wave, growth=growth,
+                      final_rel=search.FINAL_REL if final_test else np.inf)
         times.append(time.perf_counter() - t0)
     qps = n_queries / float(np.median(times))
     sample = (f"oracle FP64 C loop on {n_queries} queries per step against a {N}-vector SIFT-shaped instance "
@@ -303,13 +304,14 @@ def main():
         dist.barrier()
     sampler = ClockSampler(local)
     for _ in range(args.warmup):
-        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"])
+        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"],
+                final_test=bd["final_test"])
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     total_ms, per = run.time(bd["nprobe"], bd["delta_d"], "prune", args.steps, 0, first_wave=bd["first_wave"],
-                             growth=bd["growth"])
+                             growth=bd["growth"], final_test=bd["final_test"])
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:
@@ -328,7 +330,8 @@ def main():
     G.dade_stage_timing(True)
     G.dade_stage_timing_read()
     for _ in range(args.steps):
-        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"])
+        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"],
+                final_test=bd["final_test"])
     scan_ms, scan_launches, scan_bytes = G.dade_stage_timing_read()
     G.dade_stage_timing(False)
     per_launch_ms = scan_ms / max(1, scan_launches)
@@ -339,12 +342,13 @@ def main():
     traffic = traffic_from_profiles(khash)
 
     # --- work accounting (bytes per query) for both modes
-    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True, first_wave=bd["first_wave"], growth=bd["growth"])
+    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True, first_wave=bd["first_wave"], growth=bd["growth"],
+                final_test=bd["final_test"])
     run.result()
     st = run.stats.cpu().numpy()
     S = G.n_steps(128, bd["delta_d"])
     pruned_dims = st[:, 3] - st[:, 2] * 128
-    dade_bytes = (pruned_dims * 4 + st[:, 2] * ((S - 1) * bd["delta_d"] * 4 + 128 * 4)).sum() / run.B
+    dade_bytes = (pruned_dims * 4 + st[:, 2] * (2 * 128 * 4)).sum() / run.B
     run.run(bf["nprobe"], 0, "full", stats=True, first_wave=bf["first_wave"], growth=bf["growth"])
     run.result()
     stf = run.stats.cpu().numpy()
@@ -364,7 +368,7 @@ def main():
         run.np.copy_(n_h, non_blocking=True)
         G.dade_search(idx, run.q, run.k, run.np, bd["delta_d"], run.ids, run.d, max_K=K,
                       max_nprobe=bd["nprobe"], status=run.status, workspace=run.ws,
-                      first_wave=bd["first_wave"], wave_growth_log2=bd["growth"])
+                      first_wave=bd["first_wave"], wave_growth_log2=bd["growth"], final_test=bd["final_test"])
         ids_h.copy_(run.ids, non_blocking=True)
         d_h.copy_(run.d, non_blocking=True)
 
@@ -388,7 +392,7 @@ def main():
     if not args.no_serving:
         srv = serving.Server(G, idx, bd["delta_d"], max_K=K, max_nprobe=bd["nprobe"],
                              buckets=(64, 256, 1024, 4096), slots=3, first_wave=bd["first_wave"],
-                             wave_growth_log2=bd["growth"])
+                             wave_growth_log2=bd["growth"], final_test=bd["final_test"])
         rng = np.random.default_rng(6)
         for rate in SERVING_RATES:
             n_req = int(min(200_000, max(20_000, rate * 0.25)))
@@ -403,7 +407,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K, args.cpu_sample_queries,
-                                 first_wave=bd["first_wave"], growth=max(1, bd["growth"]))
+                                 first_wave=bd["first_wave"], growth=max(1, bd["growth"]),
+                                 final_test=bd["final_test"])
 
     launches = 12 + 2 * n_waves(bd["nprobe"], bd["first_wave"], bd["growth"])
     line = {
@@ -413,7 +418,7 @@ def main():
         "config": {"workload": f"sift1m-shaped: N={len(X)}, D=128 integer [0,255], 256-comp mixture lambda~i^-0.8; "
                                f"B={run.B} queries; nlist={nlist}, K={K}",
                    "nprobe": bd["nprobe"], "delta_d": bd["delta_d"], "first_wave": bd["first_wave"],
-                   "wave_growth_log2": bd["growth"],
+                   "wave_growth_log2": bd["growth"], "final_test": bd["final_test"],
                    "slabs": "f32", "recall@10": bd["recall"],
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (index 1.0 GB > 129 MB L2)"},
         "full_scan": {"value": full_qps, "unit": "queries/s", "nprobe": bf["nprobe"], "recall@10": bf["recall"]},

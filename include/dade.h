@@ -9,8 +9,8 @@
  * of Algorithm 2) and after each step the learned test
  * m1_s * dis' + beta_s > tau decides whether to prune it (Section V-A, V-B
  * "Incremental Correction"); a candidate that passes every test gets its
- * exact distance and competes for the result queue whose largest entry is
- * tau (Section I).
+ * exact distance, is compared with tau itself (Algorithm 2 at d = D) and
+ * competes for the result queue whose largest entry is tau (Section I).
  *
  * Conventions for every entry point:
  *  - Every call returns a dade_status; none aborts or exits.  On failure
@@ -88,6 +88,8 @@ dade_status dade_train_rotation(const float* X_host, int64_t n, int32_t D, int64
  *    the bucket's vector i at ((b * npad + i) * 8 + j) elements from the
  *    bucket's base, npad = bucket size rounded up to 32, in params->dtype;
  *  - the original FP32 vectors in the same blocked layout (exact distance);
+ *  - for BF16 / FP8 slabs, each vector's quantisation error norm
+ *    e_x = ||x' - x~|| (FP32 rotated vector minus its stored value);
  *  - the ids (params->ids, or the row numbers when NULL) as int64.
  * Inside a bucket, vectors keep increasing row order.  params->centroids
  * (nlist x D rotated-space FP32, host) replaces k-means when non-NULL;
@@ -169,8 +171,12 @@ dade_status dade_get_correction(const dade_index* idx, int32_t delta_d, float* m
  *     queue holds K entries), in parallel over (bucket, query) work units.
  *  4. mode DADE_SCAN_PRUNE: the candidate's partial distance over the rotated
  *     slabs grows delta_d dims per step and the installed table for delta_d
- *     decides pruning after each of the first S - 1 steps; survivors get the
- *     exact FP32 distance from the original vectors.  mode DADE_SCAN_FULL:
+ *     decides pruning after each of the first S - 1 steps; with
+ *     opts->final_test a survivor adds the last slab and is pruned iff
+ *     dis'_S > (sqrt(tau) + e_x)^2 (1 + 1e-3) (a rotated distance <= tau
+ *     implies dis'_S <= (sqrt(tau) + e_x)^2; the 1e-3 covers FP32 rounding);
+ *     the rest get the exact FP32 distance from the original vectors.
+ *     mode DADE_SCAN_FULL:
  *     every candidate gets the exact FP32 distance (no estimate, no table).
  *  5. candidates with exact distance <= tau join the query's top-K, ordered
  *     by (distance, id); tau becomes its K-th distance.
@@ -206,6 +212,13 @@ typedef struct {
     int32_t wave_growth_log2;  /* g: each wave after the first is 2^g times the */
                                /* previous one (0 means 1: doubling); 30 puts   */
                                /* every rank after the first wave in one wave   */
+    int32_t final_test;      /* PRUNE mode, nonzero: the test on the completed   */
+                             /* rotated distance (step 4) runs before the exact  */
+                             /* distance.  It never changes the results (it only */
+                             /* drops candidates with exact distance > tau); it  */
+                             /* trades a last slab step for fewer exact          */
+                             /* distances.  0: survivors of step S - 1 go        */
+                             /* straight to the exact distance.                  */
 } dade_search_opts;
 
 dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,
@@ -253,8 +266,8 @@ size_t dade_search_workspace_size(const dade_index* idx, int64_t B, int32_t delt
  * bucket of each input row (N int32, host); dade_index_list_sizes the
  * nlist bucket sizes (int64, host).
  * dade_index_save writes a versioned binary file (header, rotation, mean,
- * centroids, buckets, slabs, original vectors, ids, correction tables, and
- * an FNV-1a checksum); dade_index_load reads it back onto the current device
+ * centroids, buckets, slabs, original vectors, ids, quantisation error
+ * norms (BF16 / FP8), correction tables, and an FNV-1a checksum); dade_index_load reads it back onto the current device
  * and reproduces identical search results.  Errors: DADE_EIO, DADE_ENOMEM,
  * DADE_ECUDA, DADE_EINVAL.
  * ---------------------------------------------------------------------- */

@@ -14,11 +14,19 @@
  *  - After each step s < S the learned test of Section V-A is applied:
  *    prune iff m1_s * dis'_s + beta_s > tau ("Incremental Correction" gives
  *    one classifier per step).  A disabled step has m1 = 0, beta = -inf.
- *  - A candidate that passes every test reaches d = D and gets its exact
- *    distance sum_j (x_j - q_j)^2 from the original FP32 vectors
- *    (Section II-A), and enters the result queue iff it beats the queue's
- *    largest entry (Section I: tau is the largest distance in the queue).
- *    Ties are ordered by id; tau = +inf while the queue holds fewer than K.
+ *  - A candidate that passes every test adds the last slab, which completes
+ *    the rotated distance dis'_S at the stored precision.  At d = D
+ *    Algorithm 2's test has no residual term and compares the distance with
+ *    tau itself; here the candidate is kept iff
+ *    dis'_S <= (sqrt(tau) + e_x)^2 (1 + final_rel), where e_x = ||x' - x~||
+ *    is the stored vector's quantisation error (0 for FP32 slabs): by the
+ *    triangle inequality a rotated distance <= tau implies that bound, and
+ *    final_rel covers floating-point rounding.
+ *  - A kept candidate gets its exact distance sum_j (x_j - q_j)^2 from the
+ *    original FP32 vectors (Section II-A), and enters the result queue iff
+ *    it beats the queue's largest entry (Section I: tau is the largest
+ *    distance in the queue).  Ties are ordered by id; tau = +inf while the
+ *    queue holds fewer than K.
  *
  * tau schedules (the paper updates tau after every insertion and is silent
  * on parallel order):
@@ -85,8 +93,8 @@ static double exact_distance(const float* x, const float* q, int D)
  * passed every test); *pruned tells which.  partials (may be NULL) receives
  * dis'_s for every step taken. */
 static int estimate_and_test(const double* qr, const double* xs, int D, int dd, int S,
-                             const double* m1, const double* beta, double tau,
-                             int* pruned, double* partials, double amb, int64_t* n_amb)
+                             const double* m1, const double* beta, double tau, double xerr,
+                             double final_rel, int* pruned, double* partials, double amb, int64_t* n_amb)
 {
     double p = 0.0;
     *pruned = 0;
@@ -105,7 +113,21 @@ static int estimate_and_test(const double* qr, const double* xs, int D, int dd, 
             return s;
         }
     }
-    return S - 1;
+    /* d = D: the last slab, then the test on the whole rotated distance */
+    for (int j = (S - 1) * dd; j < D; j++) {
+        double t = qr[j] - xs[j];
+        p += t * t;
+    }
+    if (isfinite(tau) && isfinite(final_rel)) {
+        double r = sqrt(tau) + xerr;
+        double lim = r * r * (1.0 + final_rel);
+        if (n_amb && fabs(p - lim) <= amb * tau) (*n_amb)++;
+        if (p > lim) {
+            *pruned = 1;
+            return S;
+        }
+    }
+    return S;
 }
 
 static int64_t wave_end(int64_t b, int first_wave, int g)
@@ -116,7 +138,8 @@ static int64_t wave_end(int64_t b, int first_wave, int g)
 
 typedef struct {
     int32_t D, dd, S, P, Kmax, mode, first_wave, growth;
-    double amb;
+    double amb, final_rel;
+    const double* xerr;
     const double* Qr;
     const float* Q;
     const double* Xs;
@@ -141,7 +164,7 @@ static int visit(const oracle_args* a, int64_t b, int64_t pos, double tau, entry
     const double* qr = a->Qr + b * a->D;
     int pruned;
     int steps = estimate_and_test(qr, a->Xs + pos * a->D, a->D, a->dd, a->S, a->m1, a->beta, tau,
-                                  &pruned, NULL, a->amb, &st[4]);
+                                  a->xerr ? a->xerr[pos] : 0.0, a->final_rel, &pruned, NULL, a->amb, &st[4]);
     st[0] += 1;
     if (pruned) {
         int64_t dims = (int64_t)steps * a->dd;
@@ -205,15 +228,17 @@ static void search_one(const oracle_args* a, int64_t b)
 }
 
 int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t Kmax,
-                  int32_t mode, int32_t first_wave, int32_t growth, double amb, const double* Qr, const float* Q,
-                  const double* Xs, const float* X, const int64_t* ids, const int64_t* list_off,
+                  int32_t mode, int32_t first_wave, int32_t growth, double amb, double final_rel,
+                  const double* Qr, const float* Q, const double* Xs, const double* xerr, const float* X,
+                  const int64_t* ids, const int64_t* list_off,
                   const int64_t* members, const int32_t* probes, const int32_t* nprobe,
                   const int32_t* K, const double* m1, const double* beta, const double* tau_in,
                   int64_t* out_ids, double* out_d, int64_t* stats)
 {
-    if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1 || mode < 0 || mode > 2) return 1;
-    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, Qr, Q, Xs, X, ids, list_off,
-                     members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
+    if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1 || mode < 0 || mode > 2 || !(final_rel >= 0.0))
+        return 1;
+    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, final_rel, xerr, Qr, Q, Xs, X, ids,
+                     list_off, members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < B; b++) search_one(&a, b);
     return 0;
@@ -255,8 +280,8 @@ int oracle_collect(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, 
                 for (int64_t m = list_off[l]; m < list_off[l + 1]; m++) {
                     int64_t pos = members[m];
                     int pruned;
-                    estimate_and_test(Qr + b * D, Xs + pos * D, D, delta_d, S, never, neg_inf, tau,
-                                      &pruned, partials + row * (S > 1 ? S - 1 : 0), 0.0, NULL);
+                    estimate_and_test(Qr + b * D, Xs + pos * D, D, delta_d, S, never, neg_inf, tau, 0.0,
+                                      INFINITY, &pruned, partials + row * (S > 1 ? S - 1 : 0), 0.0, NULL);
                     tau_out[row] = tau;
                     dis_out[row] = exact_distance(X + pos * D, Q + b * D, D);
                     id_out[row] = ids[pos];

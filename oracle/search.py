@@ -44,6 +44,11 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
+# Relative slack of the test on the completed rotated distance: covers the
+# FP32 rounding of the rotation and of the accumulated sums.
+FINAL_REL = 1e-3
+
+
 def n_steps(D: int, delta_d: int) -> int:
     """S = ceil(D / Delta_d): the number of Delta_d slabs covering D dims."""
     return -(-D // delta_d)
@@ -70,6 +75,10 @@ class OracleIndex:
         self.dtype = dtype
         Xr = _pca.rotate(self.X, self.mu, self.R)
         self.Xs = np.ascontiguousarray(_storage.stored(Xr, dtype, fp8_scale))
+        # quantisation error norm ||x' - x~|| of each stored vector; FP32 and
+        # FP64 storage count as exact (FINAL_REL covers their rounding)
+        self.xerr = (np.zeros(self.N) if dtype in ("f32", "f64")
+                     else np.ascontiguousarray(np.sqrt(((Xr - self.Xs) ** 2).sum(axis=1))))
         self.list_off, self.members = _ivf.lists_from_assignment(self.assign, self.nlist)
 
     def rotate_queries(self, Q):
@@ -80,11 +89,12 @@ class OracleIndex:
 
 
 def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode="waves",
-           first_wave: int = 1, tau=None, amb: float = 0.0, growth: int = 1):
+           first_wave: int = 1, tau=None, amb: float = 0.0, growth: int = 1, final_rel: float = np.inf):
     """Returns (ids[B, Kmax], dists[B, Kmax], stats[B, 5]) where stats holds
     candidates visited, candidates pruned, exact distances taken, dims
-    scanned, and tests whose left side m1 dis' + beta lay within amb * tau
-    of tau (decisions another rounding could flip)."""
+    scanned, and tests whose two sides lay within amb * tau of each other
+    (decisions another rounding could flip).  final_rel: the slack of the
+    test on the completed rotated distance (FINAL_REL), or inf for no test."""
     lib = _load()
     Q = np.ascontiguousarray(Q, dtype=np.float32)
     B = Q.shape[0]
@@ -105,8 +115,8 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
     rc = lib.oracle_search(
         ctypes.c_int64(B), ctypes.c_int32(idx.D), ctypes.c_int32(delta_d), ctypes.c_int32(S),
         ctypes.c_int32(P), ctypes.c_int32(Kmax), ctypes.c_int32(MODES[mode]),
-        ctypes.c_int32(first_wave), ctypes.c_int32(growth), ctypes.c_double(amb), _p(Qr), _p(Q), _p(idx.Xs),
-        _p(idx.X),
+        ctypes.c_int32(first_wave), ctypes.c_int32(growth), ctypes.c_double(amb), ctypes.c_double(final_rel),
+        _p(Qr), _p(Q), _p(idx.Xs), _p(idx.xerr), _p(idx.X),
         _p(idx.ids),
         _p(idx.list_off), _p(idx.members), _p(probes), _p(nprobe), _p(K), _p(m1), _p(beta),
         _p(tau_in), _p(out_ids), _p(out_d), _p(stats))

@@ -30,7 +30,8 @@ class SearchOpts(ctypes.Structure):
     _fields_ = [("mode", c_i32), ("max_K", c_i32), ("max_nprobe", c_i32), ("first_wave", c_i32),
                 ("tau_dev", c_vp), ("probe_in_dev", c_vp), ("probe_out_dev", c_vp),
                 ("qrot_out_dev", c_vp), ("stats_dev", c_vp), ("status_dev", c_vp),
-                ("workspace", c_vp), ("workspace_bytes", c_sz), ("wave_growth_log2", c_i32)]
+                ("workspace", c_vp), ("workspace_bytes", c_sz), ("wave_growth_log2", c_i32),
+                ("final_test", c_i32)]
 
 
 class IndexInfo(ctypes.Structure):

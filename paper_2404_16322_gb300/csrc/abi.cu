@@ -72,6 +72,8 @@ dade_status upload_index_arrays(dade_index* idx) {
     DADE_TRY(idx->slab_dev.alloc(n * elem_size(idx->dtype)));
     DADE_TRY(idx->orig_dev.alloc(n * sizeof(float)));
     DADE_TRY(idx->ids_dev.alloc(sizeof(int64_t) * std::max<int64_t>(1, idx->total_slots)));
+    if (idx->dtype != DADE_SLAB_F32)
+        DADE_TRY(idx->eps_dev.alloc(sizeof(float) * std::max<int64_t>(1, idx->total_slots)));
     return DADE_OK;
 }
 
@@ -136,7 +138,7 @@ struct Reader {
 };
 
 const char kMagic[8] = {'D', 'A', 'D', 'E', 'I', 'D', 'X', '1'};
-const uint32_t kVersion = 1;
+const uint32_t kVersion = 2;
 
 }  // namespace
 
@@ -169,7 +171,7 @@ extern "C" dade_status dade_index_info_get(const dade_index* idx, dade_index_inf
     out->dtype = idx->dtype;
     out->max_list = idx->max_list;
     out->device_bytes = (int64_t)(idx->slab_dev.bytes + idx->orig_dev.bytes + idx->ids_dev.bytes +
-                                  idx->cent_dev.bytes + idx->R_dev.bytes);
+                                  idx->cent_dev.bytes + idx->R_dev.bytes + idx->eps_dev.bytes);
     return DADE_OK;
 }
 
@@ -251,6 +253,7 @@ extern "C" dade_status dade_index_save(const dade_index* idx, const char* path) 
     dump(idx->slab_dev, n * elem_size(idx->dtype));
     dump(idx->orig_dev, n * sizeof(float));
     dump(idx->ids_dev, sizeof(int64_t) * idx->total_slots);
+    if (idx->dtype != DADE_SLAB_F32) dump(idx->eps_dev, sizeof(float) * idx->total_slots);
     int32_t nt = (int32_t)idx->tables.size();
     w.pod(nt);
     for (auto& kv : idx->tables) {
@@ -324,6 +327,7 @@ extern "C" dade_status dade_index_load(const char* path, dade_index** out) {
     DADE_TRY(fill(idx->slab_dev, n * elem_size(idx->dtype)));
     DADE_TRY(fill(idx->orig_dev, n * sizeof(float)));
     DADE_TRY(fill(idx->ids_dev, sizeof(int64_t) * idx->total_slots));
+    if (idx->dtype != DADE_SLAB_F32) DADE_TRY(fill(idx->eps_dev, sizeof(float) * idx->total_slots));
     int32_t ntab = 0;
     r.pod(ntab);
     if (!r.ok || ntab < 0 || ntab > 64) return fail(DADE_EIO, "%s: bad table count", path);

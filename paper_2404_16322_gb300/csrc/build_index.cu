@@ -214,7 +214,9 @@ extern "C" dade_status ivf_build(const float* X, int64_t N, int32_t D, const dou
         la.scale = idx->scale_dev.as<float>();
         la.slab = idx->slab_dev.p;
         la.orig = idx->orig_dev.as<float>();
+        la.eps = idx->dtype == DADE_SLAB_F32 ? nullptr : idx->eps_dev.as<float>();
         DADE_CUDA_TRY(launch_layout(la, st));
+        DADE_CUDA_TRY(launch_quant_error(la, st));
         std::vector<int64_t> slot_ids((size_t)idx->total_slots, -1);
         for (int64_t s = 0; s < idx->total_slots; ++s)
             if (slot_row[(size_t)s] >= 0) slot_ids[(size_t)s] = idx->ids[(size_t)slot_row[(size_t)s]];

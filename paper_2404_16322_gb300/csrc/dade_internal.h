@@ -35,6 +35,10 @@ constexpr int kBlock = 8;        // dimensions per layout block
 constexpr int kListAlign = 32;   // bucket sizes are padded to a multiple of this
 constexpr int kMaxK = 1024;
 constexpr int kMaxD = 4096;
+// Relative slack of the test on the completed rotated distance (a candidate
+// is reranked iff dis'_S <= (sqrt(tau) + e_x)^2 (1 + kFinalRel)): covers the
+// FP32 rounding of the rotation and of the accumulated sums.
+constexpr float kFinalRel = 1e-3f;
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
@@ -101,6 +105,7 @@ struct dade_index {
     dade::DevBuf orig_dev;     // total_slots x Dpad FP32, blocked
     dade::DevBuf ids_dev;      // total_slots int64 (-1 on padding)
     dade::DevBuf scale_dev;    // Dpad FP32 (FP8 only)
+    dade::DevBuf eps_dev;      // total_slots FP32: quantisation error norm (BF16/FP8 only)
     std::map<int, dade::CorrectionTable> tables;  // by delta_d
     // internal scratch used when the caller gives no workspace
     mutable dade::DevBuf ws;
@@ -154,8 +159,10 @@ struct LayoutArgs {
     const float* scale;      // FP8 per-dim scale
     void* slab;
     float* orig;
+    float* eps;              // total_slots: ||x' - stored x'|| (BF16/FP8 only, else null)
 };
 cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st);
+cudaError_t launch_quant_error(const LayoutArgs& a, cudaStream_t st);
 cudaError_t launch_amax(const float* xrot, int64_t N, int32_t Dpad, float* amax_bits_as_float,
                         cudaStream_t st);
 cudaError_t launch_fp8_scale(float* amax_to_scale, int32_t Dpad, cudaStream_t st);

@@ -41,6 +41,32 @@ __global__ void layout_kernel(LayoutArgs a) {
     }
 }
 
+// Quantisation error norm ||x' - x~|| of every slot's stored vector (one warp
+// per slot, lanes over dimensions, fixed-order butterfly sum).
+__global__ void quant_error_kernel(LayoutArgs a) {
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (slot >= a.total_slots) return;
+    const int64_t row = a.slot_row[slot];
+    float s = 0.f;
+    if (row >= 0) {
+        for (int d = lane; d < a.D; d += 32) {
+            const float xr = a.xrot[row * a.Dpad + d];
+            float xs;
+            if (a.dtype == DADE_SLAB_BF16) {
+                xs = __bfloat162float(__float2bfloat16_rn(xr));
+            } else {
+                const __nv_fp8_storage_t v = __nv_cvt_float_to_fp8(xr / a.scale[d], __NV_SATFINITE, __NV_E4M3);
+                xs = __half2float(__half(__nv_cvt_fp8_to_halfraw(v, __NV_E4M3))) * a.scale[d];
+            }
+            const float e = xr - xs;
+            s = fmaf(e, e, s);
+        }
+    }
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) a.eps[slot] = sqrtf(s);
+}
+
 __global__ void amax_kernel(const float* __restrict__ xrot, int64_t N, int32_t Dpad,
                             unsigned int* __restrict__ amax) {
     int d = blockIdx.y;
@@ -66,6 +92,12 @@ cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st) {
     int64_t n = a.total_slots * (a.Dpad / kBlock);
     if (n == 0) return cudaSuccess;
     layout_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quant_error(const LayoutArgs& a, cudaStream_t st) {
+    if (a.total_slots == 0 || a.dtype == DADE_SLAB_F32 || !a.eps) return cudaSuccess;
+    quant_error_kernel<<<(unsigned)ceil_div(a.total_slots * 32, 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -59,12 +59,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// A waiting thread sleeps until the phase completes or this many ns pass
+// (then it re-checks), rather than spinning on the barrier.
+constexpr uint32_t kWaitHintNs = 200000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
         : "memory");
     return ok != 0;
 }
@@ -183,14 +186,34 @@ __device__ __forceinline__ void load_q8(const float* p, float (&q)[8]) {
     q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
 }
 
-// Exact distance of one candidate from the original blocked FP32 vector.
-__device__ float exact_distance(const float* xo, int64_t npad, const float* qp, int nb) {
+// Exact distance of one candidate from the original blocked FP32 vector:
+// d += s_b over the blocks in order (the staged paths' order), two blocks'
+// loads in flight at a time.
+__device__ __forceinline__ void load8_ro(const float* p, float (&x)[8]) {
+    float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+
+__device__ __forceinline__ float exact_distance(const float* xo, int64_t npad, const float* qp, int nb) {
     float d = 0.f;
-    for (int b = 0; b < nb; ++b) {
-        float x[8], q[8];
-        load8(xo + (int64_t)b * npad * kBlock, nullptr, x);
-        load_q8(qp + b * kBlock, q);
-        d += block_sq(q, x);
+    const int64_t stride = npad * kBlock;
+    int b = 0;
+    for (; b + 2 <= nb; b += 2) {
+        float x0[8], x1[8], q0[8], q1[8];
+        load8_ro(xo + (int64_t)b * stride, x0);
+        load8_ro(xo + (int64_t)(b + 1) * stride, x1);
+        load_q8(qp + b * kBlock, q0);
+        load_q8(qp + (b + 1) * kBlock, q1);
+        d += block_sq(q0, x0);
+        d += block_sq(q1, x1);
+    }
+    if (b < nb) {
+        float x0[8], q0[8];
+        load8_ro(xo + (int64_t)b * stride, x0);
+        load_q8(qp + b * kBlock, q0);
+        d += block_sq(q0, x0);
     }
     return d;
 }
@@ -210,37 +233,6 @@ __device__ __forceinline__ Unit unpack_unit(int4 d) {
     r.nq = d.w >> 16;
     r.nt = d.w & 0xffff;
     return r;
-}
-
-// ------------------------------------------------------------ exact distance
-// Exact distance of one candidate per SEG-lane segment of the warp (SEG = the
-// smallest power of two >= nb, at most 32).  Lane j of a segment forms the
-// block sums s_b of blocks j, j + SEG, ...; every lane of the segment then
-// adds the segment's s_b in block order with shuffles, so the result is the
-// same as the staged path's d += s_b (block order) and every lane holds it.
-__device__ __forceinline__ int seg_lanes(int nb) {
-    int s = 1;
-    while (s < nb && s < 32) s <<= 1;
-    return s;
-}
-
-__device__ __forceinline__ float exact_coop(const float* xo, int64_t npad, const float* qp, bool valid, int nb,
-                            int lane, int seg) {
-    const int j = lane & (seg - 1), segbase = lane & ~(seg - 1);
-    float d = 0.f;
-    for (int r = 0; r < nb; r += seg) {
-        float mine = 0.f;
-        const int b = r + j;
-        if (valid && b < nb) {
-            float x[8], q[8];
-            load8(xo + (int64_t)b * npad * kBlock, nullptr, x);
-            load_q8(qp + b * kBlock, q);
-            mine = block_sq(q, x);
-        }
-        const int nr = min(seg, nb - r);
-        for (int jj = 0; jj < nr; ++jj) d += __shfl_sync(0xffffffffu, mine, segbase + jj);
-    }
-    return d;
 }
 
 // ------------------------------------------------------------ step pipeline
@@ -272,15 +264,28 @@ struct StepShared {
 
 // Runs `nsteps` slab steps over the tile: slab k covers blocks
 // [k*NBLK, min((k+1)*NBLK, nb)) of the source (rotated slabs in PRUNE mode,
-// original vectors otherwise).  PRUNE tests after each slab and compacts;
-// otherwise every pair accumulates every slab.  A pair whose query has
-// tau = +inf is never pruned.  Returns false if a bounded wait gave up.
-template <class E, int NBLK, bool PRUNE>
+// original vectors otherwise).
+//  * Without PRUNE every step is dense: thread (warp, lane) owns candidate
+//    c = 32 warp + lane of the tile and accumulates pd[g] for every query g
+//    of the unit in registers; the unit's queries are read as broadcasts.
+//  * With PRUNE step 0 is dense as well.  Every pair is tested after it and
+//    the survivors go to the per-warp lists (warp w keeps its own
+//    candidates' survivors, query by query); later steps walk those lists,
+//    testing and compacting after each slab.  The test after slab k is the
+//    learned one, m1_k dis' + beta_k > tau (Section V-A); with FINAL the
+//    last slab (k = nsteps - 1) completes the rotated distance and the test
+//    is dis'_S > (sqrt(tau) + e_x)^2 (1 + kFinalRel) (e_x = eps_tile[c], 0
+//    without eps_tile).  A pair whose query has tau = +inf is never pruned.
+// Partial sums grow block by block in block order on every path, so a pair
+// gets the same value whichever path computed it.  Returns false if a
+// bounded wait gave up.
+template <class E, int NBLK, bool PRUNE, bool FINAL>
 __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int nt, int nq, int nsteps,
                                           int nb, int D, const StepShared& sh, uint32_t& phase_bits,
                                           const float* qsrc, int Dpad, const float* m1,
-                                          const float* beta, const float* scale, int32_t* status,
-                                          unsigned long long* staged, bool want_stats) {
+                                          const float* beta, const float* scale,
+                                          const float* eps_tile, int32_t* status,
+                                          unsigned long long* staged, bool want_stats, float (&pd)[kG]) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt_copy = (nt + 31) & ~31;
     const uint32_t blk_bytes = (uint32_t)nt_copy * kBlock * sizeof(E);
@@ -296,12 +301,17 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
                      sh.bar + (k & 1));
         if (staged) atomicAdd(staged, (unsigned long long)blk_bytes * nbk);
     };
+#pragma unroll
+    for (int g = 0; g < kG; ++g) pd[g] = 0.f;
+    if (PRUNE && tid < kWarps) sh.n[tid] = 0;  // step 0 appends with atomics
     if (nsteps <= 0) return true;
     if (tid == 0) issue(0);
     int k = 0;
     bool pending_next = false;
     uint16_t* key = sh.key + warp * kWarpCap;
     float* part = sh.part + warp * kWarpCap;
+    const int c_own = warp * 32 + lane;
+    const bool own_valid = c_own < nt;
     for (; k < nsteps; ++k) {
         const int b0 = k * NBLK, nbk = min(NBLK, nb - b0), w8 = nbk * kBlock;
         // the step's query values (and FP8 scales) for every query of the unit
@@ -317,46 +327,117 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
         if (tid == 0 && pending_next) issue(k + 1);
         const E* bk = reinterpret_cast<const E*>(sh.buf0 + (k & 1) * sh.buf_bytes);
         const int dims_k = min((k + 1) * NBLK * kBlock, D);
-        const float mm = PRUNE ? m1[k] : 0.f, bt = PRUNE ? beta[k] : 0.f;
-        const int n = sh.n[warp];
+        const bool final_k = FINAL && k == nsteps - 1;
+        const float mm = PRUNE && !final_k ? m1[k] : 0.f, bt = PRUNE && !final_k ? beta[k] : 0.f;
         int out = 0;
-        for (int base = 0; base < n; base += 32) {
-            const int i = base + lane;
-            const bool valid = i < n;
-            int kk = 0, g = 0;
-            float pd = 0.f;
-            if (valid) {
-                kk = key[i];
-                g = kk >> 8;
-                const int c = kk & 255;
-                pd = part[i];
-                const float* qg = sh.qs + g * kQsPad;
+        if (!PRUNE || k == 0) {
+            // dense: block by block, this thread's candidate against every
+            // query of the unit
 #pragma unroll
-                for (int bb = 0; bb < NBLK; ++bb) {
-                    if (bb < nbk) {
-                        float x[8], qv[8];
-                        load8_staged(bk + ((size_t)bb * kT + c) * kBlock, sh.sc + bb * kBlock, x);
-                        load8(qg + bb * kBlock, nullptr, qv);
-                        pd += block_sq(qv, x);
+            for (int bb = 0; bb < NBLK; ++bb) {
+                if (bb < nbk) {
+                    float x[8];
+                    load8_staged(bk + ((size_t)bb * kT + c_own) * kBlock, sh.sc + bb * kBlock, x);
+#pragma unroll
+                    for (int g = 0; g < kG; ++g) {
+                        if (g < nq) {
+                            float qv[8];
+                            load8(sh.qs + g * kQsPad + bb * kBlock, nullptr, qv);
+                            pd[g] += block_sq(qv, x);
+                        }
                     }
                 }
             }
-            const bool keep = valid && !(PRUNE && fmaf(mm, pd, bt) > sh.tau[g]);
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            __syncwarp();
-            if (keep) {
-                const int pos = out + __popc(bal & lanemask_lt());
-                key[pos] = (uint16_t)kk;
-                part[pos] = pd;
+            if (PRUNE) {
+                // test every pair; the survivors of (this warp, query g) go
+                // to list (warp + g) mod kWarps, so every list gets a share
+                // of every warp's candidates and of every query
+                const float e_own = FINAL && final_k && eps_tile && own_valid ? eps_tile[c_own] : 0.f;
+#pragma unroll
+                for (int g = 0; g < kG; ++g) {
+                    if (g < nq) {
+                        bool cut;
+                        if (FINAL && final_k) {
+                            const float r = sqrtf(sh.tau[g]) + e_own;
+                            cut = pd[g] > r * r * (1.f + kFinalRel);
+                        } else {
+                            cut = fmaf(mm, pd[g], bt) > sh.tau[g];
+                        }
+                        const bool keep = own_valid && !cut;
+                        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                        if (bal) {
+                            const int v = (warp + g) & (kWarps - 1);
+                            int base = 0;
+                            if (lane == 0) base = atomicAdd(&sh.n[v], __popc(bal));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            if (keep) {
+                                const int pos = v * kWarpCap + base + __popc(bal & lanemask_lt());
+                                sh.key[pos] = (uint16_t)((g << 8) | c_own);
+                                sh.part[pos] = pd[g];
+                            }
+                        }
+                        if (want_stats) {
+                            const int np = __popc(__ballot_sync(0xffffffffu, own_valid && cut));
+                            if (lane == 0 && np) {
+                                atomicAdd(&sh.st[g * 4 + 1], (unsigned long long)np);
+                                atomicAdd(&sh.st[g * 4 + 3], (unsigned long long)np * dims_k);
+                            }
+                        }
+                    }
+                }
             }
-            out += __popc(bal);
-            if (PRUNE && want_stats && valid && !keep) {
-                atomicAdd(&sh.st[g * 4 + 1], 1ull);
-                atomicAdd(&sh.st[g * 4 + 3], (unsigned long long)dims_k);
+        } else {
+            // sparse: the warp's live pairs, 32 at a time
+            const int n = sh.n[warp];
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                const bool valid = i < n;
+                int kk = 0, g = 0, c = 0;
+                float pv = 0.f;
+                if (valid) {
+                    kk = key[i];
+                    g = kk >> 8;
+                    c = kk & 255;
+                    pv = part[i];
+                    const float* qg = sh.qs + g * kQsPad;
+#pragma unroll
+                    for (int bb = 0; bb < NBLK; ++bb) {
+                        if (bb < nbk) {
+                            float x[8], qv[8];
+                            load8_staged(bk + ((size_t)bb * kT + c) * kBlock, sh.sc + bb * kBlock, x);
+                            load8(qg + bb * kBlock, nullptr, qv);
+                            pv += block_sq(qv, x);
+                        }
+                    }
+                }
+                bool cut = false;
+                if (FINAL && final_k) {
+                    if (valid) {
+                        const float r = sqrtf(sh.tau[g]) + (eps_tile ? eps_tile[c] : 0.f);
+                        cut = pv > r * r * (1.f + kFinalRel);
+                    }
+                } else {
+                    cut = fmaf(mm, pv, bt) > sh.tau[g];
+                }
+                const bool keep = valid && !cut;
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                __syncwarp();
+                if (keep) {
+                    const int pos = out + __popc(bal & lanemask_lt());
+                    key[pos] = (uint16_t)kk;
+                    part[pos] = pv;
+                }
+                out += __popc(bal);
+                if (want_stats && valid && !keep) {
+                    atomicAdd(&sh.st[g * 4 + 1], 1ull);
+                    atomicAdd(&sh.st[g * 4 + 3], (unsigned long long)dims_k);
+                }
             }
         }
-        __syncwarp();
-        if (lane == 0) sh.n[warp] = out;
+        if (PRUNE && k > 0) {
+            __syncwarp();
+            if (lane == 0) sh.n[warp] = out;
+        }
         __syncthreads();
         if (PRUNE) {
             int live = 0;
@@ -372,6 +453,27 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
         if (!__syncthreads_and(got)) return false;
     }
     return true;
+}
+
+// Append (d, slot) to query q's candidate buffer for every lane with app set,
+// q the same on every lane of the warp: one atomic for the warp.
+__device__ __forceinline__ void append_uniform(const WaveView& wv, int w, int q, bool app, float d,
+                                               int32_t slot, int lane) {
+    const unsigned bal = __ballot_sync(0xffffffffu, app);
+    if (!bal) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&wv.cand_cnt[q], __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (!app) return;
+    const int64_t* co = wv.cand_off + (int64_t)w * (wv.B + 1);
+    const int64_t off = co[q], cap = co[q + 1] - off;
+    const int s = base + __popc(bal & lanemask_lt());
+    if (s < cap) {
+        wv.cand_d[off + s] = d;
+        wv.cand_pos[off + s] = slot;
+    } else {
+        atomicCAS(wv.status, 0, (int)DADE_EINVAL);
+    }
 }
 
 // Append (d, slot) to query q's candidate buffer for every lane with app set;
@@ -402,7 +504,7 @@ constexpr int scan_smem_bytes() {
     return 2 * NBLK * kT * kBlock * 4 + kWarps * kWarpCap * (int)(sizeof(uint16_t) + sizeof(float));
 }
 
-template <int DT, int NBLK, bool FULL>
+template <int DT, int NBLK, bool FULL, bool FIN>
 __global__ void __launch_bounds__(kScanThreads, 3) wave_scan_kernel(IndexView ix, WaveView wv, int w,
                                                                  const float* __restrict__ m1,
                                                                  const float* __restrict__ beta,
@@ -442,7 +544,6 @@ __global__ void __launch_bounds__(kScanThreads, 3) wave_scan_kernel(IndexView ix
     const int total = wv.unit_off[(int64_t)w * (ix.nlist + 1) + ix.nlist];
     const int4* units = wv.units + wv.ubase[w];
     const int nsteps_full = (ix.nb + NBLK - 1) / NBLK;
-    const int eseg = seg_lanes(ix.nb);
     const bool want_stats = wv.stats != nullptr;
     // thread 0 claims the next unit and loads its descriptor one unit ahead
     int next_u = 0;
@@ -475,67 +576,56 @@ __global__ void __launch_bounds__(kScanThreads, 3) wave_scan_kernel(IndexView ix
             s_st[tid * 4 + 0] = (unsigned long long)nt;
             s_st[tid * 4 + 1] = s_st[tid * 4 + 2] = s_st[tid * 4 + 3] = 0ull;
         }
-        const int npairs = nq * nt;
-        if (tid < kWarps) {
-            int cnt = 0;
-            for (int h = tid; h * 32 < npairs; h += kWarps) cnt += min(32, npairs - h * 32);
-            s_n[tid] = cnt;
-        }
-        for (int e = tid; e < npairs; e += kScanThreads) {
-            const int g = e / nt, c = e - g * nt;
-            const int h = e >> 5;
-            const int wi = h % kWarps, pos = (h / kWarps) * 32 + (e & 31);
-            sh.key[wi * kWarpCap + pos] = (uint16_t)((g << 8) | c);
-            sh.part[wi * kWarpCap + pos] = 0.f;
-        }
         const bool all_inf = __syncthreads_and(my_inf);
         const int64_t slot_l = ix.list_slot[l];
         const int64_t npad = ix.list_slot[l + 1] - slot_l;
         const int64_t ebase = slot_l * ix.Dpad;
         const int32_t slot0 = (int32_t)(slot_l + (int64_t)t * kT);
-        uint16_t* key = sh.key + warp * kWarpCap;
-        float* part = sh.part + warp * kWarpCap;
+        const uint16_t* key = sh.key + warp * kWarpCap;
+        float pd[kG];
         bool ok;
-        if (FULL || all_inf) {
-            // every pair's exact distance through the staged pipeline
-            ok = run_steps<float, NBLK, false>(ix.orig + ebase, npad, t, nt, nq, nsteps_full, ix.nb,
-                                               ix.D, sh, ph, wv.qpad, ix.Dpad, nullptr, nullptr,
-                                               nullptr, wv.status, wv.staged_bytes, want_stats);
+        if (FULL || all_inf || (S <= 1 && !FIN)) {
+            // every pair's exact distance through the staged pipeline (with
+            // no test to run, that is also the pruned search's result)
+            ok = run_steps<float, NBLK, false, false>(ix.orig + ebase, npad, t, nt, nq, nsteps_full, ix.nb,
+                                                      ix.D, sh, ph, wv.qpad, ix.Dpad, nullptr, nullptr,
+                                                      nullptr, nullptr, wv.status, wv.staged_bytes, want_stats,
+                                                      pd);
             if (!ok) break;
+            const int c = warp * 32 + lane;
+#pragma unroll
+            for (int g = 0; g < kG; ++g)
+                if (g < nq) append_uniform(wv, w, s_q[g], c < nt && pd[g] <= s_tau[g], pd[g], slot0 + c, lane);
+            if (want_stats && tid < nq) {
+                s_st[tid * 4 + 2] += (unsigned long long)nt;
+                s_st[tid * 4 + 3] += (unsigned long long)nt * ix.D;
+            }
+        } else {
+            const E* slab = reinterpret_cast<const E*>(ix.slab) + ebase;
+            const float* scl = DT == DADE_SLAB_FP8E4M3 ? ix.scale : nullptr;
+            if (FIN)
+                ok = run_steps<E, NBLK, true, true>(slab, npad, t, nt, nq, S, ix.nb, ix.D, sh, ph, wv.qrot,
+                                                    ix.Dpad, m1, beta, scl, ix.eps ? ix.eps + slot0 : nullptr,
+                                                    wv.status, wv.staged_bytes, want_stats, pd);
+            else
+                ok = run_steps<E, NBLK, true, false>(slab, npad, t, nt, nq, S - 1, ix.nb, ix.D, sh, ph, wv.qrot,
+                                                     ix.Dpad, m1, beta, scl, nullptr, wv.status,
+                                                     wv.staged_bytes, want_stats, pd);
+            if (!ok) break;
+            // survivors: exact distance from the original vector, one lane each
             const int n = s_n[warp];
             for (int base = 0; base < n; base += 32) {
                 const int i = base + lane;
                 const bool valid = i < n;
                 const int kk = valid ? key[i] : 0;
-                const int g = kk >> 8;
-                const float d = valid ? part[i] : 0.f;
-                append_any(wv, w, s_q[g], valid && d <= s_tau[g], d, slot0 + (kk & 255), lane);
-                if (want_stats && valid) {
-                    atomicAdd(&s_st[g * 4 + 2], 1ull);
-                    atomicAdd(&s_st[g * 4 + 3], (unsigned long long)ix.D);
-                }
-            }
-        } else {
-            const E* slab = reinterpret_cast<const E*>(ix.slab) + ebase;
-            ok = run_steps<E, NBLK, true>(slab, npad, t, nt, nq, S - 1, ix.nb, ix.D, sh, ph, wv.qrot,
-                                          ix.Dpad, m1, beta,
-                                          DT == DADE_SLAB_FP8E4M3 ? ix.scale : nullptr, wv.status,
-                                          wv.staged_bytes, want_stats);
-            if (!ok) break;
-            // survivors: exact distance from the original vector, eseg lanes each
-            const int per = 32 / eseg;
-            const int n = s_n[warp];
-            for (int base = 0; base < n; base += per) {
-                const int i = base + lane / eseg;
-                const bool valid = i < n;
-                const int kk = valid ? key[i] : 0;
                 const int g = kk >> 8, c = kk & 255;
                 const int q = s_q[g];
-                const float d = exact_coop(ix.orig + ebase + ((int64_t)t * kT + c) * kBlock, npad,
-                                           wv.qpad + (int64_t)q * ix.Dpad, valid, ix.nb, lane, eseg);
-                const bool lead = valid && (lane & (eseg - 1)) == 0;
-                append_any(wv, w, q, lead && d <= s_tau[g], d, slot0 + c, lane);
-                if (want_stats && lead) {
+                float d = 0.f;
+                if (valid)
+                    d = exact_distance(ix.orig + ebase + ((int64_t)t * kT + c) * kBlock, npad,
+                                       wv.qpad + (int64_t)q * ix.Dpad, ix.nb);
+                append_any(wv, w, q, valid && d <= s_tau[g], d, slot0 + c, lane);
+                if (want_stats && valid) {
                     atomicAdd(&s_st[g * 4 + 2], 1ull);
                     atomicAdd(&s_st[g * 4 + 3], (unsigned long long)ix.D);
                 }
@@ -952,12 +1042,12 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
 }
 
 // ------------------------------------------------------------ launchers
-template <int DT, int NBLK, bool FULL>
+template <int DT, int NBLK, bool FULL, bool FIN>
 cudaError_t launch_scan_t(const IndexView& ix, const WaveView& wv, int w, const float* m1,
                           const float* beta, int S, cudaStream_t st) {
     constexpr int SMEM = scan_smem_bytes<NBLK>();
     static int grid = 0;
-    auto kern = wave_scan_kernel<DT, NBLK, FULL>;
+    auto kern = wave_scan_kernel<DT, NBLK, FULL, FIN>;
     if (grid == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
@@ -1006,10 +1096,11 @@ cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStre
 cudaError_t launch_wave_scan(const IndexView& ix, const WaveView& wv, int w, bool full,
                              int delta_d, const float* m1, const float* beta, int S,
                              cudaStream_t st) {
-    if (full) return launch_scan_t<DADE_SLAB_F32, 4, true>(ix, wv, w, m1, beta, S, st);
+    if (full) return launch_scan_t<DADE_SLAB_F32, 4, true, false>(ix, wv, w, m1, beta, S, st);
 #define DADE_SCAN_CASE(DT, NB)                                                               \
     if (ix.dtype == DT && delta_d == NB * kBlock)                                            \
-        return launch_scan_t<DT, NB, false>(ix, wv, w, m1, beta, S, st);
+        return wv.final_test ? launch_scan_t<DT, NB, false, true>(ix, wv, w, m1, beta, S, st)   \
+                             : launch_scan_t<DT, NB, false, false>(ix, wv, w, m1, beta, S, st);
     DADE_SCAN_CASE(DADE_SLAB_F32, 1)
     DADE_SCAN_CASE(DADE_SLAB_F32, 2)
     DADE_SCAN_CASE(DADE_SLAB_F32, 4)
@@ -1059,3 +1150,4 @@ cudaError_t launch_collect(const IndexView& ix, const WaveView& wv, int w, int d
 }
 
 }  // namespace dade
+

@@ -17,12 +17,14 @@ struct IndexView {
     const int64_t* list_slot;  // nlist + 1
     const int32_t* list_size;  // nlist
     const float* scale;        // FP8 per-dimension scale (Dpad)
+    const float* eps;          // per slot: quantisation error norm (null for FP32 slabs)
     int32_t D, Dpad, nb, nlist, dtype;
 };
 
 struct WaveView {
     int64_t B;
     int32_t P, Kmax, first_wave, n_waves, wave_shift;
+    int32_t final_test;       // PRUNE: test the completed rotated distance before the exact one
     const float* qrot;        // B x Dpad rotated queries
     const float* qpad;        // B x Dpad original queries, zero padded
     const int32_t* probes;    // B x P

@@ -73,6 +73,7 @@ size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* 
     v.Kmax = Kmax;
     v.first_wave = f;
     v.wave_shift = g;
+    v.final_test = o.final_test != 0;
     v.n_waves = nw;
     v.qrot = c.take<float>((size_t)B * idx->Dpad);
     v.qpad = c.take<float>((size_t)B * idx->Dpad);
@@ -180,6 +181,7 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     ix.list_slot = idx->list_slot_dev.as<int64_t>();
     ix.list_size = idx->list_size_dev.as<int32_t>();
     ix.scale = idx->scale_dev.as<float>();
+    ix.eps = idx->dtype == DADE_SLAB_F32 ? nullptr : idx->eps_dev.as<float>();
     ix.D = idx->D;
     ix.Dpad = idx->Dpad;
     ix.nb = idx->nb;

@@ -47,7 +47,7 @@ class Request:
 
 class _Slot:
     def __init__(self, torch, G, idx, D, bucket_sizes, max_K, max_nprobe, delta_d, mode, first_wave, ws_bytes,
-                 growth=0):
+                 growth=0, final_test=False):
         dev = torch.device("cuda")
         self.stream = torch.cuda.Stream()
         B = max(bucket_sizes)
@@ -68,17 +68,18 @@ class _Slot:
         self.batch = None
         self.bucket = 0
         self.bytes = 0
-        self.args = (G, idx, max_K, max_nprobe, delta_d, mode, first_wave, growth)
+        self.args = (G, idx, max_K, max_nprobe, delta_d, mode, first_wave, growth, final_test)
 
     def enqueue(self, torch, b: int):
         """H2D copies, the search over the first b rows, D2H copies."""
-        G, idx, max_K, max_nprobe, delta_d, mode, first_wave, growth = self.args
+        G, idx, max_K, max_nprobe, delta_d, mode, first_wave, growth, final_test = self.args
         self.q[:b].copy_(self.q_h[:b], non_blocking=True)
         self.k[:b].copy_(self.k_h[:b], non_blocking=True)
         self.n[:b].copy_(self.n_h[:b], non_blocking=True)
         G.dade_search(idx, self.q[:b], self.k[:b], self.n[:b], delta_d, self.ids, self.d, max_K=max_K,
                       max_nprobe=max_nprobe, mode=mode, first_wave=first_wave, status=self.status,
-                      workspace=self.ws, stream=torch.cuda.current_stream(), wave_growth_log2=growth)
+                      workspace=self.ws, stream=torch.cuda.current_stream(), wave_growth_log2=growth,
+                      final_test=final_test)
         self.ids_h[: b * max_K].copy_(self.ids[: b * max_K], non_blocking=True)
         self.d_h[: b * max_K].copy_(self.d[: b * max_K], non_blocking=True)
 
@@ -86,7 +87,7 @@ class _Slot:
 class Server:
     def __init__(self, G, idx, delta_d: int, max_K: int, max_nprobe: int, buckets=(16, 64, 256, 1024),
                  slots: int = 2, mem_budget: int | None = None, use_graphs: bool = True,
-                 mode: str = "prune", first_wave: int = 1, wave_growth_log2: int = 0):
+                 mode: str = "prune", first_wave: int = 1, wave_growth_log2: int = 0, final_test: bool = False):
         import torch
         self.torch, self.G, self.idx = torch, G, idx
         info = G.dade_index_info_get(idx)
@@ -101,7 +102,7 @@ class Server:
         if self.mem_budget < self.ws_of[self.buckets[0]]:
             raise ValueError("memory budget below the smallest batch's workspace")
         self.slots = [_Slot(torch, G, idx, self.D, self.buckets, max_K, max_nprobe, delta_d, mode, first_wave,
-                            ws_max, wave_growth_log2) for _ in range(slots)]
+                            ws_max, wave_growth_log2, final_test) for _ in range(slots)]
         self.use_graphs = use_graphs
         # warm up every (slot, bucket): first launches configure kernels; then capture
         for s in self.slots:

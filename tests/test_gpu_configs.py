@@ -32,12 +32,12 @@ def G():
     return G
 
 
-def _oracle_search(inp, Q, K, nprobe, delta_d, amb="exact"):
+def _oracle_search(inp, Q, K, nprobe, delta_d, amb="exact", final_rel=np.inf):
     oidx = inp["oidx"]
     P = int(np.max(nprobe))
     pr = oidx.probe(oidx.rotate_queries(Q), P)
     ids, d, st = search.search(oidx, Q, pr, nprobe, K, delta_d, inp["m1"].astype(np.float64),
-                               inp["beta"].astype(np.float64), amb=H.AMB[amb])
+                               inp["beta"].astype(np.float64), amb=H.AMB[amb], final_rel=final_rel)
     return ids, d, st, pr
 
 
@@ -48,12 +48,13 @@ def test_gist_shaped_bf16_slabs(G):
                           prerotate=True)
     idx = H.build_gpu(G, None, inp, 64, dtype="bf16", delta_d=32)
     Qr = inp["rot"](Q)
-    ids, d, st, pr = _oracle_search(inp, Qr, 100, 8, 32)
-    out = H.gpu_search(G, idx, Qr, 100, 8, 32, probe_in=pr, want=("stats",))
-    parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, 100, amb=st[:, 4], min_strict=0.9)
-    un = st[:, 4] == 0
-    assert np.array_equal(out["stats"][un], st[un, :4])
-    assert st[:, 1].sum() > 0
+    for final in (False, True):
+        ids, d, st, pr = _oracle_search(inp, Qr, 100, 8, 32, final_rel=search.FINAL_REL if final else np.inf)
+        out = H.gpu_search(G, idx, Qr, 100, 8, 32, probe_in=pr, final_test=final, want=("stats",))
+        parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, 100, amb=st[:, 4], min_strict=0.9)
+        un = st[:, 4] == 0
+        assert np.array_equal(out["stats"][un], st[un, :4])
+        assert st[:, 1].sum() > 0
     idx.close()
 
 
@@ -67,9 +68,13 @@ def test_vmf_shaped_fp8_slabs_uneven_requests(G):
     rng = np.random.default_rng(9)
     K = rng.integers(1, 101, len(Q)).astype(np.int32)
     npb = rng.integers(8, 17, len(Q)).astype(np.int32)
-    ids, d, st, pr = _oracle_search(inp, Qr, K, npb, 16)
-    out = H.gpu_search(G, idx, Qr, K, npb, 16, probe_in=pr, max_K=100, max_nprobe=16)
-    parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, K, amb=st[:, 4], min_strict=0.9)
+    for final in (False, True):
+        ids, d, st, pr = _oracle_search(inp, Qr, K, npb, 16, final_rel=search.FINAL_REL if final else np.inf)
+        out = H.gpu_search(G, idx, Qr, K, npb, 16, probe_in=pr, max_K=100, max_nprobe=16, final_test=final,
+                           want=("stats",))
+        parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, K, amb=st[:, 4], min_strict=0.9)
+        un = st[:, 4] == 0
+        assert np.array_equal(out["stats"][un], st[un, :4])
     idx.close()
 
 

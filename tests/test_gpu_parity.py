@@ -156,6 +156,25 @@ def test_wave_growth_schedules(G, tiny_pre, fw, g):
     assert np.array_equal(out["stats"][un], st[un, :4])
 
 
+def test_final_test_on_completed_distance(G, tiny_pre):
+    """With the test on the completed rotated distance both sides drop the
+    same candidates before the exact distance; results do not change."""
+    s = tiny_pre
+    oidx = s["inp"]["oidx"]
+    pr = oidx.probe(oidx.rotate_queries(s["Q"]), 8)
+    args = (oidx, s["Q"], pr, 8, 10, 16, s["inp"]["m1"].astype(np.float64), s["inp"]["beta"].astype(np.float64))
+    ids, d, st = search.search(*args, first_wave=2, amb=H.AMB["exact"], final_rel=search.FINAL_REL)
+    out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, first_wave=2, final_test=True,
+                       want=("stats",))
+    off = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, first_wave=2, want=("stats",))
+    assert out["status"] == 0
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb=st[:, 4], min_strict=s["strict"])
+    un = st[:, 4] == 0
+    assert np.array_equal(out["stats"][un], st[un, :4])
+    assert np.array_equal(out["ids"], off["ids"]) and np.array_equal(out["dists"], off["dists"])
+    assert out["stats"][:, 2].sum() < off["stats"][:, 2].sum()
+
+
 def test_ragged_K_and_nprobe(G, tiny_pre):
     s = tiny_pre
     rng = np.random.default_rng(5)
@@ -277,6 +296,27 @@ def test_save_load_roundtrip(G, tiny_setup, tmp_path):
     with pytest.raises(_lib.DadeError):
         G.dade_index_load(str(p))
     idx2.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_save_load_roundtrip_quantised_slabs(G, tmp_path, dtype):
+    # the quantisation error norms travel with the file: identical results
+    # and identical pruning statistics after a reload
+    X, Q, T, cfg = synth.workload("tiny")
+    mu, R, _ = G.dade_train_rotation(X)
+    idx = G.ivf_build(X, mu, R, cfg["nlist"], kmeans_iters=4, seed=3, dtype=dtype)
+    G.dade_fit_correction(idx, T[:500], 10, 8, 16)
+    p = tmp_path / f"tiny_{dtype}.dade"
+    G.dade_index_save(idx, str(p))
+    idx2 = G.dade_index_load(str(p))
+    a = H.gpu_search(G, idx, Q, 10, 8, 16, want=("stats",))
+    b = H.gpu_search(G, idx2, Q, 10, 8, 16, want=("stats",))
+    assert a["status"] == 0 and b["status"] == 0
+    for k in ("ids", "dists", "stats"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["stats"][:, 1].sum() > 0
+    idx2.close()
+    idx.close()
 
 
 def test_library_build_and_fit_end_to_end(G):

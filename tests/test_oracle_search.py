@@ -23,27 +23,31 @@ def _worked_index(order_b=(3, 2, 4)):
 
 
 def test_worked_example_by_hand():
-    """Hand evaluation with m1 = 1.75, beta = 0 (prune iff 1.75 dis'_1 > tau).
+    """Hand evaluation with m1 = 1.75, beta = 0 (prune iff 1.75 dis'_1 > tau),
+    then the test on the completed distance: prune iff dis'_2 > 1.001 tau
+    (FP64 storage: no quantisation error).
 
     Probe order: list 0 = {0, 1}, then list 1 = {3, 2, 4}.
     SEQUENTIAL: 0 -> dis 2 (tau inf); 1 -> dis 4, queue full, tau = 4;
-      3: 1.75 > 4? no -> dis 3 enters, tau = 3; 2: 3.5 > 3 -> pruned;
-      4: 7 > 3 -> pruned.  Result (0, 2), (3, 3); pruned 2, exact 3;
-      dims 4 + 4 + 4 + 2 + 2 = 16.
+      3: 1.75 > 4? no; 3 > 4.004? no -> dis 3 enters, tau = 3;
+      2: 3.5 > 3 -> pruned; 4: 7 > 3 -> pruned.  Result (0, 2), (3, 3);
+      pruned 2, exact 3; dims 4 + 4 + 4 + 2 + 2 = 16.
     WAVES (first wave 1): wave 0 = list 0 at tau inf -> 2, 4, tau = 4;
-      wave 1 at tau 4: 3 -> no (dis 3); 2: 3.5 > 4? no -> dis 11 (does not
-      enter); 4: 7 > 4 -> pruned.  Same result; pruned 1, exact 4, dims 18.
-    FROZEN tau = 3.5: 0: 1.75 > 3.5? no -> 2; 1: 7 > 3.5 pruned; 3 -> 3;
-      2: 3.5 > 3.5? no -> 11 (> tau, not kept); 4 pruned.  Result (0,2),(3,3);
-      pruned 2, exact 3, dims 16.
+      wave 1 at tau 4: 3 -> no, 3 <= 4.004 (dis 3); 2: 3.5 > 4? no, but
+      11 > 4.004 -> pruned at d = D; 4: 7 > 4 -> pruned.  Same result;
+      pruned 2, exact 3, dims 4 + 4 + 4 + 4 + 2 = 18.
+    FROZEN tau = 3.5: 0: 1.75 > 3.5? no, 2 <= 3.5035 -> 2; 1: 7 > 3.5
+      pruned; 3 -> 3; 2: 3.5 > 3.5? no, 11 > 3.5035 -> pruned at d = D;
+      4 pruned.  Result (0,2),(3,3); pruned 3, exact 2, dims 16.
     """
     idx = _worked_index()
     Q = np.zeros((1, 4), dtype=np.float32)
     probes = np.array([[0, 1]], dtype=np.int32)
     m1, beta = np.array([1.75]), np.array([0.0])
-    for mode, tau, st_exp in [("sequential", None, [5, 2, 3, 16]), ("waves", None, [5, 1, 4, 18]),
-                              ("frozen", np.array([3.5]), [5, 2, 3, 16])]:
-        ids, d, st = search.search(idx, Q, probes, 2, 2, 2, m1, beta, mode=mode, tau=tau)
+    for mode, tau, st_exp in [("sequential", None, [5, 2, 3, 16]), ("waves", None, [5, 2, 3, 18]),
+                              ("frozen", np.array([3.5]), [5, 3, 2, 16])]:
+        ids, d, st = search.search(idx, Q, probes, 2, 2, 2, m1, beta, mode=mode, tau=tau,
+                                   final_rel=search.FINAL_REL)
         assert list(ids[0]) == [0, 3], mode
         assert list(d[0]) == [2.0, 3.0], mode
         assert list(st[0][:4]) == st_exp, mode
@@ -92,11 +96,16 @@ def test_pruning_off_equals_brute_force_over_probed_candidates(small, mode):
     idx, Q = small["idx"], small["Q"]
     probes = idx.probe(idx.rotate_queries(Q), 4)
     m1, beta = search.disabled_tables(search.n_steps(small["D"], 8))
-    ids, d, st = search.search(idx, Q, probes, 4, 10, 8, m1, beta, mode=mode)
+    ids, d, st = search.search(idx, Q, probes, 4, 10, 8, m1, beta, mode=mode, final_rel=np.inf)
     for b, (ri, rd) in enumerate(_probed_brute_force(idx, Q, probes, 10)):
         # FP64 sums in another order: equal up to rounding
         assert np.array_equal(ids[b], ri) and np.allclose(d[b], rd, rtol=1e-13, atol=0)
     assert np.all(st[:, 1] == 0) and np.all(st[:, 2] == st[:, 0])
+    # with the test on the completed distance: same result, fewer exact distances
+    ids2, d2, st2 = search.search(idx, Q, probes, 4, 10, 8, m1, beta, mode=mode, final_rel=search.FINAL_REL)
+    assert np.array_equal(ids2, ids) and np.array_equal(d2, d)
+    assert st2[:, 2].sum() < st[:, 2].sum()
+    assert np.array_equal(st2[:, 3], st[:, 3])  # pruned at d = D still scanned D dims
 
 
 def test_all_lists_probed_equals_exact_knn(small):
@@ -205,3 +214,56 @@ def test_integer_data_gives_integer_distances():
     ids, d, _ = search.search(idx, Q, np.zeros((4, 1), np.int32), 1, 20, 8,
                               *search.disabled_tables(2))
     assert np.all(d == np.rint(d)) and np.all(d < 2 ** 24)
+
+
+@pytest.fixture(scope="module")
+def rotated():
+    """PCA-rotated small set stored in every slab precision."""
+    rng = np.random.default_rng(23)
+    D, N, nlist = 32, 4000, 16
+    X = np.rint((rng.standard_normal((N, D)) * np.linspace(40, 3, D)) + 100).astype(np.float32)
+    Q = np.rint((rng.standard_normal((30, D)) * np.linspace(40, 3, D)) + 100).astype(np.float32)
+    from oracle import pca
+    mu, Rm, _ = pca.train_rotation(X)
+    Xr = pca.rotate(X, mu, Rm)
+    C, _, _ = ivf.kmeans(Xr, np.arange(nlist), 4)
+    a = ivf.assign(Xr, C)
+    idx = {dt: search.OracleIndex(X, mu, Rm, C, a, dtype=dt) for dt in ("f32", "bf16", "fp8")}
+    return dict(X=X, Q=Q, idx=idx, D=D, nlist=nlist, Xr=Xr)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_quantisation_error_bound_holds_for_every_pair(rotated, dtype):
+    # ||q' - x~|| <= ||q' - x'|| + ||x' - x~|| (triangle inequality), so a
+    # candidate whose rotated distance is <= tau has dis'_S <= (sqrt(tau) + e_x)^2.
+    idx = rotated["idx"][dtype]
+    Qr = idx.rotate_queries(rotated["Q"])
+    assert np.all(idx.xerr > 0)
+    ps = ((Qr[:, None, :] - idx.Xs[None, :, :]) ** 2).sum(-1)
+    dr = ((Qr[:, None, :] - rotated["Xr"][None, :, :]) ** 2).sum(-1)
+    bound = (np.sqrt(dr) + idx.xerr[None, :]) ** 2
+    assert np.all(ps <= bound * (1 + 1e-12))
+    # and e_x is no larger than it must be: some pair uses most of the slack
+    assert np.max((ps - dr) / (bound - dr)) > 0.5
+    assert np.array_equal(rotated["idx"]["f32"].xerr, np.zeros(len(rotated["X"])))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_final_test_never_changes_the_result(rotated, dtype):
+    # It drops only candidates whose exact distance exceeds tau, which could
+    # not enter the result queue: results are identical with and without it,
+    # under every schedule, with the learned tests on or off.
+    idx, Q = rotated["idx"][dtype], rotated["Q"]
+    probes = idx.probe(idx.rotate_queries(Q), 6)
+    S = search.n_steps(rotated["D"], 8)
+    tabs = [search.disabled_tables(S), (np.full(S - 1, 1.3), np.full(S - 1, 50.0))]
+    for m1, beta in tabs:
+        for mode, fw, g in [("sequential", 1, 1), ("waves", 1, 1), ("waves", 2, 30)]:
+            a = search.search(idx, Q, probes, 6, 10, 8, m1, beta, mode=mode, first_wave=fw, growth=g,
+                              final_rel=np.inf)
+            b = search.search(idx, Q, probes, 6, 10, 8, m1, beta, mode=mode, first_wave=fw, growth=g,
+                              final_rel=search.FINAL_REL)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (mode, fw, g)
+            assert b[2][:, 2].sum() <= a[2][:, 2].sum()
+            if not np.any(m1):  # learned tests off: the final test is the only one
+                assert b[2][:, 2].sum() < a[2][:, 2].sum()
