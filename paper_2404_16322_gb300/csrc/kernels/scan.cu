@@ -312,19 +312,37 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
     float* part = sh.part + warp * kWarpCap;
     const int c_own = warp * 32 + lane;
     const bool own_valid = c_own < nt;
-    for (; k < nsteps; ++k) {
-        const int b0 = k * NBLK, nbk = min(NBLK, nb - b0), w8 = nbk * kBlock;
-        // the step's query values (and FP8 scales) for every query of the unit
-        for (int e = tid; e < nq * kQs; e += kScanThreads) {
-            const int g = e / kQs, j = e - g * kQs;
-            sh.qs[g * kQsPad + j] = j < w8 ? qsrc[(int64_t)sh.q[g] * Dpad + b0 * kBlock + j] : 0.f;
+    // the query values (and FP8 scales) of step k for every query of the
+    // unit: each thread handles up to two values (and one scale); step k + 1's
+    // are loaded into registers during step k and stored after its last read
+    float qv_next[2], sc_next = 0.f;
+    auto load_vals = [&](int kk) {
+        const int b0 = kk * NBLK, w8 = min(NBLK, nb - b0) * kBlock;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = tid + h * kScanThreads, g = e / kQs, j = e % kQs;
+            qv_next[h] = g < nq && j < w8 ? __ldg(qsrc + (int64_t)sh.q[g] * Dpad + b0 * kBlock + j) : 0.f;
         }
-        if (scale && tid < kQs) sh.sc[tid] = tid < w8 ? scale[b0 * kBlock + tid] : 0.f;
+        if (scale) sc_next = tid < w8 ? __ldg(scale + b0 * kBlock + tid) : 0.f;
+    };
+    auto store_vals = [&]() {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = tid + h * kScanThreads, g = e / kQs, j = e % kQs;
+            if (g < nq) sh.qs[g * kQsPad + j] = qv_next[h];
+        }
+        if (scale && tid < kQs) sh.sc[tid] = sc_next;
+    };
+    load_vals(0);
+    store_vals();
+    for (; k < nsteps; ++k) {
+        const int b0 = k * NBLK, nbk = min(NBLK, nb - b0);
         bool got = mbar_wait(sh.bar + (k & 1), (phase_bits >> (k & 1)) & 1u, status);
         phase_bits ^= 1u << (k & 1);
         if (!__syncthreads_and(got)) return false;
         pending_next = k + 1 < nsteps;
         if (tid == 0 && pending_next) issue(k + 1);
+        if (pending_next) load_vals(k + 1);
         const E* bk = reinterpret_cast<const E*>(sh.buf0 + (k & 1) * sh.buf_bytes);
         const int dims_k = min((k + 1) * NBLK * kBlock, D);
         const bool final_k = FINAL && k == nsteps - 1;
@@ -351,8 +369,13 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
             if (PRUNE) {
                 // test every pair; the survivors of (this warp, query g) go
                 // to list (warp + g) mod kWarps, so every list gets a share
-                // of every warp's candidates and of every query
+                // of every warp's candidates and of every query.  Pass 1
+                // counts them (lane g keeps query g's count) and reserves
+                // every query's space with one atomic instruction; pass 2
+                // writes them.
                 const float e_own = FINAL && final_k && eps_tile && own_valid ? eps_tile[c_own] : 0.f;
+                uint32_t keep_bits = 0u;
+                int mine = 0;
 #pragma unroll
                 for (int g = 0; g < kG; ++g) {
                     if (g < nq) {
@@ -364,24 +387,30 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
                             cut = fmaf(mm, pd[g], bt) > sh.tau[g];
                         }
                         const bool keep = own_valid && !cut;
-                        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                        if (bal) {
-                            const int v = (warp + g) & (kWarps - 1);
-                            int base = 0;
-                            if (lane == 0) base = atomicAdd(&sh.n[v], __popc(bal));
-                            base = __shfl_sync(0xffffffffu, base, 0);
-                            if (keep) {
-                                const int pos = v * kWarpCap + base + __popc(bal & lanemask_lt());
-                                sh.key[pos] = (uint16_t)((g << 8) | c_own);
-                                sh.part[pos] = pd[g];
-                            }
-                        }
+                        keep_bits |= (uint32_t)keep << g;
+                        const int cnt = __popc(__ballot_sync(0xffffffffu, keep));
+                        if (lane == g) mine = cnt;
                         if (want_stats) {
                             const int np = __popc(__ballot_sync(0xffffffffu, own_valid && cut));
                             if (lane == 0 && np) {
                                 atomicAdd(&sh.st[g * 4 + 1], (unsigned long long)np);
                                 atomicAdd(&sh.st[g * 4 + 3], (unsigned long long)np * dims_k);
                             }
+                        }
+                    }
+                }
+                int base_mine = 0;
+                if (lane < nq && mine) base_mine = atomicAdd(&sh.n[(warp + lane) & (kWarps - 1)], mine);
+#pragma unroll
+                for (int g = 0; g < kG; ++g) {
+                    if (g < nq) {
+                        const bool keep = (keep_bits >> g) & 1u;
+                        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                        const int base = __shfl_sync(0xffffffffu, base_mine, g);
+                        if (keep) {
+                            const int pos = ((warp + g) & (kWarps - 1)) * kWarpCap + base + __popc(bal & lanemask_lt());
+                            sh.key[pos] = (uint16_t)((g << 8) | c_own);
+                            sh.part[pos] = pd[g];
                         }
                     }
                 }
@@ -439,6 +468,7 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
             if (lane == 0) sh.n[warp] = out;
         }
         __syncthreads();
+        if (pending_next) store_vals();  // every read of step k's values is done
         if (PRUNE) {
             int live = 0;
             for (int w = 0; w < kWarps; ++w) live |= sh.n[w];
