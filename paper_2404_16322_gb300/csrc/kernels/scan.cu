@@ -236,14 +236,14 @@ __device__ __forceinline__ Unit unpack_unit(int4 d) {
 }
 
 // ------------------------------------------------------------ step pipeline
-// A unit's (query, candidate) pairs are split over the warps in one flat list
-// per warp: pair e = g * nt + c (query g of the unit, candidate c of the tile)
-// belongs to the 32-pair chunk e / 32, and chunk h goes to warp h % kWarps.
-// Each warp compacts its own list after every test, so its 32-lane chunks
-// stay full whichever queries the live pairs belong to; interleaving whole
-// chunks keeps the warps' lists about equally long while the lanes of a
-// chunk read consecutive candidates (no shared-memory bank conflicts).  A
-// pair is stored as the key g << 8 | c (kT = 256) and its partial distance.
+// A unit's first step is dense (thread c scores candidate c of the tile
+// against every query of the unit).  The (query, candidate) pairs that
+// survive it live in one list per warp: the survivors of (warp w's
+// candidates, query g) go to list (w + g) mod kWarps, so the lists are about
+// equally long, and each warp compacts its own list after every later test,
+// keeping its 32-lane chunks full whichever queries the live pairs belong
+// to.  A pair is stored as the key g << 8 | c (kT <= 256) and its partial
+// distance.
 constexpr int kQs = 4 * kBlock;     // widest step (Delta_d = 32) in floats
 constexpr int kQsPad = kQs + 4;     // query rows 16 B apart in bank terms
 constexpr int kWarpCap = kG * kT / kWarps;
@@ -313,13 +313,14 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
     const int c_own = warp * 32 + lane;
     const bool own_valid = c_own < nt;
     // the query values (and FP8 scales) of step k for every query of the
-    // unit: each thread handles up to two values (and one scale); step k + 1's
+    // unit: each thread handles kVals values (and one scale); step k + 1's
     // are loaded into registers during step k and stored after its last read
-    float qv_next[2], sc_next = 0.f;
+    constexpr int kVals = kG * kQs / kScanThreads;
+    float qv_next[kVals], sc_next = 0.f;
     auto load_vals = [&](int kk) {
         const int b0 = kk * NBLK, w8 = min(NBLK, nb - b0) * kBlock;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kVals; ++h) {
             const int e = tid + h * kScanThreads, g = e / kQs, j = e % kQs;
             qv_next[h] = g < nq && j < w8 ? __ldg(qsrc + (int64_t)sh.q[g] * Dpad + b0 * kBlock + j) : 0.f;
         }
@@ -327,7 +328,7 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
     };
     auto store_vals = [&]() {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kVals; ++h) {
             const int e = tid + h * kScanThreads, g = e / kQs, j = e % kQs;
             if (g < nq) sh.qs[g * kQsPad + j] = qv_next[h];
         }
@@ -535,7 +536,7 @@ constexpr int scan_smem_bytes() {
 }
 
 template <int DT, int NBLK, bool FULL, bool FIN>
-__global__ void __launch_bounds__(kScanThreads, 3) wave_scan_kernel(IndexView ix, WaveView wv, int w,
+__global__ void __launch_bounds__(kScanThreads, 6) wave_scan_kernel(IndexView ix, WaveView wv, int w,
                                                                  const float* __restrict__ m1,
                                                                  const float* __restrict__ beta,
                                                                  int S) {

@@ -7,8 +7,8 @@
 namespace dade {
 
 constexpr int kG = 16;             // queries per work unit
-constexpr int kT = 256;            // candidates per tile of a bucket
-constexpr int kScanThreads = 256;  // 8 warps, each owns kG / 8 queries
+constexpr int kT = 128;            // candidates per tile of a bucket (one per thread in dense steps)
+constexpr int kScanThreads = 128;  // 4 warps
 
 struct IndexView {
     const void* slab;          // rotated vectors, blocked, slab dtype
