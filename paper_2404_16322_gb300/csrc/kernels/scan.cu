@@ -316,22 +316,27 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
     // unit: each thread handles kVals values (and one scale); step k + 1's
     // are loaded into registers during step k and stored after its last read
     constexpr int kVals = kG * kQs / kScanThreads;
+    static_assert(kScanThreads % kQs == 0, "a thread keeps one column j of the query values");
     float qv_next[kVals], sc_next = 0.f;
+    // this thread's values: column j = tid % kQs of rows g = tid / kQs + h * (kScanThreads / kQs)
+    const int vj = tid % kQs, vg0 = tid / kQs;
+    const float* vsrc[kVals];
+#pragma unroll
+    for (int h = 0; h < kVals; ++h) {
+        const int g = vg0 + h * (kScanThreads / kQs);
+        vsrc[h] = g < nq ? qsrc + (int64_t)sh.q[g] * Dpad + vj : nullptr;
+    }
     auto load_vals = [&](int kk) {
         const int b0 = kk * NBLK, w8 = min(NBLK, nb - b0) * kBlock;
 #pragma unroll
-        for (int h = 0; h < kVals; ++h) {
-            const int e = tid + h * kScanThreads, g = e / kQs, j = e % kQs;
-            qv_next[h] = g < nq && j < w8 ? __ldg(qsrc + (int64_t)sh.q[g] * Dpad + b0 * kBlock + j) : 0.f;
-        }
+        for (int h = 0; h < kVals; ++h)
+            qv_next[h] = vsrc[h] && vj < w8 ? __ldg(vsrc[h] + b0 * kBlock) : 0.f;
         if (scale) sc_next = tid < w8 ? __ldg(scale + b0 * kBlock + tid) : 0.f;
     };
     auto store_vals = [&]() {
 #pragma unroll
-        for (int h = 0; h < kVals; ++h) {
-            const int e = tid + h * kScanThreads, g = e / kQs, j = e % kQs;
-            if (g < nq) sh.qs[g * kQsPad + j] = qv_next[h];
-        }
+        for (int h = 0; h < kVals; ++h)
+            if (vsrc[h]) sh.qs[(vg0 + h * (kScanThreads / kQs)) * kQsPad + vj] = qv_next[h];
         if (scale && tid < kQs) sh.sc[tid] = sc_next;
     };
     load_vals(0);
