@@ -260,6 +260,38 @@ size_t dade_search_workspace_size(const dade_index* idx, int64_t B, int32_t delt
                                   const dade_search_opts* opts);
 
 /* ------------------------------------------------------------------------
+ * Bucket-sharded search (the layout for spreading one index over several
+ * GPUs).  The paper has no counterpart: it searches one index on one CPU.
+ * dade_shard_owners: owner shard (0 .. n_shards-1) of each of the nlist
+ *   buckets, given their sizes (host arrays): buckets in decreasing size
+ *   order, ties by lower bucket id, each to the shard with the fewest
+ *   vectors so far (ties to the lower shard).  Pure host computation.
+ *   Errors: DADE_EINVAL (null pointer, nlist < 1, n_shards outside
+ *   [1, nlist], a negative size).
+ * dade_index_shard: a new index on the current device holding only the
+ *   vectors of the buckets shard `shard` owns (in the same order), with the
+ *   parent's rotation, every centroid (so a query probes the same buckets in
+ *   every shard) and every correction table.  dade_search on it scans the
+ *   owned buckets among the probed ones, with waves and tau of its own.
+ *   *out is set only on success.  Errors: DADE_EINVAL, DADE_ENOMEM,
+ *   DADE_ECUDA.
+ * dade_merge_topk: merges n_parts (<= 32) result lists per query -- part p
+ *   of query b at ids_dev / dists_dev[(p * B + b) * max_K ...], each sorted
+ *   by (distance, id), ids < 0 padding -- into the K_dev[b] best by
+ *   (distance, id) at ids_out_dev / dists_out_dev[b * max_K ...], padded
+ *   with -1 / +inf.  With pruning off in every shard, merging the shards'
+ *   results gives the unsharded result.  Asynchronous on cuda_stream.
+ *   Errors: DADE_EINVAL (n_parts outside [1, 32], max_K outside
+ *   [0, 1024], a null pointer), DADE_ECUDA.
+ * ---------------------------------------------------------------------- */
+dade_status dade_shard_owners(const int64_t* list_size_host, int32_t nlist, int32_t n_shards,
+                              int32_t* owner_out_host);
+dade_status dade_index_shard(const dade_index* idx, int32_t n_shards, int32_t shard, dade_index** out);
+dade_status dade_merge_topk(int32_t n_parts, int64_t B, int32_t max_K, const int32_t* K_dev,
+                            const int64_t* ids_dev, const float* dists_dev, int64_t* ids_out_dev,
+                            float* dists_out_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Index inspection, persistence and release.
  * dade_index_info fills the sizes.  dade_index_centroids copies the
  * nlist x D rotated-space centroids to the host; dade_index_assignment the
@@ -267,8 +299,9 @@ size_t dade_search_workspace_size(const dade_index* idx, int64_t B, int32_t delt
  * nlist bucket sizes (int64, host).
  * dade_index_save writes a versioned binary file (header, rotation, mean,
  * centroids, buckets, slabs, original vectors, ids, quantisation error
- * norms (BF16 / FP8), correction tables, and an FNV-1a checksum); dade_index_load reads it back onto the current device
- * and reproduces identical search results.  Errors: DADE_EIO, DADE_ENOMEM,
+ * norms (BF16 / FP8), correction tables, and an FNV-1a checksum);
+ * dade_index_load reads it back onto the current device and reproduces
+ * identical search results.  Errors: DADE_EIO, DADE_ENOMEM,
  * DADE_ECUDA, DADE_EINVAL.
  * ---------------------------------------------------------------------- */
 typedef struct {

@@ -248,6 +248,31 @@ def dade_index_free(idx: Index) -> None:
     idx.close()
 
 
+def dade_shard_owners(list_sizes, n_shards: int) -> np.ndarray:
+    """Owner shard of each bucket (host computation; no device needed)."""
+    sizes = np.ascontiguousarray(list_sizes, dtype=np.int64)
+    out = np.empty(len(sizes), dtype=np.int32)
+    _check(library().dade_shard_owners(sizes.ctypes.data, len(sizes), int(n_shards), out.ctypes.data))
+    return out
+
+
+def dade_index_shard(idx: Index, n_shards: int, shard: int) -> Index:
+    """The index of one shard's buckets, on the current device."""
+    out = ctypes.c_void_p()
+    _check(library().dade_index_shard(idx.ptr, int(n_shards), int(shard), ctypes.byref(out)))
+    return Index(out.value)
+
+
+def dade_merge_topk(ids, dists, K, ids_out, dists_out, *, max_K: int, stream=None) -> None:
+    """Merge per-part results: ids (int64) / dists (float32) CUDA tensors of
+    n_parts x B x max_K, K a (B,) int32 CUDA tensor; outputs B x max_K."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    n_parts, B = int(ids.shape[0]), int(ids.shape[1])
+    _check(library().dade_merge_topk(n_parts, B, int(max_K), _ptr(K), _ptr(ids), _ptr(dists), _ptr(ids_out),
+                                     _ptr(dists_out), ctypes.c_void_p(s.cuda_stream)))
+
+
 def dade_stage_timing(enable: bool) -> None:
     _check(library().dade_stage_timing(1 if enable else 0))
 

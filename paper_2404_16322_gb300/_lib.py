@@ -61,6 +61,9 @@ SIGNATURES = {
     "dade_index_save": (ctypes.c_int, [c_vp, c_cp]),
     "dade_index_load": (ctypes.c_int, [c_cp, ctypes.POINTER(c_vp)]),
     "dade_index_free": (None, [c_vp]),
+    "dade_shard_owners": (ctypes.c_int, [c_vp, c_i32, c_i32, c_vp]),
+    "dade_index_shard": (ctypes.c_int, [c_vp, c_i32, c_i32, ctypes.POINTER(c_vp)]),
+    "dade_merge_topk": (ctypes.c_int, [c_i32, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dade_stage_timing": (ctypes.c_int, [c_i32]),
     "dade_stage_timing_read": (ctypes.c_int, [c_vp, c_vp, c_vp]),
     "dade_last_error": (c_cp, []),

@@ -76,7 +76,6 @@ dade_status assign_device(const float* xrot, int64_t N, int Dpad, const float* c
 
 }  // namespace
 
-dade_status upload_index_arrays(dade_index* idx);  // abi.cpp
 
 }  // namespace dade
 

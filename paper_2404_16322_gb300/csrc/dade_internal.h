@@ -177,6 +177,15 @@ dade_status search_impl(const dade_index* idx, const float* Q_dev, int64_t B,
 size_t workspace_bytes(const dade_index* idx, int64_t B, int32_t delta_d,
                        const dade_search_opts& opts, const struct CollectArgs* collect);
 
+// Bucket metadata from idx->assign and allocation of the per-slot device
+// arrays (abi.cu); installation of a correction table.
+dade_status upload_index_arrays(dade_index* idx);
+dade_status install_table_public(dade_index* idx, int delta_d, int S, const float* m1, const float* beta);
+// Owner shard of every bucket (sizes balanced greedily, largest first).
+std::vector<int32_t> shard_owners(const std::vector<int64_t>& list_size, int n_shards);
+cudaError_t launch_merge_topk(int n_parts, int64_t B, int Kmax, const int32_t* K, const int64_t* ids,
+                              const float* dists, int64_t* ids_out, float* dists_out, cudaStream_t st);
+
 // Sample collection for the correction fit (replay with pruning off).
 struct CollectArgs {
     int32_t pass;             // 0: count label-1 rows; 1: emit rows

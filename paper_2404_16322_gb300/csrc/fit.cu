@@ -19,7 +19,6 @@
 #include "dade_internal.h"
 
 namespace dade {
-dade_status install_table_public(dade_index* idx, int delta_d, int S, const float* m1, const float* beta);
 }
 
 using namespace dade;
