@@ -200,16 +200,22 @@ __device__ __forceinline__ float exact_distance(const float* xo, int64_t npad, c
     float d = 0.f;
     const int64_t stride = npad * kBlock;
     int b = 0;
-    for (; b + 2 <= nb; b += 2) {
-        float x0[8], x1[8], q0[8], q1[8];
+    for (; b + 4 <= nb; b += 4) {
+        float x0[8], x1[8], x2[8], x3[8], q0[8], q1[8], q2[8], q3[8];
         load8_ro(xo + (int64_t)b * stride, x0);
         load8_ro(xo + (int64_t)(b + 1) * stride, x1);
+        load8_ro(xo + (int64_t)(b + 2) * stride, x2);
+        load8_ro(xo + (int64_t)(b + 3) * stride, x3);
         load_q8(qp + b * kBlock, q0);
         load_q8(qp + (b + 1) * kBlock, q1);
+        load_q8(qp + (b + 2) * kBlock, q2);
+        load_q8(qp + (b + 3) * kBlock, q3);
         d += block_sq(q0, x0);
         d += block_sq(q1, x1);
+        d += block_sq(q2, x2);
+        d += block_sq(q3, x3);
     }
-    if (b < nb) {
+    for (; b < nb; ++b) {
         float x0[8], q0[8];
         load8_ro(xo + (int64_t)b * stride, x0);
         load_q8(qp + b * kBlock, q0);
@@ -535,13 +541,15 @@ __device__ __forceinline__ void append_any(const WaveView& wv, int w, int q, boo
 }
 
 // ------------------------------------------------------------ wave scan
-template <int NBLK>
+// Dynamic shared memory: two slab buffers, and for the pruned path the
+// per-warp pair lists (the full-dimension scan has none).
+template <int NBLK, bool FULL>
 constexpr int scan_smem_bytes() {
-    return 2 * NBLK * kT * kBlock * 4 + kWarps * kWarpCap * (int)(sizeof(uint16_t) + sizeof(float));
+    return 2 * NBLK * kT * kBlock * 4 + (FULL ? 0 : kWarps * kWarpCap * (int)(sizeof(uint16_t) + sizeof(float)));
 }
 
 template <int DT, int NBLK, bool FULL, bool FIN>
-__global__ void __launch_bounds__(kScanThreads, 6) wave_scan_kernel(IndexView ix, WaveView wv, int w,
+__global__ void __launch_bounds__(kScanThreads, (NBLK <= 2 && !FULL) ? 7 : 6) wave_scan_kernel(IndexView ix, WaveView wv, int w,
                                                                  const float* __restrict__ m1,
                                                                  const float* __restrict__ beta,
                                                                  int S) {
@@ -561,8 +569,8 @@ __global__ void __launch_bounds__(kScanThreads, 6) wave_scan_kernel(IndexView ix
     StepShared sh;
     sh.buf0 = smem;
     sh.buf_bytes = BUF;
-    sh.key = reinterpret_cast<uint16_t*>(smem + 2 * BUF);
-    sh.part = reinterpret_cast<float*>(smem + 2 * BUF + kWarps * kWarpCap * sizeof(uint16_t));
+    sh.key = FULL ? nullptr : reinterpret_cast<uint16_t*>(smem + 2 * BUF);
+    sh.part = FULL ? nullptr : reinterpret_cast<float*>(smem + 2 * BUF + kWarps * kWarpCap * sizeof(uint16_t));
     sh.bar = bar;
     sh.n = s_n;
     sh.st = s_st;
@@ -1081,7 +1089,7 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
 template <int DT, int NBLK, bool FULL, bool FIN>
 cudaError_t launch_scan_t(const IndexView& ix, const WaveView& wv, int w, const float* m1,
                           const float* beta, int S, cudaStream_t st) {
-    constexpr int SMEM = scan_smem_bytes<NBLK>();
+    constexpr int SMEM = scan_smem_bytes<NBLK, FULL>();
     static int grid = 0;
     auto kern = wave_scan_kernel<DT, NBLK, FULL, FIN>;
     if (grid == 0) {

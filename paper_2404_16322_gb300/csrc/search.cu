@@ -238,7 +238,10 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
             DADE_CUDA_TRY(cudaEventCreate(&e1));
             DADE_CUDA_TRY(cudaEventRecord(e0, st));
         }
-        DADE_CUDA_TRY(launch_wave_scan(ix, v, w, full || S <= 1, delta_d, m1, beta, S, st));
+        // wave 0 has tau = +inf for every query (no frozen tau): every
+        // candidate's exact distance, through the full-scan kernel
+        const bool exact_wave = full || S <= 1 || (w == 0 && o.tau_dev == nullptr);
+        DADE_CUDA_TRY(launch_wave_scan(ix, v, w, exact_wave, delta_d, m1, beta, S, st));
         if (timed) {
             DADE_CUDA_TRY(cudaEventRecord(e1, st));
             std::lock_guard<std::mutex> lk(tm.mu);
