@@ -37,6 +37,15 @@ NPROBES = [8, 16, 24, 32, 48, 64, 96, 128, 192, 256]
 DELTAS = [8, 16, 32]
 SERVING_RATES = [200_000, 1_000_000, 3_000_000]
 METRIC = "QPS at recall@10>=0.95 (estimate-and-prune IVF search, SIFT-shaped 1M x 128, nlist 4096, K 100)"
+# --workload gist1m: the GIST-shaped set (1M x 960, strong spectral decay,
+# 1,000 queries, BF16 slabs for the estimate, FP32 exact distances)
+WORKLOAD_INFO = {
+    "sift1m": dict(metric=METRIC, slabs="f32",
+                   desc="sift1m-shaped: N={N}, D=128 integer [0,255], 256-comp mixture lambda~i^-0.8"),
+    "gist1m": dict(metric="QPS at recall@10>=0.95 (estimate-and-prune IVF search, GIST-shaped 1M x 960, nlist 4096, "
+                          "K 100, BF16 slabs)", slabs="bf16",
+                   desc="gist1m-shaped: N={N}, D=960, 512-comp mixture lambda~i^-1.3"),
+}
 
 
 def parse():
@@ -50,6 +59,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-sample-queries", type=int, default=400)
+    ap.add_argument("--workload", default="sift1m", choices=sorted(WORKLOAD_INFO),
+                    help="sift1m (the benchmark line) or gist1m")
+    ap.add_argument("--slabs", default=None, choices=["f32", "bf16", "fp8"],
+                    help="slab precision (default: f32 for sift1m, bf16 for gist1m)")
     ap.add_argument("--profile", default=None,
                     help="NPROBE,DELTA_D[,FIRST_WAVE[,GROWTH]]: skip the sweep and baselines; run W + K steps of that "
                          "configuration inside the NVTX range 'dade_timed' (for ncu captures)")
@@ -106,9 +119,9 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(n=None, nq=None):
+def make_workload(n=None, nq=None, name="sift1m"):
     import synth
-    X, Q, T, cfg = synth.workload("sift1m", N=n, n_queries=nq)
+    X, Q, T, cfg = synth.workload(name, N=n, n_queries=nq)
     return X, Q, T, cfg
 
 
@@ -174,14 +187,15 @@ def peaks():
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave=1, growth=1, final_test=False):
+def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave=1, growth=1, final_test=False,
+                    name="sift1m", dtype="f32"):
     """The oracle (plain FP64 C loop, all host threads) on a bounded sample of
     the workload: a 100k-vector instance of the same mixture with the same
     bucket size (nlist 410, ~244 vectors per bucket), the same nprobe, K and
     Delta_d, its own PCA, k-means (2 Lloyd iterations) and fitted tables."""
     import synth
     from oracle import fit, ivf, pca, search
-    spec = synth.WORKLOADS["sift1m"]["spec"]
+    spec = synth.WORKLOADS[name]["spec"]
     N = 100_000
     nlist = max(1, round(N / (cfg_full["N"] / cfg_full["nlist"])))
     X = spec.sample(N, synth.mixtures.SEED_DATA)
@@ -191,7 +205,7 @@ def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave
     Xr = pca.rotate(X, mu, R)
     init = np.random.default_rng(1).choice(N, nlist, replace=False)
     C, a, _ = ivf.kmeans(Xr, init, 2)
-    oidx = search.OracleIndex(X, mu, R, C, a, dtype="f32")
+    oidx = search.OracleIndex(X, mu, R, C, a, dtype=dtype)
     S = search.n_steps(oidx.D, delta_d)
     prt = oidx.probe(oidx.rotate_queries(T), nprobe)
     rows = search.collect(oidx, T, prt, nprobe, K, delta_d)
@@ -210,7 +224,7 @@ def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave
                       final_rel=search.FINAL_REL if final_test else np.inf)
         times.append(time.perf_counter() - t0)
     qps = n_queries / float(np.median(times))
-    sample = (f"oracle FP64 C loop on {n_queries} queries per step against a {N}-vector SIFT-shaped instance "
+    sample = (f"oracle FP64 C loop on {n_queries} queries per step against a {N}-vector {name}-shaped instance "
               f"(nlist {nlist}, ~{N // nlist}/bucket like the full 1M/4096), nprobe {nprobe}, K {K}, "
               f"delta_d {delta_d}, first wave {first_wave}, growth 2^{growth}; probing included")
     return dict(value=qps, unit="queries/s", cores=threads, kind="oracle", sample=sample), times
@@ -260,12 +274,15 @@ def main():
     gbuild.build()
 
     t_setup = time.perf_counter()
-    X, Q, T, cfg = make_workload(args.n, args.queries)
+    wl = WORKLOAD_INFO[args.workload]
+    slabs = args.slabs or wl["slabs"]
+    X, Q, T, cfg = make_workload(args.n, args.queries, args.workload)
+    D = X.shape[1]
     K, nlist = cfg["K"], cfg["nlist"]
     if args.n is not None:
         nlist = max(16, int(round(args.n / 244)))
-    mean, R, _ = G.dade_train_rotation(X, sample_n=min(len(X), 1_000_000), seed=1)
-    idx = G.ivf_build(X, mean, R, nlist, kmeans_iters=10, seed=1, dtype="f32")
+    mean, R, _ = G.dade_train_rotation(X, sample_n=min(len(X), 1_000_000 if D <= 256 else 200_000), seed=1)
+    idx = G.ivf_build(X, mean, R, nlist, kmeans_iters=10, seed=1, dtype=slabs)
     fit_nprobe = min(64, nlist)
     fit_deltas = DELTAS if not args.profile else [int(args.profile.split(",")[1])]
     for dd in fit_deltas:
@@ -274,7 +291,7 @@ def main():
     setup_s = time.perf_counter() - t_setup
 
     from paper_2404_16322_gb300 import autotune, serving
-    maxp = min(max(NPROBES), nlist)
+    maxp = min(512 if args.workload == "gist1m" else max(NPROBES), nlist)
     run = autotune.Bench(G, idx, Q, K, maxp, DELTAS)
     if args.profile:
         vals = [int(x) for x in args.profile.split(",")]
@@ -293,7 +310,7 @@ def main():
         print(json.dumps({"profile": args.profile, "recall@10": autotune.recall_at(ids, gt, 10), "steps": args.steps,
                           "launches_per_step": 12 + 2 * n_waves(npb, fw, gw), "setup_s": time.perf_counter() - t_setup}))
         return
-    nps = [p for p in NPROBES if p <= maxp]
+    nps = [p for p in NPROBES + ([384, 512] if args.workload == "gist1m" else []) if p <= maxp]
     bd, tried_p = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, nprobes=nps, mode="prune")
     bf, tried_f = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, nprobes=nps, mode="full")
     sweep = tried_f + tried_p
@@ -339,21 +356,21 @@ def main():
     peak, peak_kind = peaks()
     achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
     khash = kernel_hash()
-    traffic = traffic_from_profiles(khash)
+    traffic = traffic_from_profiles(khash) if args.workload == "sift1m" else None
 
     # --- work accounting (bytes per query) for both modes
     run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True, first_wave=bd["first_wave"], growth=bd["growth"],
                 final_test=bd["final_test"])
     run.result()
     st = run.stats.cpu().numpy()
-    S = G.n_steps(128, bd["delta_d"])
-    pruned_dims = st[:, 3] - st[:, 2] * 128
-    dade_bytes = (pruned_dims * 4 + st[:, 2] * (2 * 128 * 4)).sum() / run.B
+    esz = {"f32": 4, "bf16": 2, "fp8": 1}[slabs]
+    pruned_dims = st[:, 3] - st[:, 2] * D
+    dade_bytes = (pruned_dims * esz + st[:, 2] * (D * esz + D * 4)).sum() / run.B
     run.run(bf["nprobe"], 0, "full", stats=True, first_wave=bf["first_wave"], growth=bf["growth"])
     run.result()
     stf = run.stats.cpu().numpy()
-    full_bytes = (stf[:, 0] * 128 * 4).sum() / run.B
-    scan_ratio = st[:, 3].sum() / (st[:, 0].sum() * 128)
+    full_bytes = (stf[:, 0] * D * 4).sum() / run.B
+    scan_ratio = st[:, 3].sum() / (st[:, 0].sum() * D)
 
     # --- end to end through the C ABI with host buffers
     q_h = torch.from_numpy(Q).pin_memory()
@@ -406,21 +423,23 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K, args.cpu_sample_queries,
+        cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K,
+                                 args.cpu_sample_queries if D <= 256 else max(20, args.cpu_sample_queries // 10),
                                  first_wave=bd["first_wave"], growth=max(1, bd["growth"]),
-                                 final_test=bd["final_test"])
+                                 final_test=bd["final_test"], name=args.workload, dtype=slabs)
 
     launches = 12 + 2 * n_waves(bd["nprobe"], bd["first_wave"], bd["growth"])
     line = {
-        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "metric": wl["metric"], "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"sift1m-shaped: N={len(X)}, D=128 integer [0,255], 256-comp mixture lambda~i^-0.8; "
-                               f"B={run.B} queries; nlist={nlist}, K={K}",
+        "config": {"workload": wl["desc"].format(N=len(X)) + f"; B={run.B} queries; nlist={nlist}, K={K}",
                    "nprobe": bd["nprobe"], "delta_d": bd["delta_d"], "first_wave": bd["first_wave"],
                    "wave_growth_log2": bd["growth"], "final_test": bd["final_test"],
-                   "slabs": "f32", "recall@10": bd["recall"],
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (index 1.0 GB > 129 MB L2)"},
+                   "slabs": slabs, "recall@10": bd["recall"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 (index {G.dade_index_info_get(idx)['device_bytes'] / 1e9:.1f} GB > "
+                         "129 MB L2)"},
         "full_scan": {"value": full_qps, "unit": "queries/s", "nprobe": bf["nprobe"], "recall@10": bf["recall"]},
         "speedup_vs_full_scan": value / world / full_qps,
         "bytes_per_query": {"prune": dade_bytes, "full_scan": full_bytes, "ratio": dade_bytes / full_bytes},
