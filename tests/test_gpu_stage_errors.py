@@ -1,0 +1,76 @@
+"""Error of each stage of the path against the FP64 oracle, on the small
+workload: the query rotation (tcgen05 split-TF32 GEMM), the probe lists
+(split-TF32 centroid distances and the top-nprobe select), the slab
+precisions' partial distances, the returned exact distances and the
+returned ids.  Each bound below is the one stated for the stage; the test
+prints the measured values (run with -s to see them)."""
+import json
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import search, storage
+
+from . import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2404_16322_gb300 import build
+    build.build()
+    import paper_2404_16322_gb300 as G
+    return G
+
+
+def test_stage_errors_against_fp64(G):
+    X, Q, T, cfg = synth.workload("tiny")
+    inp = H.oracle_inputs(X, T, cfg["nlist"], K=10, nprobe=8, delta_d=16)
+    idx = H.build_gpu(G, None, inp, cfg["nlist"])
+    oidx = inp["oidx"]
+    out = H.gpu_search(G, idx, Q, 10, 8, 16, want=("qrot", "probes"))
+    report = {}
+    # a1: rotation, max |q'_gpu - q'_fp64| / ||q'||
+    ref = oidx.rotate_queries(Q)
+    rot = np.abs(out["qrot"] - ref).max(axis=1) / np.linalg.norm(ref, axis=1)
+    report["rotation_max_rel"] = float(rot.max())
+    assert rot.max() < 4e-6
+    # a2: probe lists equal to the FP64 probes except at near ties
+    pr = oidx.probe(ref, 8)
+    same = np.all(out["probes"] == pr, axis=1)
+    report["probe_lists_identical"] = float(same.mean())
+    cd = ((ref[:, None, :] - oidx.C[None, :, :]) ** 2).sum(-1)
+    for b in np.nonzero(~same)[0]:
+        # a differing list differs only among centroids within 1e-5 of the 8th distance
+        d8 = np.sort(cd[b])[7]
+        diff = set(out["probes"][b].tolist()) ^ set(pr[b].tolist())
+        assert all(abs(cd[b, l] - d8) <= 1e-5 * d8 for l in diff)
+    # a4: partial distances at the stored precision against FP64 partial
+    # distances of the exact rotated vectors (oracle emulation of the stored
+    # values, bit-identical to the library's RNE conversions)
+    Xr = oidx.rotate_queries(X)  # same rotation as the data
+    q, x = ref[:50], Xr[:2000]
+    for dt, bound in (("f32", 1e-5), ("bf16", 2e-2), ("fp8", 2e-1)):
+        xs = storage.stored(x, dt, storage.fp8_scales(storage.to_fp32(Xr)) if dt == "fp8" else None)
+        for s, dims in ((1, 16), (4, 64), (8, 128)):
+            p_ex = ((q[:, None, :dims] - x[None, :, :dims]) ** 2).sum(-1)
+            p_st = ((q[:, None, :dims] - xs[None, :, :dims]) ** 2).sum(-1)
+            rel = np.abs(p_st - p_ex) / np.maximum(p_ex, 1e-12)
+            report[f"partial_{dt}_step{s}_p99_rel"] = float(np.percentile(rel, 99))
+            assert np.percentile(rel, 99) < bound
+    # a5: returned distances against the FP64 exact distances of their ids
+    ids, d = out["ids"], out["dists"]
+    ex = ((X[ids].astype(np.float64) - Q[:, None, :].astype(np.float64)) ** 2).sum(-1)
+    rel = np.abs(d - ex) / ex
+    report["exact_max_rel"] = float(rel.max())
+    assert rel.max() < 2e-6
+    # result: ids identical to the oracle's (device rotation)
+    oi, od, st = search.search(oidx, Q, pr, 8, 10, 16, inp["m1"].astype(np.float64),
+                               inp["beta"].astype(np.float64), amb=H.AMB["f32"])
+    report["ids_identical_queries"] = float(np.mean(np.all(ids == oi, axis=1)))
+    report["queries_with_ambiguous_test"] = float(np.mean(st[:, 4] > 0))
+    assert report["ids_identical_queries"] >= 0.9
+    print("STAGE_ERRORS " + json.dumps(report))
+    idx.close()
