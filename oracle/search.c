@@ -14,6 +14,13 @@
  *  - After each step s < S the learned test of Section V-A is applied:
  *    prune iff m1_s * dis'_s + beta_s > tau ("Incremental Correction" gives
  *    one classifier per step).  A disabled step has m1 = 0, beta = -inf.
+ *  - Or (RES) the Gaussian-bound test of Section IV-C and Algorithms 1-2:
+ *    with d = s*dd, the estimate C1 - C2 of Eq. 1 -- here dis'_s plus the
+ *    residual norms ||x_r||^2 + ||q_r||^2 over dims [d, D) -- is corrected by
+ *    m * sigma, sigma^2 = 4 sum_{i >= d} q_i^2 sigma_i^2 (Eq. 2), and the
+ *    candidate is pruned iff C1 - C2 - m sigma > tau.  sigma_i^2 is the
+ *    variance of rotated dimension i over the indexed vectors; x_r is taken
+ *    at the stored precision, like dis'_s, so the estimate is exact at d = D.
  *  - A candidate that passes every test adds the last slab, which completes
  *    the rotated distance dis'_S at the stored precision.  At d = D
  *    Algorithm 2's test has no residual term and compares the distance with
@@ -92,12 +99,27 @@ static double exact_distance(const float* x, const float* q, int D)
  * steps taken (the step at which the candidate was pruned, or S-1 when it
  * passed every test); *pruned tells which.  partials (may be NULL) receives
  * dis'_s for every step taken. */
+/* RES terms of a query: suffix sums over dims [d, D) of q_i^2 and of
+ * q_i^2 sigma_i^2 (arrays of D + 1), the multiplier m, and a candidate
+ * scratch of D + 1 doubles for its suffix sums of x_i^2. */
+typedef struct {
+    const double* rq;
+    const double* sg;
+    double m;
+    double* rx;
+} res_terms;
+
 static int estimate_and_test(const double* qr, const double* xs, int D, int dd, int S,
                              const double* m1, const double* beta, double tau, double xerr,
-                             double final_rel, int* pruned, double* partials, double amb, int64_t* n_amb)
+                             double final_rel, int* pruned, double* partials, double amb, int64_t* n_amb,
+                             const res_terms* res)
 {
     double p = 0.0;
     *pruned = 0;
+    if (res) {
+        res->rx[D] = 0.0;
+        for (int j = D - 1; j >= 0; j--) res->rx[j] = res->rx[j + 1] + xs[j] * xs[j];
+    }
     for (int s = 1; s < S; s++) {
         int j1 = s * dd < D ? s * dd : D;
         for (int j = (s - 1) * dd; j < j1; j++) {
@@ -105,10 +127,16 @@ static int estimate_and_test(const double* qr, const double* xs, int D, int dd, 
             p += t * t;
         }
         if (partials) partials[s - 1] = p;
+        double lhs;
+        if (res) {
+            lhs = p + res->rx[j1] + res->rq[j1] - res->m * 2.0 * sqrt(res->sg[j1]);
+        } else {
+            lhs = m1[s - 1] * p + beta[s - 1];
+        }
         /* a decision within amb * tau of the threshold may flip under another
          * rounding of the same arithmetic: count it */
-        if (n_amb && isfinite(tau) && fabs(m1[s - 1] * p + beta[s - 1] - tau) <= amb * tau) (*n_amb)++;
-        if (m1[s - 1] * p + beta[s - 1] > tau) {
+        if (n_amb && isfinite(tau) && fabs(lhs - tau) <= amb * tau) (*n_amb)++;
+        if (lhs > tau) {
             *pruned = 1;
             return s;
         }
@@ -140,6 +168,9 @@ typedef struct {
     int32_t D, dd, S, P, Kmax, mode, first_wave, growth;
     double amb, final_rel;
     const double* xerr;
+    int32_t est;            /* 0: learned tables, 1: RES */
+    double res_m;
+    const double* var;      /* D: sigma_i^2 (RES) */
     const double* Qr;
     const float* Q;
     const double* Xs;
@@ -159,12 +190,13 @@ typedef struct {
 } oracle_args;
 
 /* One candidate: estimate, test, and if it survives, its exact distance. */
-static int visit(const oracle_args* a, int64_t b, int64_t pos, double tau, entry* out, int64_t* st)
+static int visit(const oracle_args* a, int64_t b, int64_t pos, double tau, entry* out, int64_t* st,
+                 const res_terms* res)
 {
     const double* qr = a->Qr + b * a->D;
     int pruned;
     int steps = estimate_and_test(qr, a->Xs + pos * a->D, a->D, a->dd, a->S, a->m1, a->beta, tau,
-                                  a->xerr ? a->xerr[pos] : 0.0, a->final_rel, &pruned, NULL, a->amb, &st[4]);
+                                  a->xerr ? a->xerr[pos] : 0.0, a->final_rel, &pruned, NULL, a->amb, &st[4], res);
     st[0] += 1;
     if (pruned) {
         int64_t dims = (int64_t)steps * a->dd;
@@ -190,13 +222,33 @@ static void search_one(const oracle_args* a, int64_t b)
     q.K = K;
     q.n = 0;
     q.e = (entry*)malloc(sizeof(entry) * (size_t)(K > 0 ? K : 1));
+    res_terms rt, *res = NULL;
+    double* rbuf = NULL;
+    if (a->est == 1) {
+        const int D = a->D;
+        const double* qr = a->Qr + b * D;
+        rbuf = (double*)malloc(sizeof(double) * 3 * (size_t)(D + 1));
+        double* rq = rbuf;
+        double* sg = rbuf + (D + 1);
+        rq[D] = 0.0;
+        sg[D] = 0.0;
+        for (int j = D - 1; j >= 0; j--) {
+            rq[j] = rq[j + 1] + qr[j] * qr[j];
+            sg[j] = sg[j + 1] + qr[j] * qr[j] * a->var[j];
+        }
+        rt.rq = rq;
+        rt.sg = sg;
+        rt.m = a->res_m;
+        rt.rx = rbuf + 2 * (D + 1);
+        res = &rt;
+    }
 
     if (a->mode == MODE_SEQUENTIAL) {
         for (int r = 0; r < np; r++) {
             int l = pr[r];
             for (int64_t m = a->list_off[l]; m < a->list_off[l + 1]; m++) {
                 entry e;
-                if (visit(a, b, a->members[m], queue_tau(&q), &e, st)) queue_offer(&q, e);
+                if (visit(a, b, a->members[m], queue_tau(&q), &e, st, res)) queue_offer(&q, e);
             }
         }
     } else {
@@ -212,7 +264,7 @@ static void search_one(const oracle_args* a, int64_t b)
             for (int64_t r = b0; r < b1; r++) {
                 int l = pr[r];
                 for (int64_t m = a->list_off[l]; m < a->list_off[l + 1]; m++)
-                    if (visit(a, b, a->members[m], tau, &surv[ns], st)) ns++;
+                    if (visit(a, b, a->members[m], tau, &surv[ns], st, res)) ns++;
             }
             for (int64_t i = 0; i < ns; i++)
                 if (a->mode != MODE_FROZEN || surv[i].d <= tau) queue_offer(&q, surv[i]);
@@ -225,20 +277,23 @@ static void search_one(const oracle_args* a, int64_t b)
         a->out_d[b * a->Kmax + k] = k < q.n ? q.e[k].d : INFINITY;
     }
     free(q.e);
+    free(rbuf);
 }
 
 int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t Kmax,
                   int32_t mode, int32_t first_wave, int32_t growth, double amb, double final_rel,
+                  int32_t est, double res_m, const double* var,
                   const double* Qr, const float* Q, const double* Xs, const double* xerr, const float* X,
                   const int64_t* ids, const int64_t* list_off,
                   const int64_t* members, const int32_t* probes, const int32_t* nprobe,
                   const int32_t* K, const double* m1, const double* beta, const double* tau_in,
                   int64_t* out_ids, double* out_d, int64_t* stats)
 {
-    if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1 || mode < 0 || mode > 2 || !(final_rel >= 0.0))
+    if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1 || mode < 0 || mode > 2 || !(final_rel >= 0.0) ||
+        est < 0 || est > 1 || (est == 1 && (!var || !(res_m >= 0.0))))
         return 1;
-    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, final_rel, xerr, Qr, Q, Xs, X, ids,
-                     list_off, members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
+    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, final_rel, xerr, est, res_m, var, Qr, Q,
+                     Xs, X, ids, list_off, members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < B; b++) search_one(&a, b);
     return 0;
@@ -281,7 +336,7 @@ int oracle_collect(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, 
                     int64_t pos = members[m];
                     int pruned;
                     estimate_and_test(Qr + b * D, Xs + pos * D, D, delta_d, S, never, neg_inf, tau, 0.0,
-                                      INFINITY, &pruned, partials + row * (S > 1 ? S - 1 : 0), 0.0, NULL);
+                                      INFINITY, &pruned, partials + row * (S > 1 ? S - 1 : 0), 0.0, NULL, NULL);
                     tau_out[row] = tau;
                     dis_out[row] = exact_distance(X + pos * D, Q + b * D, D);
                     id_out[row] = ids[pos];

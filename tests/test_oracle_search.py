@@ -267,3 +267,71 @@ def test_final_test_never_changes_the_result(rotated, dtype):
             assert b[2][:, 2].sum() <= a[2][:, 2].sum()
             if not np.any(m1):  # learned tests off: the final test is the only one
                 assert b[2][:, 2].sum() < a[2][:, 2].sum()
+
+
+def test_res_worked_example_by_hand():
+    """RES (Section IV-C, Algorithm 2) on two vectors, D = 4, Delta_d = 2,
+    identity rotation, frozen tau = 2, query q = (1, 0, 1, 0).
+    sigma_i^2 over the two vectors (1/N): dims 0 and 2 have values {1, 3}
+    and {2, 0}: variance 1; dims 1 and 3: 0.
+    After dims [0, 2): sigma = 2 sqrt(q_2^2 * 1) = 2.
+      x0 = (1, 0, 2, 0): dis'_1 = 0, ||x_r||^2 = 4, ||q_r||^2 = 1 -> C1 - C2 = 5; dis = 1.
+      x1 = (3, 0, 0, 0): dis'_1 = 4, ||x_r||^2 = 0, ||q_r||^2 = 1 -> C1 - C2 = 5; dis = 5.
+    m = 1: 5 - 2 = 3 > 2: both pruned (x0 is lost: the bound fails at m = 1).
+    m = 2: 5 - 4 = 1 <= 2: both get exact distances; x0 (1) is kept, x1 (5) is not.
+    m = 1.4: 2.2 > 2: both pruned."""
+    X = np.array([[1, 0, 2, 0], [3, 0, 0, 0]], dtype=np.float32)
+    idx = search.OracleIndex(X, np.zeros(4), np.eye(4), np.zeros((1, 4)), np.zeros(2, np.int32), dtype="f64")
+    assert np.array_equal(idx.var, [1.0, 0.0, 1.0, 0.0])
+    Q = np.array([[1, 0, 1, 0]], dtype=np.float32)
+    pr = np.zeros((1, 1), np.int32)
+    for m, ids_exp, st_exp in [(1.0, [-1, -1], [2, 2, 0, 4]), (2.0, [0, -1], [2, 0, 2, 8]),
+                               (1.4, [-1, -1], [2, 2, 0, 4])]:
+        ids, d, st = search.search(idx, Q, pr, 1, 2, 2, None, None, mode="frozen", tau=np.array([2.0]),
+                                   estimator="res", res_m=m)
+        assert list(ids[0]) == ids_exp, m
+        assert list(st[0][:4]) == st_exp, m
+
+
+def test_res_estimate_is_exact_for_a_query_at_the_origin(small):
+    # q = 0: ||q_r||^2 = 0 and sigma = 0, so C1 - C2 = ||x||^2 = dis at every
+    # step and RES prunes exactly the candidates with dis > tau: the results
+    # equal the pruning-off results, and every exact distance taken is <= tau
+    idx = small["idx"]
+    Q = np.zeros((1, small["D"]), np.float32)
+    probes = idx.probe(idx.rotate_queries(Q), small["nlist"])
+    S = search.n_steps(small["D"], 8)
+    off = search.search(idx, Q, probes, small["nlist"], 10, 8, *search.disabled_tables(S))
+    res = search.search(idx, Q, probes, small["nlist"], 10, 8, None, None, estimator="res", res_m=8.0,
+                        mode="sequential")
+    assert np.array_equal(res[0], off[0]) and np.allclose(res[1], off[1], rtol=1e-13)
+    assert res[2][0, 1] > 0 and res[2][0, 1] + res[2][0, 2] == res[2][0, 0]
+
+
+@pytest.mark.parametrize("m", [0.5, 1.0, 2.0])
+def test_res_loss_rate_follows_the_gaussian_error_model(m):
+    # x ~ N(0, diag(lam)) (already rotated), so for a query q the error
+    # C1 - C2 - dis = 2 <q_r, x_r> ~ N(0, sigma^2) exactly (Eq. 2).  With a
+    # frozen tau just above a candidate's distance, the candidate is lost iff
+    # that error exceeds m sigma: probability 1 - Phi(m).
+    from math import erf, sqrt
+    rng = np.random.default_rng(5)
+    D, N = 32, 20000
+    lam = np.linspace(4.0, 0.2, D)
+    X = (rng.standard_normal((N, D)) * np.sqrt(lam)).astype(np.float32)
+    Q = (rng.standard_normal((400, D)) * np.sqrt(lam)).astype(np.float32)
+    idx = search.OracleIndex(X, np.zeros(D), np.eye(D), np.zeros((1, D)), np.zeros(N, np.int32), dtype="f64")
+    # one query per candidate: tau = that candidate's distance (+ a hair)
+    cand = rng.choice(N, len(Q), replace=False)
+    dis = ((X[cand].astype(np.float64) - Q.astype(np.float64)) ** 2).sum(1)
+    lost = 0
+    for b in range(len(Q)):
+        one = search.OracleIndex(X[cand[b:b + 1]], np.zeros(D), np.eye(D), np.zeros((1, D)), np.zeros(1, np.int32),
+                                 dtype="f64", ids=cand[b:b + 1])
+        one.var = idx.var  # sigma_i^2 of the whole population
+        ids, _, _ = search.search(one, Q[b:b + 1], np.zeros((1, 1), np.int32), 1, 1, 16, None, None,
+                                  mode="frozen", tau=np.array([dis[b] * (1 + 1e-12)]), estimator="res", res_m=m)
+        lost += ids[0, 0] < 0
+    want = 1 - 0.5 * (1 + erf(m / sqrt(2)))
+    got = lost / len(Q)
+    assert abs(got - want) < 4 * sqrt(want * (1 - want) / len(Q)) + 0.01, (got, want)
