@@ -171,13 +171,21 @@ dade_status dade_get_correction(const dade_index* idx, int32_t delta_d, float* m
  *     queue holds K entries), in parallel over (bucket, query) work units.
  *  4. mode DADE_SCAN_PRUNE: the candidate's partial distance over the rotated
  *     slabs grows delta_d dims per step and the installed table for delta_d
- *     decides pruning after each of the first S - 1 steps; with
+ *     decides pruning after each of the first S - 1 steps (or, with
+ *     opts->estimator = DADE_EST_RES, the Gaussian-bound test below); with
  *     opts->final_test a survivor adds the last slab and is pruned iff
  *     dis'_S > (sqrt(tau) + e_x)^2 (1 + 1e-3) (a rotated distance <= tau
  *     implies dis'_S <= (sqrt(tau) + e_x)^2; the 1e-3 covers FP32 rounding);
  *     the rest get the exact FP32 distance from the original vectors.
  *     mode DADE_SCAN_FULL:
  *     every candidate gets the exact FP32 distance (no estimate, no table).
+ *     DADE_EST_RES (Section IV-C, Algorithms 1-2, Eq. 1-2): after the step
+ *     that completes dims [0, d) the candidate is pruned iff
+ *       dis'_d + ||x~_r||^2 + ||q'_r||^2 - m * 2 sqrt(sum_{i>=d} q'_i^2 s_i^2) > tau
+ *     where x~_r, q'_r are the stored vector and the rotated query over
+ *     dims [d, D), s_i^2 is the variance of rotated dim i over the indexed
+ *     vectors (computed at build) and m = opts->res_m.  It needs no
+ *     correction table.
  *  5. candidates with exact distance <= tau join the query's top-K, ordered
  *     by (distance, id); tau becomes its K-th distance.
  * Outputs: for query b, ids_dev / dists_dev at [off_b, off_b + K_b) with
@@ -192,6 +200,7 @@ dade_status dade_get_correction(const dade_index* idx, int32_t delta_d, float* m
  * it is never cleared by the library.
  * ---------------------------------------------------------------------- */
 typedef enum { DADE_SCAN_PRUNE = 0, DADE_SCAN_FULL = 1 } dade_scan_mode;
+typedef enum { DADE_EST_LEARNED = 0, DADE_EST_RES = 1 } dade_estimator;
 
 typedef struct {
     int32_t mode;            /* dade_scan_mode                                    */
@@ -219,6 +228,9 @@ typedef struct {
                              /* trades a last slab step for fewer exact          */
                              /* distances.  0: survivors of step S - 1 go        */
                              /* straight to the exact distance.                  */
+    int32_t estimator;       /* PRUNE mode: dade_estimator (0: learned tables)  */
+    float res_m;             /* DADE_EST_RES: the multiplier m of sigma, >= 0   */
+                             /* (larger m prunes less; the paper's default 8)  */
 } dade_search_opts;
 
 dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,

@@ -19,6 +19,7 @@ STATUS = {0: "DADE_OK", 1: "DADE_EINVAL", 2: "DADE_ENOMEM", 3: "DADE_ECUDA", 4: 
           5: "DADE_ESTATE", 6: "DADE_ENOTIMPL", 7: "DADE_EIO"}
 SLAB = {"f32": 0, "bf16": 1, "fp8": 2}
 MODE = {"prune": 0, "full": 1}
+ESTIMATOR = {"learned": 0, "res": 1}
 
 
 class BuildParams(ctypes.Structure):
@@ -31,7 +32,7 @@ class SearchOpts(ctypes.Structure):
                 ("tau_dev", c_vp), ("probe_in_dev", c_vp), ("probe_out_dev", c_vp),
                 ("qrot_out_dev", c_vp), ("stats_dev", c_vp), ("status_dev", c_vp),
                 ("workspace", c_vp), ("workspace_bytes", c_sz), ("wave_growth_log2", c_i32),
-                ("final_test", c_i32)]
+                ("final_test", c_i32), ("estimator", c_i32), ("res_m", ctypes.c_float)]
 
 
 class IndexInfo(ctypes.Structure):

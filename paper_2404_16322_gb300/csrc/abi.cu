@@ -95,6 +95,16 @@ static dade_status install_table(dade_index* idx, int delta_d, int S, const floa
     return DADE_OK;
 }
 
+dade_status build_residual_norms(dade_index* idx) {
+    const int64_t n = (int64_t)(idx->nb + 1) * std::max<int64_t>(1, idx->total_slots);
+    DADE_TRY(idx->sfx_dev.alloc(sizeof(float) * n));
+    DADE_CUDA_TRY(launch_residual_norms(idx->slab_dev.p, idx->dtype, idx->scale_dev.as<float>(),
+                                        idx->list_slot_dev.as<int64_t>(), idx->nlist, idx->total_slots, idx->Dpad,
+                                        idx->sfx_dev.as<float>(), 0));
+    DADE_CUDA_TRY(cudaDeviceSynchronize());
+    return DADE_OK;
+}
+
 dade_status install_table_public(dade_index* idx, int delta_d, int S, const float* m1, const float* beta) {
     return install_table(idx, delta_d, S, m1, beta);
 }
@@ -138,7 +148,7 @@ struct Reader {
 };
 
 const char kMagic[8] = {'D', 'A', 'D', 'E', 'I', 'D', 'X', '1'};
-const uint32_t kVersion = 2;
+const uint32_t kVersion = 3;
 
 }  // namespace
 
@@ -171,7 +181,8 @@ extern "C" dade_status dade_index_info_get(const dade_index* idx, dade_index_inf
     out->dtype = idx->dtype;
     out->max_list = idx->max_list;
     out->device_bytes = (int64_t)(idx->slab_dev.bytes + idx->orig_dev.bytes + idx->ids_dev.bytes +
-                                  idx->cent_dev.bytes + idx->R_dev.bytes + idx->eps_dev.bytes);
+                                  idx->cent_dev.bytes + idx->R_dev.bytes + idx->eps_dev.bytes + idx->var_dev.bytes +
+                                  idx->sfx_dev.bytes);
     return DADE_OK;
 }
 
@@ -242,6 +253,7 @@ extern "C" dade_status dade_index_save(const dade_index* idx, const char* path) 
     w.put(idx->assign.data(), sizeof(int32_t) * idx->assign.size());
     w.put(idx->ids.data(), sizeof(int64_t) * idx->ids.size());
     if (idx->dtype == DADE_SLAB_FP8E4M3) w.put(idx->fp8_scale.data(), sizeof(float) * idx->fp8_scale.size());
+    w.put(idx->var.data(), sizeof(float) * idx->var.size());
     // device contents
     std::vector<char> host;
     auto dump = [&](const DevBuf& b, size_t n) {
@@ -314,6 +326,8 @@ extern "C" dade_status dade_index_load(const char* path, dade_index** out) {
         idx->fp8_scale.resize((size_t)Dp);
         r.get(idx->fp8_scale.data(), sizeof(float) * Dp);
     }
+    idx->var.resize((size_t)Dp);
+    r.get(idx->var.data(), sizeof(float) * Dp);
     DADE_TRY(upload_index_arrays(idx.get()));
     std::vector<char> host;
     auto fill = [&](DevBuf& b, size_t n) -> dade_status {
@@ -364,6 +378,9 @@ extern "C" dade_status dade_index_load(const char* path, dade_index** out) {
         DADE_TRY(idx->scale_dev.alloc(sizeof(float) * Dp));
         DADE_CUDA_TRY(cudaMemcpy(idx->scale_dev.p, idx->fp8_scale.data(), sizeof(float) * Dp, cudaMemcpyHostToDevice));
     }
+    DADE_TRY(idx->var_dev.alloc(sizeof(float) * Dp));
+    DADE_CUDA_TRY(cudaMemcpy(idx->var_dev.p, idx->var.data(), sizeof(float) * Dp, cudaMemcpyHostToDevice));
+    DADE_TRY(build_residual_norms(idx.get()));
     *out = idx.release();
     return DADE_OK;
 }

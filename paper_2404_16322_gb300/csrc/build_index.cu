@@ -216,6 +216,10 @@ extern "C" dade_status ivf_build(const float* X, int64_t N, int32_t D, const dou
         la.eps = idx->dtype == DADE_SLAB_F32 ? nullptr : idx->eps_dev.as<float>();
         DADE_CUDA_TRY(launch_layout(la, st));
         DADE_CUDA_TRY(launch_quant_error(la, st));
+        DADE_TRY(idx->var_dev.alloc(sizeof(float) * Dp));
+        DADE_CUDA_TRY(launch_dim_var(xr_dev.as<float>(), N, Dp, idx->var_dev.as<float>(), st));
+        idx->var.resize((size_t)Dp);
+        DADE_CUDA_TRY(cudaMemcpyAsync(idx->var.data(), idx->var_dev.p, sizeof(float) * Dp, cudaMemcpyDeviceToHost, st));
         std::vector<int64_t> slot_ids((size_t)idx->total_slots, -1);
         for (int64_t s = 0; s < idx->total_slots; ++s)
             if (slot_row[(size_t)s] >= 0) slot_ids[(size_t)s] = idx->ids[(size_t)slot_row[(size_t)s]];
@@ -223,6 +227,7 @@ extern "C" dade_status ivf_build(const float* X, int64_t N, int32_t D, const dou
                                       cudaMemcpyHostToDevice, st));
         DADE_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    DADE_TRY(build_residual_norms(idx.get()));
     *out = idx.release();
     return DADE_OK;
 }

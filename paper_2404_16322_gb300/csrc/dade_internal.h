@@ -106,6 +106,9 @@ struct dade_index {
     dade::DevBuf ids_dev;      // total_slots int64 (-1 on padding)
     dade::DevBuf scale_dev;    // Dpad FP32 (FP8 only)
     dade::DevBuf eps_dev;      // total_slots FP32: quantisation error norm (BF16/FP8 only)
+    dade::DevBuf var_dev;      // Dpad FP32: variance of each rotated dimension (RES)
+    dade::DevBuf sfx_dev;      // (nb + 1) x total_slots FP32: residual norms from block b on (RES)
+    std::vector<float> var;    // host copy of var_dev
     std::map<int, dade::CorrectionTable> tables;  // by delta_d
     // internal scratch used when the caller gives no workspace
     mutable dade::DevBuf ws;
@@ -163,6 +166,11 @@ struct LayoutArgs {
 };
 cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st);
 cudaError_t launch_quant_error(const LayoutArgs& a, cudaStream_t st);
+cudaError_t launch_dim_var(const float* xrot, int64_t N, int32_t Dpad, float* var, cudaStream_t st);
+cudaError_t launch_residual_norms(const void* slab, int dtype, const float* scale, const int64_t* list_slot,
+                                  int nlist, int64_t total_slots, int32_t Dpad, float* sfx, cudaStream_t st);
+// The per-slot residual norms of idx's slabs (RES), computed on the device.
+dade_status build_residual_norms(dade_index* idx);
 cudaError_t launch_amax(const float* xrot, int64_t N, int32_t Dpad, float* amax_bits_as_float,
                         cudaStream_t st);
 cudaError_t launch_fp8_scale(float* amax_to_scale, int32_t Dpad, cudaStream_t st);

@@ -67,6 +67,73 @@ __global__ void quant_error_kernel(LayoutArgs a) {
     if (lane == 0) a.eps[slot] = sqrtf(s);
 }
 
+// Variance of each rotated dimension over the N rows (1/N; two passes in
+// FP64, one block per dimension, fixed reduction order).
+__global__ void dim_var_kernel(const float* __restrict__ xrot, int64_t N, int32_t Dpad, float* __restrict__ var) {
+    __shared__ double red[256];
+    const int d = blockIdx.x, tid = threadIdx.x;
+    double s = 0.0;
+    for (int64_t r = tid; r < N; r += 256) s += xrot[r * Dpad + d];
+    red[tid] = s;
+    __syncthreads();
+    for (int h = 128; h; h >>= 1) {
+        if (tid < h) red[tid] += red[tid + h];
+        __syncthreads();
+    }
+    const double mean = red[0] / (double)(N > 0 ? N : 1);
+    __syncthreads();
+    s = 0.0;
+    for (int64_t r = tid; r < N; r += 256) {
+        const double t = xrot[r * Dpad + d] - mean;
+        s += t * t;
+    }
+    red[tid] = s;
+    __syncthreads();
+    for (int h = 128; h; h >>= 1) {
+        if (tid < h) red[tid] += red[tid + h];
+        __syncthreads();
+    }
+    if (tid == 0) var[d] = (float)(red[0] / (double)(N > 0 ? N : 1));
+}
+
+// Residual norms of every slot's stored vector: sfx[b][slot] = sum over
+// blocks b' >= b of ||x~_b'||^2 (dequantised, FP32, from the last block
+// back), b = 0 .. nb; padding slots get 0.  The slot's bucket comes from a
+// binary search of list_slot.
+__global__ void residual_norms_kernel(const void* __restrict__ slab, int dtype, const float* __restrict__ scale,
+                                      const int64_t* __restrict__ list_slot, int nlist, int64_t total_slots,
+                                      int32_t Dpad, float* __restrict__ sfx) {
+    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= total_slots) return;
+    int lo = 0, hi = nlist - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (list_slot[mid] <= slot) lo = mid; else hi = mid - 1;
+    }
+    const int64_t s0 = list_slot[lo], npad = list_slot[lo + 1] - s0, i = slot - s0;
+    const int nb = Dpad / kBlock;
+    float acc = 0.f;
+    sfx[(int64_t)nb * total_slots + slot] = 0.f;
+    for (int b = nb - 1; b >= 0; --b) {
+        const int64_t e = s0 * Dpad + ((int64_t)b * npad + i) * kBlock;
+        float s = 0.f;
+        for (int j = 0; j < kBlock; ++j) {
+            float v;
+            if (dtype == DADE_SLAB_F32) {
+                v = static_cast<const float*>(slab)[e + j];
+            } else if (dtype == DADE_SLAB_BF16) {
+                v = __bfloat162float(static_cast<const __nv_bfloat16*>(slab)[e + j]);
+            } else {
+                const __nv_fp8_storage_t u = static_cast<const __nv_fp8_storage_t*>(slab)[e + j];
+                v = __half2float(__half(__nv_cvt_fp8_to_halfraw(u, __NV_E4M3))) * scale[b * kBlock + j];
+            }
+            s = fmaf(v, v, s);
+        }
+        acc += s;
+        sfx[(int64_t)b * total_slots + slot] = acc;
+    }
+}
+
 __global__ void amax_kernel(const float* __restrict__ xrot, int64_t N, int32_t Dpad,
                             unsigned int* __restrict__ amax) {
     int d = blockIdx.y;
@@ -98,6 +165,19 @@ cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st) {
 cudaError_t launch_quant_error(const LayoutArgs& a, cudaStream_t st) {
     if (a.total_slots == 0 || a.dtype == DADE_SLAB_F32 || !a.eps) return cudaSuccess;
     quant_error_kernel<<<(unsigned)ceil_div(a.total_slots * 32, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dim_var(const float* xrot, int64_t N, int32_t Dpad, float* var, cudaStream_t st) {
+    dim_var_kernel<<<(unsigned)Dpad, 256, 0, st>>>(xrot, N, Dpad, var);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_norms(const void* slab, int dtype, const float* scale, const int64_t* list_slot,
+                                  int nlist, int64_t total_slots, int32_t Dpad, float* sfx, cudaStream_t st) {
+    if (total_slots == 0) return cudaSuccess;
+    residual_norms_kernel<<<(unsigned)ceil_div(total_slots, 128), 128, 0, st>>>(slab, dtype, scale, list_slot, nlist,
+                                                                               total_slots, Dpad, sfx);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@ struct IndexView {
     const int32_t* list_size;  // nlist
     const float* scale;        // FP8 per-dimension scale (Dpad)
     const float* eps;          // per slot: quantisation error norm (null for FP32 slabs)
+    const float* sfx;          // (nb + 1) x total_slots: sum of the stored x_i^2 over blocks >= b
+    int64_t total_slots;
     int32_t D, Dpad, nb, nlist, dtype;
 };
 
@@ -25,6 +27,9 @@ struct WaveView {
     int64_t B;
     int32_t P, Kmax, first_wave, n_waves, wave_shift;
     int32_t final_test;       // PRUNE: test the completed rotated distance before the exact one
+    int32_t est;              // PRUNE: 0 learned tables, 1 the Gaussian-bound (RES) test
+    int32_t res_stride;       // S - 1: entries of res_q per query
+    const float* res_q;       // B x (S - 1): ||q'_r||^2 - m sigma after each step (RES)
     const float* qrot;        // B x Dpad rotated queries
     const float* qpad;        // B x Dpad original queries, zero padded
     const int32_t* probes;    // B x P
@@ -58,6 +63,13 @@ cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStre
 cudaError_t launch_wave_scan(const IndexView& ix, const WaveView& wv, int w, bool full,
                              int delta_d, const float* m1, const float* beta, int S,
                              cudaStream_t st);
+// The RES variants of launch_wave_scan (scan_res.cu), and the per-query RES
+// terms res_q[b][s] = sum_{i >= d_s} q'_i^2 - m 2 sqrt(sum_{i >= d_s} q'_i^2 var_i),
+// d_s = min((s + 1) delta_d, D), for s < S - 1.
+cudaError_t launch_wave_scan_res(const IndexView& ix, const WaveView& wv, int w, int delta_d, int S,
+                                 cudaStream_t st);
+cudaError_t launch_res_terms(const float* qrot, int64_t B, int32_t D, int32_t Dpad, const float* var,
+                             int delta_d, int S, float m, float* res_q, cudaStream_t st);
 cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStream_t st);
 cudaError_t launch_output(const WaveView& wv, int64_t* ids, float* dists,
                           const int64_t* offsets, cudaStream_t st);

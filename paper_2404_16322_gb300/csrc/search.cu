@@ -57,7 +57,10 @@ int64_t wave_bound(const dade_index* idx, int P, int f, int g, int w) {
     return idx->sizes_desc_prefix[n];
 }
 
-size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* base, Plan* pl) {
+// The RES test is in use (PRUNE mode with estimator RES).
+bool uses_res(const dade_search_opts& o) { return o.mode == DADE_SCAN_PRUNE && o.estimator == DADE_EST_RES; }
+
+size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o, char* base, Plan* pl) {
     const int P = o.max_nprobe, Kmax = o.max_K;
     const bool frozen = o.tau_dev != nullptr;
     const int f = frozen ? P : std::max(1, o.first_wave);
@@ -74,6 +77,8 @@ size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* 
     v.first_wave = f;
     v.wave_shift = g;
     v.final_test = o.final_test != 0;
+    v.est = uses_res(o) ? 1 : 0;
+    v.res_stride = v.est ? (int)ceil_div(idx->Dpad, delta_d) - 1 : 0;
     v.n_waves = nw;
     v.qrot = c.take<float>((size_t)B * idx->Dpad);
     v.qpad = c.take<float>((size_t)B * idx->Dpad);
@@ -99,6 +104,7 @@ size_t carve(const dade_index* idx, int64_t B, const dade_search_opts& o, char* 
     v.top_d = c.take<float>((size_t)B * Kmax);
     v.top_id = c.take<int64_t>((size_t)B * Kmax);
     v.tau = c.take<float>((size_t)B);
+    v.res_q = v.res_stride > 0 ? c.take<float>((size_t)B * v.res_stride) : nullptr;
     // zero-initialised block
     c.off = (size_t)round_up((int64_t)c.off, 256);
     size_t z0 = c.off;
@@ -123,11 +129,14 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
     if (o.mode != DADE_SCAN_PRUNE && o.mode != DADE_SCAN_FULL) return fail(DADE_EINVAL, "bad mode");
     if (o.first_wave < 0) return fail(DADE_EINVAL, "first_wave < 0");
     if (o.wave_growth_log2 < 0 || o.wave_growth_log2 > 30) return fail(DADE_EINVAL, "wave_growth_log2 must be in [0, 30]");
+    if (o.estimator != DADE_EST_LEARNED && o.estimator != DADE_EST_RES) return fail(DADE_EINVAL, "bad estimator");
+    if (o.estimator == DADE_EST_RES && !(o.res_m >= 0.f && o.res_m < INFINITY))
+        return fail(DADE_EINVAL, "res_m must be finite and >= 0");
     if (o.mode == DADE_SCAN_PRUNE) {
         if (delta_d != 8 && delta_d != 16 && delta_d != 32)
             return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32 (got %d)", delta_d);
         int S = (int)ceil_div(idx->Dpad, delta_d);
-        if (S > 1 && !idx->tables.count(delta_d))
+        if (S > 1 && o.estimator == DADE_EST_LEARNED && !idx->tables.count(delta_d))
             return fail(DADE_ESTATE, "no correction table for delta_d = %d", delta_d);
     }
     return DADE_OK;
@@ -137,9 +146,8 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
 
 size_t workspace_bytes(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o,
                        const CollectArgs*) {
-    (void)delta_d;
     Plan pl;
-    return carve(idx, B, o, nullptr, &pl);
+    return carve(idx, B, delta_d, o, nullptr, &pl);
 }
 
 dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const int32_t* K_dev,
@@ -150,7 +158,7 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     if (B == 0) return DADE_OK;
     if (!Q || !K_dev || !nprobe_dev || !ids_dev || !dists_dev) return fail(DADE_EINVAL, "null buffer");
     Plan pl;
-    size_t need = carve(idx, B, o, nullptr, &pl);
+    size_t need = carve(idx, B, delta_d, o, nullptr, &pl);
     char* base;
     if (o.workspace) {
         if (o.workspace_bytes < need)
@@ -164,7 +172,7 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
         base = idx->ws.as<char>();
     }
     base = reinterpret_cast<char*>(round_up(reinterpret_cast<int64_t>(base), 256));
-    carve(idx, B, o, base, &pl);
+    carve(idx, B, delta_d, o, base, &pl);
     WaveView& v = pl.wv;
     v.nprobe = nprobe_dev;
     v.K = K_dev;
@@ -182,6 +190,8 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     ix.list_size = idx->list_size_dev.as<int32_t>();
     ix.scale = idx->scale_dev.as<float>();
     ix.eps = idx->dtype == DADE_SLAB_F32 ? nullptr : idx->eps_dev.as<float>();
+    ix.sfx = idx->sfx_dev.as<float>();
+    ix.total_slots = idx->total_slots;
     ix.D = idx->D;
     ix.Dpad = idx->Dpad;
     ix.nb = idx->nb;
@@ -191,7 +201,7 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     const bool full = o.mode == DADE_SCAN_FULL;
     const int S = (int)ceil_div(idx->Dpad, delta_d > 0 ? delta_d : idx->Dpad);
     const float *m1 = nullptr, *beta = nullptr;
-    if (!full && S > 1) {
+    if (!full && S > 1 && !v.est) {
         const CorrectionTable& tb = idx->tables.at(delta_d);
         m1 = tb.m1_dev;
         beta = tb.beta_dev;
@@ -207,6 +217,9 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     DADE_CUDA_TRY(launch_tc_dot(Q, idx->D, idx->mean_dev.as<float>(), idx->R_dev.as<float>(), idx->Dpad,
                                 const_cast<float*>(v.qrot), idx->Dpad, B, idx->Dpad, idx->D, v.status, st));
     DADE_CUDA_TRY(launch_prepare_queries(Q, B, idx->D, idx->Dpad, const_cast<float*>(v.qpad), st));
+    if (v.est)
+        DADE_CUDA_TRY(launch_res_terms(v.qrot, B, idx->D, idx->Dpad, idx->var_dev.as<float>(), delta_d, S, o.res_m,
+                                       const_cast<float*>(v.res_q), st));
     if (o.qrot_out_dev) {
         DADE_CUDA_TRY(cudaMemcpy2DAsync(o.qrot_out_dev, sizeof(float) * idx->D, v.qrot,
                                         sizeof(float) * idx->Dpad, sizeof(float) * idx->D, B,

@@ -126,6 +126,7 @@ extern "C" dade_status dade_index_shard(const dade_index* idx, int32_t n_shards,
     sh->R = idx->R;
     sh->centroids = idx->centroids;
     sh->fp8_scale = idx->fp8_scale;
+    sh->var = idx->var;
     for (int64_t i = 0; i < idx->N; ++i) {
         const int32_t l = idx->assign[(size_t)i];
         if (owner[(size_t)l] != shard) continue;
@@ -165,6 +166,8 @@ extern "C" dade_status dade_index_shard(const dade_index* idx, int32_t n_shards,
     DADE_TRY(dup(sh->cent_dev, idx->cent_dev));
     DADE_TRY(dup(sh->cnorm_dev, idx->cnorm_dev));
     DADE_TRY(dup(sh->scale_dev, idx->scale_dev));
+    DADE_TRY(dup(sh->var_dev, idx->var_dev));
+    DADE_TRY(build_residual_norms(sh.get()));
     for (const auto& kv : idx->tables)
         DADE_TRY(install_table_public(sh.get(), kv.first, kv.second.S, kv.second.m1.data(), kv.second.beta.data()));
     *out = sh.release();

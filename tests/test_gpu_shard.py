@@ -103,3 +103,24 @@ def test_merge_uneven_K_and_padding(G):
         want_i[:len(o)] = i[ok][o]
         want_d[:len(o)] = d[ok][o]
         assert np.array_equal(mi[b], want_i) and np.array_equal(md[b], want_d), b
+
+
+def test_res_on_shards_with_a_frozen_tau_matches_unsharded(G, built):
+    # the RES test of a (query, candidate) pair depends only on the pair,
+    # the index-wide variances (shards keep their parent's) and tau: with one
+    # frozen tau per query the shards' decisions are the unsharded ones
+    idx, Q = built["idx"], built["Q"]
+    ref = H.gpu_search(G, idx, Q, 10, 8, 0, mode="full", want=("probes",))
+    tau = ref["dists"][:, 9].astype(np.float32)
+    base = H.gpu_search(G, idx, Q, 10, 8, 16, probe_in=ref["probes"], tau=tau, estimator="res", res_m=1.0,
+                        want=("stats",))
+    shards = [G.dade_index_shard(idx, 2, s) for s in range(2)]
+    parts = [H.gpu_search(G, sh, Q, 10, 8, 16, probe_in=ref["probes"], tau=tau, estimator="res", res_m=1.0,
+                          want=("stats",)) for sh in shards]
+    assert base["status"] == 0 and all(p["status"] == 0 for p in parts)
+    assert np.array_equal(sum(p["stats"] for p in parts), base["stats"])
+    assert base["stats"][:, 1].sum() > 0
+    mi, md = _merge(G, parts, 10, 10)
+    assert np.array_equal(mi, base["ids"]) and np.array_equal(md, base["dists"])
+    for sh in shards:
+        sh.close()
