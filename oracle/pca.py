@@ -38,3 +38,17 @@ def train_rotation(X: np.ndarray):
 def rotate(X: np.ndarray, mu: np.ndarray, R: np.ndarray) -> np.ndarray:
     """x' = R (x - mu), FP64 (Section IV-A: x_D = R x, after centring)."""
     return (np.asarray(X, dtype=np.float64) - mu) @ np.asarray(R, dtype=np.float64).T
+
+
+def haar_rotation(D: int, seed: int) -> np.ndarray:
+    """A random orthogonal R[D, D] from the Haar measure, FP64: the random
+    rotation of ADS (Section III, Distance Estimation).  Q from the QR
+    decomposition of a standard Gaussian matrix, with each column's sign set
+    by the sign of R's diagonal entry so that the distribution is exactly
+    Haar (Mezzadri, "How to generate random matrices from the classical
+    compact groups", 2007).  Returned as rows (x' = R x)."""
+    G = np.random.default_rng(seed).standard_normal((D, D))
+    Qm, Rm = np.linalg.qr(G)
+    s = np.sign(np.diag(Rm))
+    s[s == 0] = 1.0
+    return (Qm * s[None, :]).T.copy()

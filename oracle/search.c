@@ -21,6 +21,12 @@
  *    candidate is pruned iff C1 - C2 - m sigma > tau.  sigma_i^2 is the
  *    variance of rotated dimension i over the indexed vectors; x_r is taken
  *    at the stored precision, like dis'_s, so the estimate is exact at d = D.
+ *  - Or (ADS) the test of Section III (Distance Estimation / Distance
+ *    Correction): over a random rotation, dis' = (D/d) dis'_s estimates dis
+ *    from the first d dims, and the candidate is pruned iff
+ *    dis' > (1 + eps) tau.  eps = eps0 / sqrt(d): the lemma's failure
+ *    probability 2 exp(-c0 d eps^2) equals the significance level
+ *    2 exp(-c0 eps0^2) of the test exactly when d eps^2 = eps0^2.
  *  - A candidate that passes every test adds the last slab, which completes
  *    the rotated distance dis'_S at the stored precision.  At d = D
  *    Algorithm 2's test has no residual term and compares the distance with
@@ -99,14 +105,17 @@ static double exact_distance(const float* x, const float* q, int D)
  * steps taken (the step at which the candidate was pruned, or S-1 when it
  * passed every test); *pruned tells which.  partials (may be NULL) receives
  * dis'_s for every step taken. */
-/* RES terms of a query: suffix sums over dims [d, D) of q_i^2 and of
- * q_i^2 sigma_i^2 (arrays of D + 1), the multiplier m, and a candidate
- * scratch of D + 1 doubles for its suffix sums of x_i^2. */
+/* Terms of the RES and ADS tests.  kind 1 (RES): a query's suffix sums
+ * over dims [d, D) of q_i^2 and of q_i^2 sigma_i^2 (arrays of D + 1), the
+ * multiplier m, and a candidate scratch of D + 1 doubles for its suffix
+ * sums of x_i^2.  kind 2 (ADS): eps0. */
 typedef struct {
+    int kind;
     const double* rq;
     const double* sg;
     double m;
     double* rx;
+    double eps0;
 } res_terms;
 
 static int estimate_and_test(const double* qr, const double* xs, int D, int dd, int S,
@@ -116,7 +125,7 @@ static int estimate_and_test(const double* qr, const double* xs, int D, int dd, 
 {
     double p = 0.0;
     *pruned = 0;
-    if (res) {
+    if (res && res->kind == 1) {
         res->rx[D] = 0.0;
         for (int j = D - 1; j >= 0; j--) res->rx[j] = res->rx[j + 1] + xs[j] * xs[j];
     }
@@ -127,16 +136,19 @@ static int estimate_and_test(const double* qr, const double* xs, int D, int dd, 
             p += t * t;
         }
         if (partials) partials[s - 1] = p;
-        double lhs;
-        if (res) {
+        double lhs, rhs = tau;
+        if (res && res->kind == 1) {
             lhs = p + res->rx[j1] + res->rq[j1] - res->m * 2.0 * sqrt(res->sg[j1]);
+        } else if (res && res->kind == 2) {
+            lhs = (double)D / (double)j1 * p;
+            rhs = (1.0 + res->eps0 / sqrt((double)j1)) * tau;
         } else {
             lhs = m1[s - 1] * p + beta[s - 1];
         }
         /* a decision within amb * tau of the threshold may flip under another
          * rounding of the same arithmetic: count it */
-        if (n_amb && isfinite(tau) && fabs(lhs - tau) <= amb * tau) (*n_amb)++;
-        if (lhs > tau) {
+        if (n_amb && isfinite(tau) && fabs(lhs - rhs) <= amb * tau) (*n_amb)++;
+        if (lhs > rhs) {
             *pruned = 1;
             return s;
         }
@@ -168,8 +180,8 @@ typedef struct {
     int32_t D, dd, S, P, Kmax, mode, first_wave, growth;
     double amb, final_rel;
     const double* xerr;
-    int32_t est;            /* 0: learned tables, 1: RES */
-    double res_m;
+    int32_t est;            /* 0: learned tables, 1: RES, 2: ADS */
+    double est_param;       /* RES: m; ADS: eps0 */
     const double* var;      /* D: sigma_i^2 (RES) */
     const double* Qr;
     const float* Q;
@@ -224,6 +236,11 @@ static void search_one(const oracle_args* a, int64_t b)
     q.e = (entry*)malloc(sizeof(entry) * (size_t)(K > 0 ? K : 1));
     res_terms rt, *res = NULL;
     double* rbuf = NULL;
+    if (a->est == 2) {
+        rt.kind = 2;
+        rt.eps0 = a->est_param;
+        res = &rt;
+    }
     if (a->est == 1) {
         const int D = a->D;
         const double* qr = a->Qr + b * D;
@@ -238,7 +255,8 @@ static void search_one(const oracle_args* a, int64_t b)
         }
         rt.rq = rq;
         rt.sg = sg;
-        rt.m = a->res_m;
+        rt.kind = 1;
+        rt.m = a->est_param;
         rt.rx = rbuf + 2 * (D + 1);
         res = &rt;
     }
@@ -282,7 +300,7 @@ static void search_one(const oracle_args* a, int64_t b)
 
 int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t Kmax,
                   int32_t mode, int32_t first_wave, int32_t growth, double amb, double final_rel,
-                  int32_t est, double res_m, const double* var,
+                  int32_t est, double est_param, const double* var,
                   const double* Qr, const float* Q, const double* Xs, const double* xerr, const float* X,
                   const int64_t* ids, const int64_t* list_off,
                   const int64_t* members, const int32_t* probes, const int32_t* nprobe,
@@ -290,9 +308,10 @@ int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, i
                   int64_t* out_ids, double* out_d, int64_t* stats)
 {
     if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1 || mode < 0 || mode > 2 || !(final_rel >= 0.0) ||
-        est < 0 || est > 1 || (est == 1 && (!var || !(res_m >= 0.0))))
+        est < 0 || est > 2 || (est == 1 && (!var || !(est_param >= 0.0))) ||
+        (est == 2 && !(est_param >= 0.0 && est_param < INFINITY)))
         return 1;
-    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, final_rel, xerr, est, res_m, var, Qr, Q,
+    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, final_rel, xerr, est, est_param, var, Qr, Q,
                      Xs, X, ids, list_off, members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < B; b++) search_one(&a, b);

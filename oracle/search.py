@@ -93,14 +93,15 @@ class OracleIndex:
 
 def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode="waves",
            first_wave: int = 1, tau=None, amb: float = 0.0, growth: int = 1, final_rel: float = np.inf,
-           estimator: str = "learned", res_m: float = 8.0):
+           estimator: str = "learned", res_m: float = 8.0, ads_eps0: float = 2.1):
     """Returns (ids[B, Kmax], dists[B, Kmax], stats[B, 5]) where stats holds
     candidates visited, candidates pruned, exact distances taken, dims
     scanned, and tests whose two sides lay within amb * tau of each other
     (decisions another rounding could flip).  final_rel: the slack of the
     test on the completed rotated distance (FINAL_REL), or inf for no test.
-    estimator "res": the Gaussian-bound test with multiplier res_m (m1 and
-    beta unused; None accepted)."""
+    estimator "res": the Gaussian-bound test with multiplier res_m; "ads":
+    the ADS test with parameter ads_eps0 (for both, m1 and beta are unused;
+    None accepted)."""
     lib = _load()
     Q = np.ascontiguousarray(Q, dtype=np.float32)
     B = Q.shape[0]
@@ -116,7 +117,9 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
     m1 = np.ascontiguousarray(m1, dtype=np.float64)
     beta = np.ascontiguousarray(beta, dtype=np.float64)
     assert m1.shape == (max(S - 1, 0),) and beta.shape == m1.shape
-    assert estimator in ("learned", "res")
+    assert estimator in ("learned", "res", "ads")
+    est = {"learned": 0, "res": 1, "ads": 2}[estimator]
+    est_param = res_m if estimator == "res" else ads_eps0
     tau_in = np.ascontiguousarray(np.full(B, np.inf) if tau is None else tau, dtype=np.float64)
     out_ids = np.empty((B, Kmax), dtype=np.int64)
     out_d = np.empty((B, Kmax))
@@ -125,7 +128,7 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
         ctypes.c_int64(B), ctypes.c_int32(idx.D), ctypes.c_int32(delta_d), ctypes.c_int32(S),
         ctypes.c_int32(P), ctypes.c_int32(Kmax), ctypes.c_int32(MODES[mode]),
         ctypes.c_int32(first_wave), ctypes.c_int32(growth), ctypes.c_double(amb), ctypes.c_double(final_rel),
-        ctypes.c_int32(1 if estimator == "res" else 0), ctypes.c_double(res_m), _p(idx.var),
+        ctypes.c_int32(est), ctypes.c_double(est_param), _p(idx.var),
         _p(Qr), _p(Q), _p(idx.Xs), _p(idx.xerr), _p(idx.X),
         _p(idx.ids),
         _p(idx.list_off), _p(idx.members), _p(probes), _p(nprobe), _p(K), _p(m1), _p(beta),

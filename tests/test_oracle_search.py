@@ -3,7 +3,7 @@ structure, Section V-A/B learned test and incremental correction)."""
 import numpy as np
 import pytest
 
-from oracle import ivf, knn, search
+from oracle import ivf, knn, pca, search
 
 
 def _worked_index(order_b=(3, 2, 4)):
@@ -335,3 +335,76 @@ def test_res_loss_rate_follows_the_gaussian_error_model(m):
     want = 1 - 0.5 * (1 + erf(m / sqrt(2)))
     got = lost / len(Q)
     assert abs(got - want) < 4 * sqrt(want * (1 - want) / len(Q)) + 0.01, (got, want)
+
+
+def test_ads_worked_example_by_hand():
+    """ADS (Section III: dis' = (D/d) dis'_s over a random rotation, pruned iff
+    dis' > (1 + eps) tau, eps = eps0 / sqrt(d)) on two vectors, D = 4,
+    Delta_d = 2, identity rotation, frozen tau = 3, q = (1, 0, 1, 0).
+    After dims [0, 2) (d = 2): x0 = (1, 0, 2, 0): dis'_1 = 0, dis' = 0, dis = 1;
+    x1 = (3, 0, 0, 0): dis'_1 = 4, dis' = 8, dis = 5.
+      eps0 = 0:         8 > 3: x1 pruned; x0 kept.
+      eps0 = sqrt(2):   eps = 1, (1 + eps) tau = 6 < 8: x1 pruned.
+      eps0 = 2 sqrt(2): eps = 2, 9 >= 8: x1 gets its exact distance (5 > 3: dropped).
+    A dropped D/d factor (dis' = 4) would keep x1 at eps0 = sqrt(2); eps0 / d in
+    place of eps0 / sqrt(d) (eps = sqrt(2), 7.24 < 8) would prune it at 2 sqrt(2)."""
+    X = np.array([[1, 0, 2, 0], [3, 0, 0, 0]], dtype=np.float32)
+    idx = search.OracleIndex(X, np.zeros(4), np.eye(4), np.zeros((1, 4)), np.zeros(2, np.int32), dtype="f64")
+    Q = np.array([[1, 0, 1, 0]], dtype=np.float32)
+    pr = np.zeros((1, 1), np.int32)
+    for e0, st_exp in [(0.0, [2, 1, 1, 6]), (np.sqrt(2), [2, 1, 1, 6]), (2 * np.sqrt(2), [2, 0, 2, 8])]:
+        ids, d, st = search.search(idx, Q, pr, 1, 2, 2, None, None, mode="frozen", tau=np.array([3.0]),
+                                   estimator="ads", ads_eps0=e0)
+        assert list(ids[0]) == [0, -1], e0
+        assert d[0, 0] == 1.0
+        assert list(st[0][:4]) == st_exp, e0
+
+
+def test_ads_estimate_is_unbiased_over_random_rotations():
+    # over Haar rotations, (D/d) times the squared norm of the first d rotated
+    # coordinates has mean ||x||^2 (each coordinate's square has mean
+    # ||x||^2 / D); and its relative spread shrinks like 1/sqrt(d), which is
+    # what makes eps = eps0 / sqrt(d) a fixed significance level
+    rng = np.random.default_rng(3)
+    D = 32
+    x = rng.standard_normal(D)
+    n2 = float(x @ x)
+    est = {4: [], 16: []}
+    for seed in range(4000):
+        y = pca.haar_rotation(D, seed) @ x
+        for d in est:
+            est[d].append(D / d * float(y[:d] @ y[:d]))
+    for d, v in est.items():
+        v = np.asarray(v)
+        assert abs(v.mean() / n2 - 1) < 4 * v.std() / n2 / np.sqrt(len(v)), d
+    r = np.std(est[4]) / np.std(est[16])
+    # for a uniformly random direction the first d squared coordinates sum
+    # to Beta(d/2, (D-d)/2) times ||x||^2, so Var[(D/d) ...] = 2 (D-d) / (d (D+2)) ||x||^4
+    want = np.sqrt((2 * (D - 4) / (4 * (D + 2))) / (2 * (D - 16) / (16 * (D + 2))))
+    assert abs(r / want - 1) < 0.1, (r, want)
+
+
+def test_ads_prunes_nothing_at_large_eps0_and_matches_pruning_off(small):
+    idx = small["idx"]
+    Q = small["Q"][:20]
+    probes = idx.probe(idx.rotate_queries(Q), 8)
+    S = search.n_steps(small["D"], 8)
+    off = search.search(idx, Q, probes, 8, 10, 8, *search.disabled_tables(S))
+    ads = search.search(idx, Q, probes, 8, 10, 8, None, None, estimator="ads", ads_eps0=1e9)
+    assert np.array_equal(ads[0], off[0]) and np.array_equal(ads[1], off[1])
+    assert ads[2][:, 1].sum() == 0
+    tight = search.search(idx, Q, probes, 8, 10, 8, None, None, estimator="ads", ads_eps0=0.5)
+    assert tight[2][:, 1].sum() > 0
+
+
+def test_haar_rotation_is_orthogonal_and_uniform():
+    D = 24
+    R = pca.haar_rotation(D, 1)
+    assert np.abs(R @ R.T - np.eye(D)).max() < 1e-12
+    # the first row is uniform on the sphere: over seeds its entries have
+    # mean 0 and variance 1/D, and the sign of R's determinant is +-1 at random
+    rows = np.stack([pca.haar_rotation(D, s)[0] for s in range(3000)])
+    assert abs(rows.mean()) < 4 / np.sqrt(rows.size * D)
+    assert abs(rows.var() * D - 1) < 0.05
+    dets = [np.sign(np.linalg.det(pca.haar_rotation(6, s))) for s in range(400)]
+    assert 0.35 < np.mean(np.asarray(dets) > 0) < 0.65
