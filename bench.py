@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-estimators", action="store_true",
+                    help="skip the RES and ADS comparison lines")
     ap.add_argument("--cpu-sample-queries", type=int, default=400)
     ap.add_argument("--workload", default="sift1m", choices=sorted(WORKLOAD_INFO),
                     help="sift1m (the benchmark line) or gist1m")
@@ -256,6 +258,52 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------- main arm
+def compare_estimators(G, X, Q, gt, idx, mean, R, nlist, K, slabs, maxp, nps, steps, warmup):
+    """The other estimators of the paper on the same data and buckets, each
+    autotuned to the same recall target and timed like the main line:
+      res: the Gaussian-bound test of Section IV-C on the PCA index, m = 8
+           (the paper's multiplier for SIFT- and GIST-like data);
+      ads: ADS (Section III) -- a Haar-random rotation of the same buckets
+           (centroids mapped through the rotations) and the scaled test with
+           eps0 = 2.1, Delta_d = 32 (the paper's ADS setting)."""
+    from paper_2404_16322_gb300 import autotune
+    D = X.shape[1]
+    esz = {"f32": 4, "bf16": 2, "fp8": 1}[slabs]
+    out = {}
+
+    def measure(run, best):
+        total, per = run.time(best["nprobe"], best["delta_d"], "prune", steps, warmup,
+                              first_wave=best["first_wave"], growth=best["growth"], final_test=best["final_test"])
+        run.run(best["nprobe"], best["delta_d"], "prune", stats=True, first_wave=best["first_wave"],
+                growth=best["growth"], final_test=best["final_test"])
+        run.result()
+        st = run.stats.cpu().numpy()
+        pruned_dims = st[:, 3] - st[:, 2] * D
+        return {"value": run.B / (total / steps / 1000.0), "unit": "queries/s", "nprobe": best["nprobe"],
+                "delta_d": best["delta_d"], "first_wave": best["first_wave"], "wave_growth_log2": best["growth"],
+                "final_test": best["final_test"], "recall@10": best["recall"],
+                "scanned_dims_ratio": float(st[:, 3].sum() / (st[:, 0].sum() * D)),
+                "bytes_per_query": float((pruned_dims * esz + st[:, 2] * (D * esz + D * 4)).sum() / run.B)}
+
+    run = autotune.Bench(G, idx, Q, K, maxp, DELTAS, estimator="res", res_m=8.0)
+    best, _ = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, nprobes=nps, mode="prune")
+    out["res"] = dict(measure(run, best), res_m=8.0)
+    del run
+
+    Rh = G.dade_random_rotation(D, seed=4)
+    C = G.dade_index_centroids(idx).astype(np.float64) @ R     # back to the centred input space
+    Ch = (C @ Rh.T).astype(np.float32)
+    ads_idx = G.ivf_build(X, mean, Rh, nlist, dtype=slabs, centroids=Ch, assign=G.dade_index_assignment(idx))
+    m1, beta = G.dade_ads_table(D, 32, 2.1)
+    G.dade_set_correction(ads_idx, 32, m1, beta)
+    run = autotune.Bench(G, ads_idx, Q, K, maxp, (32,))
+    best, _ = autotune.autotune(run, gt, TARGET_RECALL, 10, (32,), nprobes=nps, mode="prune")
+    out["ads"] = dict(measure(run, best), eps0=2.1)
+    del run
+    ads_idx.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -421,6 +469,16 @@ def main():
             serve_out.append(o)
         del srv
 
+    estimators = None
+    if not args.no_estimators:
+        estimators = compare_estimators(G, X, Q, gt, idx, mean, R, nlist, K, slabs, maxp, nps, args.steps,
+                                        args.warmup)
+        estimators["learned"] = {"value": value / world, "unit": "queries/s", "nprobe": bd["nprobe"],
+                                 "delta_d": bd["delta_d"], "recall@10": bd["recall"], "scanned_dims_ratio": scan_ratio,
+                                 "bytes_per_query": dade_bytes}
+        estimators["speedup_learned_vs_ads"] = value / world / estimators["ads"]["value"]
+        estimators["speedup_learned_vs_res"] = value / world / estimators["res"]["value"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K,
@@ -446,6 +504,7 @@ def main():
         "scanned_dims_ratio": scan_ratio,
         "latency_ms": {"batch_p50": float(np.percentile(per, 50)), "batch_p99": float(np.percentile(per, 99))},
         "serving": serve_out,
+        "estimators": estimators,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "wave_scan_kernel", "per_launch_ms": per_launch_ms,

@@ -76,6 +76,30 @@ dade_status dade_train_rotation(const float* X_host, int64_t n, int32_t D, int64
                                 double* eigvals_out);
 
 /* ------------------------------------------------------------------------
+ * ADS baseline (Section III, "Distance Estimation" and "Distance
+ * Correction"): a random rotation and a scaled partial-distance test, run
+ * by the same search kernels through a correction table.
+ *
+ * dade_random_rotation: R_out[D x D] (host, caller-owned FP64) is a random
+ * orthogonal matrix from the Haar measure, row i the i-th output axis
+ * (x' = R x): the positive-diagonal QR factor of a seeded standard Gaussian
+ * matrix.  Pass it to ivf_build in place of the PCA rotation.
+ *
+ * dade_ads_table: the table (m1_s, beta_s), s = 1..S-1, S = ceil(D/delta_d),
+ * for which the search's test m1_s dis'_s + beta_s > tau is ADS's test
+ * (D/d) dis'_s > (1 + eps) tau with d = min(s delta_d, D) and
+ * eps = eps0 / sqrt(d) (the lemma's failure probability 2 exp(-c0 d eps^2)
+ * held at the significance level 2 exp(-c0 eps0^2)): m1_s = (D/d) / (1 + eps),
+ * beta_s = 0.  Install it with dade_set_correction.  The paper's setting is
+ * eps0 = 2.1 with delta_d = 32.  m1_out, beta_out: host, S - 1 floats.
+ * Errors: DADE_EINVAL (null pointer, D or delta_d out of range, eps0 < 0 or
+ * not finite).
+ * ---------------------------------------------------------------------- */
+dade_status dade_random_rotation(int32_t D, uint64_t seed, double* R_out);
+
+dade_status dade_ads_table(int32_t D, int32_t delta_d, double eps0, float* m1_out, float* beta_out);
+
+/* ------------------------------------------------------------------------
  * ivf_build -- rotate the database and build the IVF index (Section II-A).
  *
  * X_host: N x D FP32 rows; mean[D], R[D x D] FP64 from dade_train_rotation

@@ -14,13 +14,13 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["dade_train_rotation", "ivf_build", "dade_fit_correction", "dade_fit_samples",
+__all__ = ["dade_train_rotation", "dade_random_rotation", "dade_ads_table", "ivf_build", "dade_fit_correction", "dade_fit_samples",
            "dade_set_correction", "dade_get_correction", "dade_search", "dade_search_noalloc",
            "dade_search_workspace_size",
            "dade_index_info_get", "dade_index_centroids", "dade_index_assignment",
            "dade_index_list_sizes", "dade_index_save", "dade_index_load", "dade_index_free",
            "dade_stage_timing", "dade_stage_timing_read", "dade_last_error", "Index", "library",
-           "n_steps"]
+           "n_steps", "dade_shard_owners", "dade_index_shard", "dade_merge_topk"]
 
 _LIB = None
 
@@ -94,6 +94,23 @@ def dade_train_rotation(X, sample_n: int = 0, seed: int = 0):
     _check(library().dade_train_rotation(X.ctypes.data, n, D, int(sample_n), int(seed), mean.ctypes.data,
                                          R.ctypes.data, lam.ctypes.data))
     return mean, R, lam
+
+
+def dade_random_rotation(D: int, seed: int = 0):
+    """Haar-random orthogonal R[D, D] (FP64, host): the ADS rotation."""
+    R = np.empty((int(D), int(D)))
+    _check(library().dade_random_rotation(int(D), int(seed), R.ctypes.data))
+    return R
+
+
+def dade_ads_table(D: int, delta_d: int, eps0: float = 2.1):
+    """The correction table that makes the search's test ADS's
+    (D/d) dis' > (1 + eps0/sqrt(d)) tau: returns (m1, beta), S - 1 floats."""
+    S = n_steps(D, delta_d)
+    m1 = np.zeros(max(S - 1, 1), np.float32)
+    beta = np.zeros(max(S - 1, 1), np.float32)
+    _check(library().dade_ads_table(int(D), int(delta_d), float(eps0), m1.ctypes.data, beta.ctypes.data))
+    return m1[:S - 1], beta[:S - 1]
 
 
 def ivf_build(X, mean, R, nlist: int, kmeans_iters: int = 10, seed: int = 0, dtype: str = "f32",

@@ -43,6 +43,8 @@ class IndexInfo(ctypes.Structure):
 # name -> (restype, argtypes), in the order of include/dade.h
 SIGNATURES = {
     "dade_train_rotation": (ctypes.c_int, [c_vp, c_i64, c_i32, c_i64, c_u64, c_vp, c_vp, c_vp]),
+    "dade_random_rotation": (ctypes.c_int, [c_i32, c_u64, c_vp]),
+    "dade_ads_table": (ctypes.c_int, [c_i32, c_i32, c_f64, c_vp, c_vp]),
     "ivf_build": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp, ctypes.POINTER(BuildParams),
                                  ctypes.POINTER(c_vp)]),
     "dade_fit_correction": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_f64, c_u64, c_i64,

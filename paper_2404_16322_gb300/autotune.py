@@ -24,11 +24,15 @@ def recall_at(ids: np.ndarray, gt: np.ndarray, k: int) -> float:
 
 
 class Bench:
-    """Device-resident batch for repeated dade_search calls."""
+    """Device-resident batch for repeated dade_search calls.  estimator
+    "learned" uses the index's tables; "res" the Gaussian-bound test with
+    multiplier res_m."""
 
-    def __init__(self, G, idx, Q, K: int, max_nprobe: int, deltas=(8, 16, 32), schedules=None):
+    def __init__(self, G, idx, Q, K: int, max_nprobe: int, deltas=(8, 16, 32), schedules=None,
+                 estimator: str = "learned", res_m: float = 8.0):
         import torch
         self.G, self.idx, self.torch = G, idx, torch
+        self.estimator, self.res_m = estimator, res_m
         dev = torch.device("cuda")
         self.B, self.K = len(Q), K
         self.q = torch.from_numpy(np.ascontiguousarray(Q, np.float32)).to(dev)
@@ -40,7 +44,7 @@ class Bench:
         self.stats = torch.zeros((self.B, 4), dtype=torch.int64, device=dev)
         sched = ((1, 1),) + tuple(schedules if schedules is not None else SCHEDULES)
         ws = max(G.dade_search_workspace_size(idx, self.B, dd, K, max_nprobe, mode=m, first_wave=fw,
-                                              wave_growth_log2=g)
+                                              wave_growth_log2=g, estimator=estimator)
                  for m in ("prune", "full") for dd in deltas for fw, g in sched)
         self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
 
@@ -51,7 +55,7 @@ class Bench:
         self.G.dade_search(self.idx, self.q, self.k, self.np, delta_d, self.ids, self.d, max_K=self.K,
                            max_nprobe=nprobe, mode=mode, status=self.status, first_wave=first_wave,
                            stats=self.stats if stats else None, workspace=self.ws, wave_growth_log2=growth,
-                           final_test=final_test)
+                           final_test=final_test, estimator=self.estimator, res_m=self.res_m)
 
     def result(self) -> np.ndarray:
         self.torch.cuda.synchronize()

@@ -413,6 +413,27 @@ extern "C" dade_status dade_train_rotation(const float* X, int64_t n, int32_t D,
     return jacobi_eigh(D, cov.data(), eig_out, R_out);
 }
 
+extern "C" dade_status dade_random_rotation(int32_t D, uint64_t seed, double* R_out) {
+    clear_error();
+    if (!R_out) return fail(DADE_EINVAL, "null argument");
+    if (D < 1 || D > kMaxD) return fail(DADE_EINVAL, "D out of range");
+    return haar_rotation(D, seed, R_out);
+}
+
+extern "C" dade_status dade_ads_table(int32_t D, int32_t delta_d, double eps0, float* m1_out, float* beta_out) {
+    clear_error();
+    if (!m1_out || !beta_out) return fail(DADE_EINVAL, "null argument");
+    if (D < 1 || D > kMaxD || delta_d < 1) return fail(DADE_EINVAL, "D or delta_d out of range");
+    if (!(eps0 >= 0.0 && eps0 < INFINITY)) return fail(DADE_EINVAL, "eps0 must be finite and >= 0");
+    const int S = (int)ceil_div(D, delta_d);
+    for (int s = 1; s < S; ++s) {
+        const double d = (double)std::min<int64_t>((int64_t)s * delta_d, D);
+        m1_out[s - 1] = (float)((double)D / d / (1.0 + eps0 / sqrt(d)));
+        beta_out[s - 1] = 0.f;
+    }
+    return DADE_OK;
+}
+
 extern "C" dade_status dade_fit_samples(const double* partials, const double* tau, const int8_t* label,
                                         int64_t n, int32_t D, int32_t delta_d, double target_recall,
                                         int32_t min_label0, double* m1_out, double* beta_out) {

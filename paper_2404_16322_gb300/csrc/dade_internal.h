@@ -121,6 +121,7 @@ namespace dade {
 dade_status covariance_fp64(const float* X, int64_t n, int32_t D, const int64_t* rows,
                             int64_t m, double* mean, double* cov);
 dade_status jacobi_eigh(int32_t D, const double* A, double* eigvals, double* R);
+dade_status haar_rotation(int32_t D, uint64_t seed, double* R_out);
 dade_status fit_tables(const double* partials, const double* tau, const int8_t* label,
                        int64_t n, int32_t S, double target_recall, int32_t min_label0,
                        double* m1_out, double* beta_out);

@@ -309,4 +309,70 @@ dade_status fit_tables(const double* partials, const double* tau, const int8_t* 
     return DADE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Haar-random rotation (the random projection of ADS, Section III "Distance
+// Estimation"): a D x D standard Gaussian matrix (Box-Muller on counter-based
+// SplitMix64 uniforms of (seed, index)), its Householder QR in FP64
+// (Golub and Van Loan, Sec. 5.2), and Q with column j times sign(R_jj), the
+// QR factor with a positive diagonal, which is Haar distributed for a
+// Gaussian input (Mezzadri 2007).  R_out's row i is Q's column i.
+dade_status haar_rotation(int32_t D, uint64_t seed, double* R_out) {
+    const size_t n = (size_t)D;
+    std::vector<double> A(n * n);  // column-major: A[j * n + i] = A(i, j)
+    const double two_pi = 6.283185307179586476925286766559;
+    for (size_t k = 0; k < n * n; k += 2) {
+        const uint64_t z1 = splitmix64(seed ^ splitmix64(2 * (uint64_t)k));
+        const uint64_t z2 = splitmix64(seed ^ splitmix64(2 * (uint64_t)k + 1));
+        const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1.0p-53;  // (0, 1]
+        const double u2 = (double)(z2 >> 11) * 0x1.0p-53;          // [0, 1)
+        const double r = sqrt(-2.0 * log(u1));
+        A[k] = r * cos(two_pi * u2);
+        if (k + 1 < n * n) A[k + 1] = r * sin(two_pi * u2);
+    }
+    // Householder: column k is reduced by H_k = I - 2 v v^T (|v| = 1);
+    // vs[k] holds v (entries k..n-1), diag[k] = R_kk
+    std::vector<double> vs(n * n, 0.0), diag(n);
+    for (size_t k = 0; k < n; ++k) {
+        double* a = &A[k * n];
+        double nrm = 0.0;
+        for (size_t i = k; i < n; ++i) nrm += a[i] * a[i];
+        nrm = sqrt(nrm);
+        const double alpha = a[k] > 0 ? -nrm : nrm;  // avoids cancellation in v_k
+        double* v = &vs[k * n];
+        for (size_t i = k; i < n; ++i) v[i] = a[i];
+        v[k] -= alpha;
+        double vn = 0.0;
+        for (size_t i = k; i < n; ++i) vn += v[i] * v[i];
+        vn = sqrt(vn);
+        diag[k] = alpha;
+        if (vn == 0.0) continue;  // column already reduced (measure zero)
+        for (size_t i = k; i < n; ++i) v[i] /= vn;
+        for (size_t j = k; j < n; ++j) {
+            double* c = &A[j * n];
+            double dot = 0.0;
+            for (size_t i = k; i < n; ++i) dot += v[i] * c[i];
+            for (size_t i = k; i < n; ++i) c[i] -= 2.0 * dot * v[i];
+        }
+    }
+    // Q = H_0 H_1 ... H_{n-1} I, built from the right: Q e_j for every j
+    std::vector<double> Q(n * n, 0.0);  // column-major
+    for (size_t j = 0; j < n; ++j) {
+        double* q = &Q[j * n];
+        q[j] = 1.0;
+        for (size_t kk = n; kk-- > 0;) {
+            const double* v = &vs[kk * n];
+            double dot = 0.0;
+            for (size_t i = kk; i < n; ++i) dot += v[i] * q[i];
+            if (dot != 0.0)
+                for (size_t i = kk; i < n; ++i) q[i] -= 2.0 * dot * v[i];
+        }
+    }
+    for (size_t j = 0; j < n; ++j) {
+        const double sg = diag[j] < 0 ? -1.0 : 1.0;
+        for (size_t i = 0; i < n; ++i) R_out[j * n + i] = sg * Q[j * n + i];
+    }
+    return DADE_OK;
+}
+
 }  // namespace dade
+

@@ -96,3 +96,48 @@ def test_library_errors_are_status_codes(lib):
     assert e.value.status == 1 and "at least 2 rows" in str(e.value)
     with pytest.raises(_lib.DadeError):
         lib.dade_fit_samples(np.zeros((1, 7)), np.ones(1), np.zeros(1), 128, 12)
+
+
+def test_library_random_rotation_is_orthogonal_seeded_and_haar(lib):
+    R = lib.dade_random_rotation(40, seed=5)
+    assert np.abs(R @ R.T - np.eye(40)).max() < 1e-12
+    assert np.array_equal(R, lib.dade_random_rotation(40, seed=5))
+    assert not np.allclose(R, lib.dade_random_rotation(40, seed=6))
+    # Haar: every entry has mean 0 and variance 1/D; the determinant's sign
+    # is +-1 with equal odds (a plain Householder Q without the sign fix has
+    # a fixed pattern); the first row is uniform on the sphere, so its largest
+    # |entry| has the distribution of a uniform direction's, compared here by
+    # the mean against the oracle's numpy-made Haar rotations
+    from oracle import pca
+    D = 8
+    Rs = np.stack([lib.dade_random_rotation(D, seed=s) for s in range(2000)])
+    assert abs(Rs.mean()) < 4 / np.sqrt(Rs.size * D)
+    assert abs(Rs.var() * D - 1) < 0.03
+    dets = np.sign(np.linalg.det(Rs))
+    assert 0.45 < np.mean(dets > 0) < 0.55
+    ref = np.stack([pca.haar_rotation(D, s) for s in range(2000)])
+    a, b = np.abs(Rs[:, 0]).max(1), np.abs(ref[:, 0]).max(1)
+    assert abs(a.mean() - b.mean()) < 4 * np.sqrt(a.var() / len(a) + b.var() / len(b))
+    # diagonal entries are not biased toward positive values
+    assert abs(np.mean(Rs[:, np.arange(D), np.arange(D)])) < 4 / np.sqrt(2000 * D * D) * np.sqrt(D)
+
+
+def test_library_ads_table_reproduces_the_oracle_ads_test(lib, tiny):
+    # the installed table turns the learned test into ADS's: the oracle run
+    # with the table as a learned test prunes exactly as the oracle's own ADS
+    # test (decisions inside the FP32 rounding band of m1 excepted)
+    from oracle import search
+    idx = search.OracleIndex(tiny["X"], tiny["mu"], tiny["R"], tiny["C"], tiny["assign"])
+    Q = tiny["Q"][:40]
+    pr = idx.probe(idx.rotate_queries(Q), 8)
+    for dd, e0 in [(16, 2.1), (32, 2.1), (8, 0.7)]:
+        m1, beta = lib.dade_ads_table(128, dd, e0)
+        assert m1.shape == (search.n_steps(128, dd) - 1,) and np.all(beta == 0)
+        ads = search.search(idx, Q, pr, 8, 10, dd, None, None, estimator="ads", ads_eps0=e0, amb=1e-6)
+        tab = search.search(idx, Q, pr, 8, 10, dd, m1.astype(np.float64), beta.astype(np.float64))
+        un = ads[2][:, 4] == 0
+        assert un.mean() > 0.9
+        assert np.array_equal(ads[2][un, :4], tab[2][un, :4]), (dd, e0)
+        assert ads[2][:, 1].sum() > 0
+    with pytest.raises(Exception):
+        lib.dade_ads_table(128, 16, -1.0)
