@@ -255,6 +255,11 @@ typedef struct {
     int32_t estimator;       /* PRUNE mode: dade_estimator (0: learned tables)  */
     float res_m;             /* DADE_EST_RES: the multiplier m of sigma, >= 0   */
                              /* (larger m prunes less; the paper's default 8)  */
+    int32_t test_steps;      /* PRUNE mode: only the first test_steps steps are */
+                             /* tested; their survivors go straight to the     */
+                             /* exact distance (the same results as a table    */
+                             /* whose later steps are disabled).  0: all S - 1. */
+                             /* Not with final_test (DADE_ENOTIMPL).           */
 } dade_search_opts;
 
 dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,

@@ -32,7 +32,8 @@ class SearchOpts(ctypes.Structure):
                 ("tau_dev", c_vp), ("probe_in_dev", c_vp), ("probe_out_dev", c_vp),
                 ("qrot_out_dev", c_vp), ("stats_dev", c_vp), ("status_dev", c_vp),
                 ("workspace", c_vp), ("workspace_bytes", c_sz), ("wave_growth_log2", c_i32),
-                ("final_test", c_i32), ("estimator", c_i32), ("res_m", ctypes.c_float)]
+                ("final_test", c_i32), ("estimator", c_i32), ("res_m", ctypes.c_float),
+                ("test_steps", c_i32)]
 
 
 class IndexInfo(ctypes.Structure):

@@ -29,6 +29,7 @@ struct WaveView {
     int32_t final_test;       // PRUNE: test the completed rotated distance before the exact one
     int32_t est;              // PRUNE: 0 learned tables, 1 the Gaussian-bound (RES) test
     int32_t res_stride;       // S - 1: entries of res_q per query
+    int32_t test_steps;       // PRUNE without final_test: steps tested (<= S - 1)
     const float* res_q;       // B x (S - 1): ||q'_r||^2 - m sigma after each step (RES)
     const float* qrot;        // B x Dpad rotated queries
     const float* qpad;        // B x Dpad original queries, zero padded

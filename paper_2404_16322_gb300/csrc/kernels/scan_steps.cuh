@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(kScanThreads, (NBLK <= 2 && !FULL && !EST) ? 7
                                                          ix.Dpad, m1, beta, scl, ix.eps ? ix.eps + slot0 : nullptr,
                                                          rt, wv.status, wv.staged_bytes, want_stats, pd);
             else
-                ok = run_steps<E, NBLK, true, false, EST>(slab, npad, t, nt, nq, S - 1, ix.nb, ix.D, sh, ph,
+                ok = run_steps<E, NBLK, true, false, EST>(slab, npad, t, nt, nq, wv.test_steps, ix.nb, ix.D, sh, ph,
                                                           wv.qrot, ix.Dpad, m1, beta, scl, nullptr, rt, wv.status,
                                                           wv.staged_bytes, want_stats, pd);
             if (!ok) break;

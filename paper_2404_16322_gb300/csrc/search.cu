@@ -80,6 +80,10 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     v.est = uses_res(o) ? 1 : 0;
     v.res_stride = v.est ? (int)ceil_div(idx->Dpad, delta_d) - 1 : 0;
     v.n_waves = nw;
+    {
+        const int all = delta_d > 0 ? (int)ceil_div(idx->Dpad, delta_d) - 1 : 0;
+        v.test_steps = o.test_steps > 0 ? std::min(all, (int)o.test_steps) : all;
+    }
     v.qrot = c.take<float>((size_t)B * idx->Dpad);
     v.qpad = c.take<float>((size_t)B * idx->Dpad);
     pl->scores = o.probe_in_dev ? nullptr : c.take<float>((size_t)B * nl);
@@ -130,6 +134,9 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
     if (o.first_wave < 0) return fail(DADE_EINVAL, "first_wave < 0");
     if (o.wave_growth_log2 < 0 || o.wave_growth_log2 > 30) return fail(DADE_EINVAL, "wave_growth_log2 must be in [0, 30]");
     if (o.estimator != DADE_EST_LEARNED && o.estimator != DADE_EST_RES) return fail(DADE_EINVAL, "bad estimator");
+    if (o.test_steps < 0) return fail(DADE_EINVAL, "test_steps < 0");
+    if (o.test_steps > 0 && o.final_test && o.mode == DADE_SCAN_PRUNE)
+        return fail(DADE_ENOTIMPL, "test_steps with final_test");
     if (o.estimator == DADE_EST_RES && !(o.res_m >= 0.f && o.res_m < INFINITY))
         return fail(DADE_EINVAL, "res_m must be finite and >= 0");
     if (o.mode == DADE_SCAN_PRUNE) {

@@ -58,7 +58,7 @@ def build_gpu(G, X, inp, nlist, dtype="f32", delta_d=16):
 
 def gpu_search(G, idx, Q, K, nprobe, delta_d, mode="prune", probe_in=None, tau=None, max_K=None,
                max_nprobe=None, first_wave=0, growth=0, final_test=False, estimator="learned", res_m=8.0,
-               want=()):
+               test_steps=0, want=()):
     import torch
     B = Q.shape[0]
     Kv = np.broadcast_to(np.asarray(K, np.int32), (B,)).copy()
@@ -83,7 +83,7 @@ def gpu_search(G, idx, Q, K, nprobe, delta_d, mode="prune", probe_in=None, tau=N
     tin = None if tau is None else torch.from_numpy(np.ascontiguousarray(tau, np.float32)).to(dev)
     G.dade_search(idx, q, k, n, delta_d, ids, dists, max_K=max_K, max_nprobe=max_nprobe, mode=mode,
                   first_wave=first_wave, tau=tin, probe_in=pin, status=status, wave_growth_log2=growth,
-                  final_test=final_test, estimator=estimator, res_m=res_m,
+                  final_test=final_test, estimator=estimator, res_m=res_m, test_steps=test_steps,
                   **{kw: t for kw, t in extra.values()})
     torch.cuda.synchronize()
     st = int(status.item())

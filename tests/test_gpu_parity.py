@@ -279,6 +279,11 @@ def test_host_errors(G, tiny_setup):
         H.gpu_search(G, s["idx"], s["Q"], 10, 8, 12)
     with pytest.raises(_lib.DadeError):
         H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, max_K=2000)
+    with pytest.raises(_lib.DadeError) as e:
+        H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, test_steps=2, final_test=True)
+    assert e.value.status == 6
+    with pytest.raises(_lib.DadeError):
+        H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, test_steps=-1)
 
 
 def test_save_load_roundtrip(G, tiny_setup, tmp_path):
@@ -341,3 +346,20 @@ def test_library_build_and_fit_end_to_end(G):
     assert r_prune >= r_full - 0.02
     assert out["stats"][:, 1].sum() > 0.5 * out["stats"][:, 0].sum()
     idx.close()
+
+
+@pytest.mark.parametrize("L", [1, 3])
+def test_tested_steps_limit_matches_disabled_later_steps(G, tiny_pre, L):
+    """test_steps = L tests only the first L steps and sends their survivors
+    to the exact distance: the oracle runs the same search with every later
+    step of the table disabled (m1 = 0, beta = -inf)."""
+    s = tiny_pre
+    m1 = s["inp"]["m1"].astype(np.float64).copy()
+    beta = s["inp"]["beta"].astype(np.float64).copy()
+    m1[L:], beta[L:] = 0.0, -np.inf
+    ids, d, st, pr = _oracle(s, s["Q"], 10, 8, m1=m1, beta=beta)
+    out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, test_steps=L, want=("stats",))
+    assert out["status"] == 0
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb=st[:, 4], min_strict=s["strict"])
+    un = st[:, 4] == 0
+    assert np.array_equal(out["stats"][un], st[un, :4])
