@@ -92,7 +92,7 @@ def cache_key(G, idx, K: int, target: float, mode: str) -> str:
             f"|{h}|K{K}|r{target}|{mode}")
 
 
-SCHEDULES = ((1, 1), (4, 1), (8, 1), (8, 2), (8, 30), (16, 30))
+SCHEDULES = ((1, 1), (4, 1), (8, 1), (8, 2), (4, 30), (8, 30), (16, 30))
 
 
 def autotune(bench: Bench, gt: np.ndarray, target: float = 0.95, k_recall: int = 10,
