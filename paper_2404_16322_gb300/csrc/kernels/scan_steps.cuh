@@ -342,6 +342,7 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
     float* part = sh.part + warp * kWarpCap;
     const int c_own = warp * 32 + lane;
     const bool own_valid = c_own < nt;
+    const bool warp_live = warp * 32 < nt;  // warps past the tile's end skip the dense work
     // the query values (and FP8 scales) of step k for every query of the
     // unit: each thread handles kVals values (and one scale); step k + 1's
     // are loaded into registers during step k and stored after its last read
@@ -399,7 +400,7 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
             // query of the unit
 #pragma unroll
             for (int bb = 0; bb < NBLK; ++bb) {
-                if (bb < nbk) {
+                if (warp_live && bb < nbk) {
                     float x[8];
                     load8_staged(bk + ((size_t)bb * kT + c_own) * kBlock, sh.sc + bb * kBlock, x);
 #pragma unroll
@@ -412,7 +413,7 @@ __device__ __forceinline__ bool run_steps(const E* src, int64_t npad, int t, int
                     }
                 }
             }
-            if (PRUNE) {
+            if (PRUNE && warp_live) {
                 // test every pair; the survivors of (this warp, query g) go
                 // to list (warp + g) mod kWarps, so every list gets a share
                 // of every warp's candidates and of every query.  Pass 1
