@@ -175,7 +175,7 @@ def traffic_from_profiles(kernel_src_hash):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ["scan.cu", "scan.cuh"]:
+    for f in ["scan.cu", "scan.cuh", "scan_steps.cuh"]:
         h.update(open(os.path.join(ROOT, "paper_2404_16322_gb300", "csrc", "kernels", f), "rb").read())
     return h.hexdigest()[:12]
 
