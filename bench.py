@@ -83,7 +83,7 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                       "-i", str(gpu_index), "-lms", "50"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -91,6 +91,16 @@ class ClockSampler:
 
     def mark(self):
         self.marks.append(time.time())
+
+    def wait_ready(self, timeout_s=5.0):
+        """Block until nvidia-smi has written its first sample, so that the
+        samples cover the timed region that follows."""
+        t0 = time.time()
+        while self.p and time.time() - t0 < timeout_s:
+            self.f.flush()
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.02)
 
     def stop(self):
         if self.p:
@@ -240,7 +250,9 @@ def reference_arm(args):
     cfg = dict(synth.WORKLOADS["sift1m"])
     n_q = 40
     t0 = time.perf_counter()
-    cb, times = oracle_baseline(cfg, 64, 16, 100, n_q, steps=args.steps + args.warmup, first_wave=4)
+    # the configuration the GPU arm's autotuner selects on this workload
+    # (nprobe 64, Delta_d 16, first wave 8, one later wave)
+    cb, times = oracle_baseline(cfg, 64, 16, 100, n_q, steps=args.steps + args.warmup, first_wave=8, growth=30)
     wall = time.perf_counter() - t0
     timed = times[args.warmup:] or times
     ms = 1000.0 * float(np.mean(timed))
@@ -250,7 +262,7 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "sift1m-shaped sample (see cpu_baseline.sample)", "nprobe": 64, "K": 100,
-                       "delta_d": 16, "first_wave": 4},
+                       "delta_d": 16, "first_wave": 8, "wave_growth_log2": 30},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
@@ -368,6 +380,7 @@ def main():
         import torch.distributed as dist
         dist.barrier()
     sampler = ClockSampler(local)
+    sampler.wait_ready()
     for _ in range(args.warmup):
         run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"],
                 final_test=bd["final_test"])
