@@ -183,10 +183,16 @@ def traffic_from_profiles(kernel_src_hash):
     return float(t.group(1))
 
 
-def kernel_hash():
+def kernel_hash(root=ROOT):
+    """sha256 of the scan kernel's sources with comments and blank lines
+    removed (a comment edit does not make the recorded counters stale)."""
     h = hashlib.sha256()
     for f in ["scan.cu", "scan.cuh", "scan_steps.cuh"]:
-        h.update(open(os.path.join(ROOT, "paper_2404_16322_gb300", "csrc", "kernels", f), "rb").read())
+        src = open(os.path.join(root, "paper_2404_16322_gb300", "csrc", "kernels", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
     return h.hexdigest()[:12]
 
 

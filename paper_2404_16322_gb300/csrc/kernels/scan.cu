@@ -1,6 +1,9 @@
-// Refinement kernels: work units per wave, the persistent estimate-and-prune
-// scan, the exact distance, the per-query top-K merge and the replay that
-// collects training samples for the correction.
+// Refinement kernels around the wave scan: work units per wave (counting
+// sort of (bucket, query) items, prefix scans, unit descriptors), the
+// per-query top-K merge, the output, the replay that collects training
+// samples for the correction, and the launchers.  The estimate-and-prune
+// scan itself is the template in scan_steps.cuh; this file instantiates its
+// learned-table and full-scan variants (scan_res.cu the RES ones).
 //
 // Method (arXiv 2404.16322): a candidate's distance is accumulated Delta_d
 // rotated dimensions at a time (the loop of Algorithm 2); after each step the
@@ -9,18 +12,6 @@
 // the exact distance and join the result queue whose largest entry is tau
 // (Section I).  tau is frozen per wave of probe ranks so that all
 // (bucket, query) pairs of a wave run in parallel.
-//
-// Work unit = (bucket l, tile of up to kT candidates, group of up to kG
-// queries probing l in this wave).  The unit's Delta_d slab of the tile is
-// one bulk copy per 8-dim block (cp.async.bulk into shared memory, double
-// buffered, completion on an mbarrier) and is shared by every query of the
-// group.  Each warp owns queries; a query's live candidates are a compacted
-// list (index, partial distance) rebuilt after each test with a warp ballot.
-//
-// Distance arithmetic (identical in every path, so a pair's distance does
-// not depend on which path computed it): per 8-dim block b,
-// s_b = sum_j fma((q_j - x_j)^2) from 0 in j order; the distance adds s_b in
-// block order.  This bounds the FP32 rounding by (8 + D/8) ulp-terms.
 #include "scan_steps.cuh"
 #include "warp_select.cuh"
 

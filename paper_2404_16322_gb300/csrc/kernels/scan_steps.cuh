@@ -1,31 +1,25 @@
-// The estimate-and-prune wave scan (Algorithm 2 loop, tested per step) as a
-// template over slab type, step width and test, included by the
-// translation units that instantiate it (scan.cu: learned tables and the
-// full scan; scan_res.cu: the Gaussian-bound test of Section IV-C).
-//
-// Refinement kernels: work units per wave, the persistent estimate-and-prune
-// scan, the exact distance, the per-query top-K merge and the replay that
-// collects training samples for the correction.
+// The estimate-and-prune wave scan as a template over slab type, step width
+// and test, included by the translation units that instantiate it (scan.cu:
+// learned tables and the full scan; scan_res.cu: the Gaussian-bound test of
+// Section IV-C).
 //
 // Method (arXiv 2404.16322): a candidate's distance is accumulated Delta_d
-// rotated dimensions at a time (the loop of Algorithm 2); after each step the
-// learned test m1_s * dis' + beta_s > tau prunes it (Section V-A; one
-// classifier per step, Section V-B "Incremental Correction"); survivors get
-// the exact distance and join the result queue whose largest entry is tau
-// (Section I).  tau is frozen per wave of probe ranks so that all
-// (bucket, query) pairs of a wave run in parallel.
+// rotated dimensions at a time (the loop of Algorithm 2); after each step a
+// test prunes it against tau, the result queue's largest entry (Section I);
+// survivors get the exact distance from the original vector.
 //
 // Work unit = (bucket l, tile of up to kT candidates, group of up to kG
 // queries probing l in this wave).  The unit's Delta_d slab of the tile is
 // one bulk copy per 8-dim block (cp.async.bulk into shared memory, double
 // buffered, completion on an mbarrier) and is shared by every query of the
-// group.  Each warp owns queries; a query's live candidates are a compacted
-// list (index, partial distance) rebuilt after each test with a warp ballot.
+// group.  Step 0 is dense (thread c scores candidate c against every query);
+// the surviving (query, candidate) pairs then live in per-warp lists that
+// are compacted with warp ballots after every later test.
 //
 // Distance arithmetic (identical in every path, so a pair's distance does
-// not depend on which path computed it): per 8-dim block b,
-// s_b = sum_j fma((q_j - x_j)^2) from 0 in j order; the distance adds s_b in
-// block order.  This bounds the FP32 rounding by (8 + D/8) ulp-terms.
+// not depend on which path computed it): per 8-dim block b, the even and the
+// odd dims each form an FMA chain of (q_j - x_j)^2 in dim order (packed FP32
+// pairs), s_b = even + odd; the distance adds s_b in block order.
 #pragma once
 
 #include <climits>
