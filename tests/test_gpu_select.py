@@ -1,8 +1,8 @@
-"""The top-nprobe bucket selection on the device: its filtered path (a
-prefix's np-th smallest distance bounds the row's, one pass keeps the keys
-below the bound) against its direct path, on 4096 centroids of which every
-one has three exact duplicates, so that ties in distance are exact and must
-be broken by the lower list id.  The direct path runs for nprobe > 256."""
+"""The top-nprobe bucket selection on the device, on 4096 centroids of
+which every one has three exact duplicates, so that ties in distance are
+exact and must be broken by the lower list id: the nprobe nearest are the
+first nprobe of any larger selection (the order is a total order on
+(distance, id)), and equal distances come out in increasing id order."""
 import numpy as np
 import pytest
 
@@ -39,9 +39,9 @@ def _probes(G, s, nprobe):
     return out["probes"]
 
 
-def test_filtered_selection_equals_the_direct_one(G, dup_index):
-    ref = _probes(G, dup_index, 600)                    # direct path
-    for np_ in (1, 7, 64, 200, 256):                    # filtered path
+def test_smaller_selections_are_prefixes_of_larger_ones(G, dup_index):
+    ref = _probes(G, dup_index, 600)
+    for np_ in (1, 7, 64, 200, 256):
         got = _probes(G, dup_index, np_)
         assert np.array_equal(got[:, :np_], ref[:, :np_]), np_
 
