@@ -74,23 +74,27 @@ def label_rows(rows: dict, topk_ids: np.ndarray, seed: int = 0, cap: int = 500_0
 
 
 def _loss_grad(theta, A, y, ridge):
+    k = len(theta) - 1
     z = A @ theta
     # log(1 + e^z) - y z, computed stably
-    loss = np.mean(np.logaddexp(0.0, z) - y * z) + 0.5 * ridge * (theta[0] ** 2 + theta[1] ** 2)
+    loss = np.mean(np.logaddexp(0.0, z) - y * z) + 0.5 * ridge * float(theta[:k] @ theta[:k])
     p = 0.5 * (1.0 + np.tanh(0.5 * z))
     g = A.T @ (p - y) / len(y)
-    g[:2] += ridge * theta[:2]
+    g[:k] += ridge * theta[:k]
     return loss, g, p
 
 
 def fit_logistic(F: np.ndarray, y: np.ndarray, ridge: float = 1e-8, max_iter: int = 50,
                  tol: float = 1e-10):
-    """Minimise mean binary cross-entropy + ridge/2 * (w1^2 + w2^2) of
-    P(y = 1) = sigmoid(w1 f1 + w2 f2 + b) by damped Newton steps.
-    Returns (theta = [w1, w2, b], iterations, max |gradient|)."""
+    """Minimise mean binary cross-entropy + ridge/2 * |w|^2 of
+    P(y = 1) = sigmoid(w . f + b) by damped Newton steps (any number of
+    features; the correction of Section V-A uses f = (dis', tau), OPQ-L adds
+    the quantisation error).  Returns (theta = [w..., b], iterations,
+    max |gradient|)."""
     A = np.column_stack([np.asarray(F, dtype=np.float64), np.ones(len(y))])
     y = np.asarray(y, dtype=np.float64)
-    theta = np.zeros(3)
+    k = A.shape[1] - 1
+    theta = np.zeros(k + 1)
     loss, g, p = _loss_grad(theta, A, y, ridge)
     it = 0
     for it in range(1, max_iter + 1):
@@ -99,8 +103,7 @@ def fit_logistic(F: np.ndarray, y: np.ndarray, ridge: float = 1e-8, max_iter: in
             break
         w = p * (1.0 - p) / len(y)
         H = A.T @ (A * w[:, None])
-        H[0, 0] += ridge
-        H[1, 1] += ridge
+        H[np.arange(k), np.arange(k)] += ridge
         step = np.linalg.solve(H, g)
         t = 1.0
         while True:
@@ -180,3 +183,37 @@ def fit_correction(partials: np.ndarray, tau: np.ndarray, label: np.ndarray, D: 
                 active = active & ~(m * p + bp > tau)
         info.append(rec)
     return m1, beta, info
+
+
+def fit_pq_correction(dis: np.ndarray, err: np.ndarray, tau: np.ndarray, label: np.ndarray, r: float = 0.995,
+                      min_label0: int = 100):
+    """OPQ-L's classifier (Section V-B "Approximate Distances": features the
+    asymmetric distance dis', the threshold tau and the distance e from the
+    vector to its quantised reconstruction; one classifier, no steps).
+    Logistic fit on (dis'/tau_bar, tau/tau_bar, e/sqrt(tau_bar)) as above;
+    prune iff m1 dis' + m3 e + beta > tau with m1 = -w1/w2,
+    m3 = -w3 sqrt(tau_bar)/w2; beta' is the largest value keeping label-0
+    recall >= r (v_i = tau_i - m1 dis'_i - m3 e_i over label 0, the
+    (floor((1 - r) n0) + 1)-th smallest).  Returns (m1, m3, beta', info);
+    a failed fit (w2 >= 0, too few samples) returns (0, 0, -inf)."""
+    dis = np.asarray(dis, dtype=np.float64)
+    err = np.asarray(err, dtype=np.float64)
+    tau = np.asarray(tau, dtype=np.float64)
+    lab0 = np.asarray(label) == 0
+    n0, n1 = int(lab0.sum()), int((~lab0).sum())
+    info = dict(n0=n0, n1=n1, enabled=False)
+    if n0 < min_label0 or n1 == 0:
+        return 0.0, 0.0, -np.inf, info
+    tb = float(tau.mean())
+    F = np.column_stack([dis / tb, tau / tb, err / math.sqrt(tb)])
+    theta, iters, gmax = fit_logistic(F, (~lab0).astype(np.float64))
+    w1, w2, w3, b = theta
+    info.update(w1=w1, w2=w2, w3=w3, b=b, tau_bar=tb, iters=iters, grad=gmax)
+    if not w2 < 0:
+        return 0.0, 0.0, -np.inf, info
+    m1 = -w1 / w2
+    m3 = -w3 * math.sqrt(tb) / w2
+    v = tau[lab0] - m1 * dis[lab0] - m3 * err[lab0]
+    bp = beta_prime_closed_form(v, r)
+    info.update(enabled=True, m1=m1, m3=m3, beta=-b * tb / w2, beta_prime=bp)
+    return m1, m3, bp, info

@@ -27,6 +27,11 @@
  *    dis' > (1 + eps) tau.  eps = eps0 / sqrt(d): the lemma's failure
  *    probability 2 exp(-c0 d eps^2) equals the significance level
  *    2 exp(-c0 eps0^2) of the test exactly when d eps^2 = eps0^2.
+ *  - Or (OPQ-L, Section V-B "Approximate Distances") one test before the
+ *    exact distance, on the asymmetric distance dis' = sum_j lut_q[j][code_j]
+ *    of the vector's product-quantisation codes and its quantisation error
+ *    e: pruned iff m1 dis' + m3 e + beta > tau (the learned classifier with
+ *    three features); a pruned candidate scans no rotated dimension.
  *  - A candidate that passes every test adds the last slab, which completes
  *    the rotated distance dis'_S at the stored precision.  At d = D
  *    Algorithm 2's test has no residual term and compares the distance with
@@ -180,8 +185,12 @@ typedef struct {
     int32_t D, dd, S, P, Kmax, mode, first_wave, growth;
     double amb, final_rel;
     const double* xerr;
-    int32_t est;            /* 0: learned tables, 1: RES, 2: ADS */
-    double est_param;       /* RES: m; ADS: eps0 */
+    int32_t est;            /* 0: learned tables, 1: RES, 2: ADS, 3: OPQ-L */
+    double est_param;       /* RES: m; ADS: eps0; OPQ-L: m3 */
+    int32_t pq_m;           /* OPQ-L: subspaces */
+    const uint8_t* pq_codes; /* OPQ-L: N x pq_m codes (rows as Xs) */
+    const double* pq_err;   /* OPQ-L: N quantisation errors */
+    const double* pq_lut;   /* OPQ-L: B x pq_m x 256 tables */
     const double* var;      /* D: sigma_i^2 (RES) */
     const double* Qr;
     const float* Q;
@@ -207,8 +216,20 @@ static int visit(const oracle_args* a, int64_t b, int64_t pos, double tau, entry
 {
     const double* qr = a->Qr + b * a->D;
     int pruned;
-    int steps = estimate_and_test(qr, a->Xs + pos * a->D, a->D, a->dd, a->S, a->m1, a->beta, tau,
+    int steps;
+    if (a->est == 3) {
+        const double* t = a->pq_lut + b * (int64_t)a->pq_m * 256;
+        const uint8_t* c = a->pq_codes + pos * a->pq_m;
+        double dis = 0.0;
+        for (int j = 0; j < a->pq_m; j++) dis += t[j * 256 + c[j]];
+        double lhs = a->m1[0] * dis + a->est_param * a->pq_err[pos] + a->beta[0];
+        if (isfinite(tau) && fabs(lhs - tau) <= a->amb * tau) st[4]++;
+        pruned = lhs > tau;
+        steps = 0;
+    } else {
+        steps = estimate_and_test(qr, a->Xs + pos * a->D, a->D, a->dd, a->S, a->m1, a->beta, tau,
                                   a->xerr ? a->xerr[pos] : 0.0, a->final_rel, &pruned, NULL, a->amb, &st[4], res);
+    }
     st[0] += 1;
     if (pruned) {
         int64_t dims = (int64_t)steps * a->dd;
@@ -301,6 +322,7 @@ static void search_one(const oracle_args* a, int64_t b)
 int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t Kmax,
                   int32_t mode, int32_t first_wave, int32_t growth, double amb, double final_rel,
                   int32_t est, double est_param, const double* var,
+                  int32_t pq_m, const uint8_t* pq_codes, const double* pq_err, const double* pq_lut,
                   const double* Qr, const float* Q, const double* Xs, const double* xerr, const float* X,
                   const int64_t* ids, const int64_t* list_off,
                   const int64_t* members, const int32_t* probes, const int32_t* nprobe,
@@ -308,10 +330,12 @@ int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, i
                   int64_t* out_ids, double* out_d, int64_t* stats)
 {
     if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1 || mode < 0 || mode > 2 || !(final_rel >= 0.0) ||
-        est < 0 || est > 2 || (est == 1 && (!var || !(est_param >= 0.0))) ||
-        (est == 2 && !(est_param >= 0.0 && est_param < INFINITY)))
+        est < 0 || est > 3 || (est == 1 && (!var || !(est_param >= 0.0))) ||
+        (est == 2 && !(est_param >= 0.0 && est_param < INFINITY)) ||
+        (est == 3 && (pq_m < 1 || !pq_codes || !pq_err || !pq_lut || !m1 || !beta)))
         return 1;
-    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, final_rel, xerr, est, est_param, var, Qr, Q,
+    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, final_rel, xerr, est, est_param,
+                     pq_m, pq_codes, pq_err, pq_lut, var, Qr, Q,
                      Xs, X, ids, list_off, members, probes, nprobe, K, m1, beta, tau_in, out_ids, out_d, stats};
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < B; b++) search_one(&a, b);

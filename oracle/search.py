@@ -93,7 +93,7 @@ class OracleIndex:
 
 def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode="waves",
            first_wave: int = 1, tau=None, amb: float = 0.0, growth: int = 1, final_rel: float = np.inf,
-           estimator: str = "learned", res_m: float = 8.0, ads_eps0: float = 2.1):
+           estimator: str = "learned", res_m: float = 8.0, ads_eps0: float = 2.1, pq=None):
     """Returns (ids[B, Kmax], dists[B, Kmax], stats[B, 5]) where stats holds
     candidates visited, candidates pruned, exact distances taken, dims
     scanned, and tests whose two sides lay within amb * tau of each other
@@ -101,7 +101,9 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
     test on the completed rotated distance (FINAL_REL), or inf for no test.
     estimator "res": the Gaussian-bound test with multiplier res_m; "ads":
     the ADS test with parameter ads_eps0 (for both, m1 and beta are unused;
-    None accepted)."""
+    None accepted); "pq": OPQ-L's single test m1 dis' + m3 e + beta > tau
+    with pq = dict(codes[N, m] uint8, err[N], lut[B, m, 256], m1, m3, beta)
+    (rows in the index's row order)."""
     lib = _load()
     Q = np.ascontiguousarray(Q, dtype=np.float32)
     B = Q.shape[0]
@@ -116,10 +118,20 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
         m1, beta = np.zeros(max(S - 1, 0)), np.zeros(max(S - 1, 0))
     m1 = np.ascontiguousarray(m1, dtype=np.float64)
     beta = np.ascontiguousarray(beta, dtype=np.float64)
-    assert m1.shape == (max(S - 1, 0),) and beta.shape == m1.shape
-    assert estimator in ("learned", "res", "ads")
-    est = {"learned": 0, "res": 1, "ads": 2}[estimator]
+    assert (m1.shape == (max(S - 1, 0),) or estimator == "pq") and beta.shape == m1.shape
+    assert estimator in ("learned", "res", "ads", "pq")
+    est = {"learned": 0, "res": 1, "ads": 2, "pq": 3}[estimator]
     est_param = res_m if estimator == "res" else ads_eps0
+    pq_m, pq_codes, pq_err, pq_lut = 0, None, None, None
+    if estimator == "pq":
+        pq_codes = np.ascontiguousarray(pq["codes"], dtype=np.uint8)
+        pq_m = pq_codes.shape[1]
+        pq_err = np.ascontiguousarray(pq["err"], dtype=np.float64)
+        pq_lut = np.ascontiguousarray(pq["lut"], dtype=np.float64)
+        assert pq_codes.shape[0] == idx.N and pq_lut.shape == (B, pq_m, 256)
+        m1 = np.array([pq["m1"]])
+        beta = np.array([pq["beta"]])
+        est_param = float(pq["m3"])
     tau_in = np.ascontiguousarray(np.full(B, np.inf) if tau is None else tau, dtype=np.float64)
     out_ids = np.empty((B, Kmax), dtype=np.int64)
     out_d = np.empty((B, Kmax))
@@ -129,6 +141,8 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
         ctypes.c_int32(P), ctypes.c_int32(Kmax), ctypes.c_int32(MODES[mode]),
         ctypes.c_int32(first_wave), ctypes.c_int32(growth), ctypes.c_double(amb), ctypes.c_double(final_rel),
         ctypes.c_int32(est), ctypes.c_double(est_param), _p(idx.var),
+        ctypes.c_int32(pq_m), None if pq_codes is None else _p(pq_codes), None if pq_err is None else _p(pq_err),
+        None if pq_lut is None else _p(pq_lut),
         _p(Qr), _p(Q), _p(idx.Xs), _p(idx.xerr), _p(idx.X),
         _p(idx.ids),
         _p(idx.list_off), _p(idx.members), _p(probes), _p(nprobe), _p(K), _p(m1), _p(beta),
