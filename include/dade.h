@@ -224,7 +224,7 @@ dade_status dade_get_correction(const dade_index* idx, int32_t delta_d, float* m
  * it is never cleared by the library.
  * ---------------------------------------------------------------------- */
 typedef enum { DADE_SCAN_PRUNE = 0, DADE_SCAN_FULL = 1 } dade_scan_mode;
-typedef enum { DADE_EST_LEARNED = 0, DADE_EST_RES = 1 } dade_estimator;
+typedef enum { DADE_EST_LEARNED = 0, DADE_EST_RES = 1, DADE_EST_PQ = 2 } dade_estimator;
 
 typedef struct {
     int32_t mode;            /* dade_scan_mode                                    */
@@ -252,7 +252,9 @@ typedef struct {
                              /* trades a last slab step for fewer exact          */
                              /* distances.  0: survivors of step S - 1 go        */
                              /* straight to the exact distance.                  */
-    int32_t estimator;       /* PRUNE mode: dade_estimator (0: learned tables)  */
+    int32_t estimator;       /* PRUNE mode: dade_estimator (0: learned tables;  */
+                             /* DADE_EST_PQ: OPQ-L, see dade_pq_train; it      */
+                             /* ignores delta_d, final_test and test_steps)    */
     float res_m;             /* DADE_EST_RES: the multiplier m of sigma, >= 0   */
                              /* (larger m prunes less; the paper's default 8)  */
     int32_t test_steps;      /* PRUNE mode: only the first test_steps steps are */
@@ -261,6 +263,54 @@ typedef struct {
                              /* whose later steps are disabled).  0: all S - 1. */
                              /* Not with final_test (DADE_ENOTIMPL).           */
 } dade_search_opts;
+
+/* ------------------------------------------------------------------------
+ * OPQ-L (Section V-B "Approximate Distances"): the approximate distance is
+ * OPQ's asymmetric distance dis' = sum_j ||q'_j - c_j,code_j||^2 over m
+ * subspaces of D/m rotated dims (256 centroids each; the query exact), and
+ * the learned correction has a third feature, the stored vector's distance
+ * e to its quantised reconstruction: a candidate is pruned iff
+ * m1 dis' + m3 e + beta > tau, one test before its exact distance.  OPQ's
+ * rotation is its parametric solution on the index's PCA basis: the rotated
+ * dims, in decreasing variance, are dealt m per round to the subspaces, the
+ * larger variances to the subspaces of smaller product of variances so far.
+ *
+ * dade_pq_train: X_host (n x D FP32, n >= 256) is rotated on the host in
+ * FP64; codebooks by Lloyd k-means in FP64 per subspace (iters iterations
+ * from a seeded sample of 256 rows); then as dade_pq_set.  perm_out (D
+ * int32) and codebooks_out (m x 256 x D/m FP32) may be NULL.
+ * dade_pq_set: installs the allocation perm (subspace j's dims at
+ * perm[j D/m .. (j + 1) D/m)) and the codebooks, and encodes every stored
+ * vector on the device (nearest centroid per subspace, the lower index on a
+ * tie; e in FP32).  Replaces any earlier quantiser and its correction.
+ * D/m must be <= 64.
+ * dade_pq_fit_correction: the classifier fitted on replayed training
+ * queries as dade_fit_correction does (same labels and thinning); logistic
+ * regression on (dis'/tau_bar, tau/tau_bar, e/sqrt(tau_bar)), m1 = -w1/w2,
+ * m3 = -w3 sqrt(tau_bar)/w2, beta' the largest value keeping label-0 recall
+ * >= target_recall (w2 >= 0 or too few samples: m1 = m3 = 0, beta = -inf,
+ * never prunes).  out3 (host, may be NULL) = {m1, m3, beta'}.
+ * dade_pq_fit_samples: that host FP64 fit alone on caller samples.
+ * dade_pq_set_correction / dade_pq_get: install / read the classifier; read
+ * m, and the codes (N x m, input-row order) and e (N) of the stored vectors.
+ * Errors: DADE_EINVAL, DADE_ESTATE (no quantiser), DADE_ENOMEM, DADE_ECUDA.
+ * ---------------------------------------------------------------------- */
+dade_status dade_pq_train(dade_index* idx, const float* X_host, int64_t n, int32_t m, int32_t iters,
+                          uint64_t seed, int32_t* perm_out, float* codebooks_out);
+
+dade_status dade_pq_set(dade_index* idx, int32_t m, const int32_t* perm_host, const float* codebooks_host);
+
+dade_status dade_pq_fit_correction(dade_index* idx, const float* train_q_host, int64_t nt, int32_t K,
+                                   int32_t nprobe, double target_recall, uint64_t seed, int64_t label1_cap,
+                                   float* out3);
+
+dade_status dade_pq_fit_samples(const double* dis, const double* err, const double* tau, const int8_t* label,
+                                int64_t n, double target_recall, int32_t min_label0, double* out3);
+
+dade_status dade_pq_set_correction(dade_index* idx, float m1, float m3, float beta);
+
+dade_status dade_pq_get(const dade_index* idx, int32_t* m_out, float* correction3, uint8_t* codes_host,
+                        float* err_host);
 
 dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,
                         const int32_t* K_dev, const int32_t* nprobe_dev, int32_t delta_d,

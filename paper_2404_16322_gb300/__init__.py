@@ -20,7 +20,8 @@ __all__ = ["dade_train_rotation", "dade_random_rotation", "dade_ads_table", "ivf
            "dade_index_info_get", "dade_index_centroids", "dade_index_assignment",
            "dade_index_list_sizes", "dade_index_save", "dade_index_load", "dade_index_free",
            "dade_stage_timing", "dade_stage_timing_read", "dade_last_error", "Index", "library",
-           "n_steps", "dade_shard_owners", "dade_index_shard", "dade_merge_topk"]
+           "n_steps", "dade_shard_owners", "dade_index_shard", "dade_merge_topk", "dade_pq_train", "dade_pq_set",
+           "dade_pq_fit_correction", "dade_pq_fit_samples", "dade_pq_set_correction", "dade_pq_get"]
 
 _LIB = None
 
@@ -154,6 +155,70 @@ def dade_fit_samples(partials, tau, label, D: int, delta_d: int, target_recall: 
                                       int(delta_d), float(target_recall), int(min_label0), m1.ctypes.data,
                                       beta.ctypes.data))
     return m1[:S - 1], beta[:S - 1]
+
+
+def dade_pq_train(idx: Index, X, m: int, iters: int = 10, seed: int = 0):
+    """OPQ-L quantiser (parametric OPQ on the index's PCA basis, m subspaces
+    of 256 centroids) trained on the rows of X (host FP32, original space);
+    every stored vector is encoded on the device.  Returns (perm, codebooks)."""
+    X = _host(X, np.float32)
+    n, D = X.shape
+    perm = np.empty(D, np.int32)
+    cb = np.empty((int(m), 256, D // int(m)), np.float32)
+    _check(library().dade_pq_train(idx.ptr, X.ctypes.data, n, int(m), int(iters), int(seed), perm.ctypes.data,
+                                   cb.ctypes.data))
+    return perm, cb
+
+
+def dade_pq_set(idx: Index, perm, codebooks) -> None:
+    perm = _host(perm, np.int32)
+    cb = _host(codebooks, np.float32)
+    _check(library().dade_pq_set(idx.ptr, int(cb.shape[0]), perm.ctypes.data, cb.ctypes.data))
+
+
+def dade_pq_fit_correction(idx: Index, T, K: int, nprobe: int, target_recall: float = 0.995, seed: int = 0,
+                           label1_cap: int = 500_000):
+    """OPQ-L's three-feature classifier fitted on replayed training queries;
+    returns (m1, m3, beta)."""
+    T = _host(T, np.float32)
+    out = np.zeros(3, np.float32)
+    _check(library().dade_pq_fit_correction(idx.ptr, T.ctypes.data, len(T), int(K), int(nprobe), float(target_recall),
+                                            int(seed), int(label1_cap), out.ctypes.data))
+    return tuple(float(v) for v in out)
+
+
+def dade_pq_fit_samples(dis, err, tau, label, target_recall: float = 0.995, min_label0: int = 100):
+    d = _host(dis, np.float64)
+    e = _host(err, np.float64)
+    t = _host(tau, np.float64)
+    lab = _host(label, np.int8)
+    out = np.zeros(3)
+    _check(library().dade_pq_fit_samples(d.ctypes.data, e.ctypes.data, t.ctypes.data, lab.ctypes.data, len(t),
+                                         float(target_recall), int(min_label0), out.ctypes.data))
+    return tuple(float(v) for v in out)
+
+
+def dade_pq_set_correction(idx: Index, m1: float, m3: float, beta: float) -> None:
+    _check(library().dade_pq_set_correction(idx.ptr, float(m1), float(m3), float(beta)))
+
+
+def dade_pq_get(idx: Index, codes: bool = False):
+    """(m, (m1, m3, beta) or None, codes[N, m] and err[N] in input-row order if asked)."""
+    m = ctypes.c_int32(0)
+    _check(library().dade_pq_get(idx.ptr, ctypes.byref(m), None, None, None))
+    corr = np.zeros(3, np.float32)
+    try:
+        _check(library().dade_pq_get(idx.ptr, None, corr.ctypes.data, None, None))
+        c3 = tuple(float(v) for v in corr)
+    except L.DadeError:
+        c3 = None
+    if not codes:
+        return m.value, c3
+    N = dade_index_info_get(idx)["N"]
+    cd = np.empty((N, m.value), np.uint8)
+    er = np.empty(N, np.float32)
+    _check(library().dade_pq_get(idx.ptr, None, None, cd.ctypes.data, er.ctypes.data))
+    return m.value, c3, cd, er
 
 
 def dade_set_correction(idx: Index, delta_d: int, m1, beta) -> None:

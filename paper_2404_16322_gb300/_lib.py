@@ -19,7 +19,7 @@ STATUS = {0: "DADE_OK", 1: "DADE_EINVAL", 2: "DADE_ENOMEM", 3: "DADE_ECUDA", 4: 
           5: "DADE_ESTATE", 6: "DADE_ENOTIMPL", 7: "DADE_EIO"}
 SLAB = {"f32": 0, "bf16": 1, "fp8": 2}
 MODE = {"prune": 0, "full": 1}
-ESTIMATOR = {"learned": 0, "res": 1}
+ESTIMATOR = {"learned": 0, "res": 1, "pq": 2}
 
 
 class BuildParams(ctypes.Structure):
@@ -45,6 +45,12 @@ class IndexInfo(ctypes.Structure):
 SIGNATURES = {
     "dade_train_rotation": (ctypes.c_int, [c_vp, c_i64, c_i32, c_i64, c_u64, c_vp, c_vp, c_vp]),
     "dade_random_rotation": (ctypes.c_int, [c_i32, c_u64, c_vp]),
+    "dade_pq_train": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_i32, c_u64, c_vp, c_vp]),
+    "dade_pq_set": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),
+    "dade_pq_fit_correction": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_i32, c_f64, c_u64, c_i64, c_vp]),
+    "dade_pq_fit_samples": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f64, c_i32, c_vp]),
+    "dade_pq_set_correction": (ctypes.c_int, [c_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "dade_pq_get": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dade_ads_table": (ctypes.c_int, [c_i32, c_i32, c_f64, c_vp, c_vp]),
     "ivf_build": (ctypes.c_int, [c_vp, c_i64, c_i32, c_vp, c_vp, ctypes.POINTER(BuildParams),
                                  ctypes.POINTER(c_vp)]),

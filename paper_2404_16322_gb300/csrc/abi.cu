@@ -182,7 +182,8 @@ extern "C" dade_status dade_index_info_get(const dade_index* idx, dade_index_inf
     out->max_list = idx->max_list;
     out->device_bytes = (int64_t)(idx->slab_dev.bytes + idx->orig_dev.bytes + idx->ids_dev.bytes +
                                   idx->cent_dev.bytes + idx->R_dev.bytes + idx->eps_dev.bytes + idx->var_dev.bytes +
-                                  idx->sfx_dev.bytes);
+                                  idx->sfx_dev.bytes + idx->pq_codes_dev.bytes + idx->pq_err_dev.bytes +
+                                  idx->pq_cb_dev.bytes + idx->pq_perm_dev.bytes);
     return DADE_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -109,6 +110,15 @@ struct dade_index {
     dade::DevBuf var_dev;      // Dpad FP32: variance of each rotated dimension (RES)
     dade::DevBuf sfx_dev;      // (nb + 1) x total_slots FP32: residual norms from block b on (RES)
     std::vector<float> var;    // host copy of var_dev
+    // OPQ-L: product quantisation of the stored rotated vectors
+    int32_t pq_m = 0, pq_ds = 0;
+    std::vector<int32_t> pq_perm;      // D: rotated dims of subspace j at [j*ds, (j+1)*ds)
+    std::vector<float> pq_cb;          // m x 256 x ds codebooks
+    dade::DevBuf pq_perm_dev, pq_cb_dev;
+    dade::DevBuf pq_codes_dev;         // m x total_slots uint8 (subspace-major)
+    dade::DevBuf pq_err_dev;           // total_slots FP32: ||x~ - reconstruction||
+    bool pq_has_table = false;
+    float pq_m1 = 0.f, pq_m3 = 0.f, pq_beta = -INFINITY;
     std::map<int, dade::CorrectionTable> tables;  // by delta_d
     // internal scratch used when the caller gives no workspace
     mutable dade::DevBuf ws;
@@ -125,6 +135,10 @@ dade_status haar_rotation(int32_t D, uint64_t seed, double* R_out);
 dade_status fit_tables(const double* partials, const double* tau, const int8_t* label,
                        int64_t n, int32_t S, double target_recall, int32_t min_label0,
                        double* m1_out, double* beta_out);
+// OPQ-L's three-feature classifier (m1, m3, beta'): prune iff
+// m1 dis' + m3 e + beta' > tau; out = {0, 0, -inf} when the fit fails.
+dade_status fit_pq_host(const double* dis, const double* err, const double* tau, const int8_t* label,
+                        int64_t n, double target_recall, int32_t min_label0, double* out3);
 uint64_t splitmix64(uint64_t z);
 double sample_uniform(uint64_t seed, uint64_t query, uint64_t id);
 
@@ -172,6 +186,12 @@ cudaError_t launch_residual_norms(const void* slab, int dtype, const float* scal
                                   int nlist, int64_t total_slots, int32_t Dpad, float* sfx, cudaStream_t st);
 // The per-slot residual norms of idx's slabs (RES), computed on the device.
 dade_status build_residual_norms(dade_index* idx);
+// OPQ-L kernels (kernels/pq.cu).
+cudaError_t launch_pq_encode(const void* slab, int dtype, const float* scale, const int64_t* list_slot,
+                             int nlist, int64_t total_slots, int32_t Dpad, const int32_t* perm, const float* cb,
+                             int m, int ds, uint8_t* codes, float* err, cudaStream_t st);
+cudaError_t launch_pq_lut(const float* qrot, int64_t B, int32_t Dpad, const int32_t* perm, const float* cb, int m,
+                          int ds, float* lut, cudaStream_t st);
 cudaError_t launch_amax(const float* xrot, int64_t N, int32_t Dpad, float* amax_bits_as_float,
                         cudaStream_t st);
 cudaError_t launch_fp8_scale(float* amax_to_scale, int32_t Dpad, cudaStream_t st);
@@ -206,7 +226,11 @@ struct CollectArgs {
     unsigned long long* n_label1;  // pass 0 counter
     unsigned long long* n_rows;    // pass 1 counter
     int64_t row_cap;
-    float* partials;          // row_cap x (S - 1)
+    float* partials;          // row_cap x (S - 1); OPQ-L: row_cap x 2 (dis', e)
+    int32_t pq_m;             // > 0: OPQ-L rows from the codes and tables below
+    const uint8_t* pq_codes;
+    const float* pq_err;
+    const float* pq_lut;
     float* tau;               // row_cap
     int8_t* label;            // row_cap
 };

@@ -18,27 +18,21 @@
 
 #include "dade_internal.h"
 
-namespace dade {
-}
-
 using namespace dade;
 
-extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int64_t nt, int32_t K,
-                                           int32_t nprobe, int32_t delta_d, double target_recall,
-                                           uint64_t seed, int64_t label1_cap, float* m1_out,
-                                           float* beta_out) {
-    clear_error();
-    if (!idx || !Tq) return fail(DADE_EINVAL, "null argument");
-    if (nt < 1) return fail(DADE_EINVAL, "need training queries");
-    if (K < 1 || K > kMaxK) return fail(DADE_EINVAL, "K out of range");
-    if (nprobe < 1 || nprobe > std::min(idx->nlist, 1024)) return fail(DADE_EINVAL, "nprobe out of range");
-    if (delta_d != 8 && delta_d != 16 && delta_d != 32) return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32");
-    if (!(target_recall > 0 && target_recall <= 1)) return fail(DADE_EINVAL, "target_recall in (0, 1]");
-    if (label1_cap < 1) return fail(DADE_EINVAL, "label1_cap must be >= 1");
-    const int S = (int)ceil_div(idx->Dpad, delta_d);
-    std::vector<float> m1f((size_t)std::max(1, S - 1), 0.f), btf((size_t)std::max(1, S - 1), -INFINITY);
-    if (S <= 1) return install_table_public(idx, delta_d, S, m1f.data(), btf.data());
+namespace {
 
+// Training samples of a replay: ncols values per row (the partial distances
+// dis'_1..dis'_{S-1}, or OPQ-L's (dis', e)), tau at the test and the label,
+// sorted so that the fit does not depend on the device's atomic order.
+struct Samples {
+    int64_t n = 0;
+    std::vector<double> P, T;
+    std::vector<int8_t> L;
+};
+
+dade_status replay_samples(dade_index* idx, const float* Tq, int64_t nt, int32_t K, int32_t nprobe, int32_t delta_d,
+                           uint64_t seed, int64_t label1_cap, int32_t estimator, int ncols, Samples* out) {
     cudaStream_t st;
     DADE_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     struct G {
@@ -69,13 +63,13 @@ extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int
     o.max_nprobe = nprobe;
     o.first_wave = 1;
     o.status_dev = status.as<int32_t>();
+    o.estimator = estimator;
 
     CollectArgs ca{};
     ca.seed = seed;
     ca.topk_stride = K;
     ca.n_label1 = cnt.as<unsigned long long>();
     ca.n_rows = cnt.as<unsigned long long>() + 1;
-
 
     // The collect replays write their own top-K to a scratch output.
     DevBuf scratch_ids;
@@ -108,7 +102,7 @@ extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int
     ca.keep_rate = n1 > (double)label1_cap ? (double)label1_cap / n1 : 1.0;
     ca.row_cap = nt * K + label1_cap + (int64_t)(6.0 * sqrt((double)label1_cap)) + 1024;
     DevBuf rp, rt, rl;
-    DADE_TRY(rp.alloc(sizeof(float) * ca.row_cap * (S - 1)));
+    DADE_TRY(rp.alloc(sizeof(float) * ca.row_cap * ncols));
     DADE_TRY(rt.alloc(sizeof(float) * ca.row_cap));
     DADE_TRY(rl.alloc(sizeof(int8_t) * ca.row_cap));
     ca.partials = rp.as<float>();
@@ -120,7 +114,7 @@ extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int
     DADE_CUDA_TRY(cudaMemcpy(&dev_status, status.p, sizeof dev_status, cudaMemcpyDeviceToHost));
     if (dev_status) return fail((dade_status)dev_status, "device status %d during the replay", dev_status);
     const int64_t n = std::min<int64_t>((int64_t)counts[1], ca.row_cap);
-    std::vector<float> pf((size_t)n * (S - 1)), tf((size_t)n);
+    std::vector<float> pf((size_t)n * ncols), tf((size_t)n);
     std::vector<int8_t> lab((size_t)n);
     DADE_CUDA_TRY(cudaMemcpy(pf.data(), rp.p, sizeof(float) * pf.size(), cudaMemcpyDeviceToHost));
     DADE_CUDA_TRY(cudaMemcpy(tf.data(), rt.p, sizeof(float) * tf.size(), cudaMemcpyDeviceToHost));
@@ -131,22 +125,52 @@ extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int
     std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
         if (lab[a] != lab[b]) return lab[a] < lab[b];
         if (tf[a] != tf[b]) return tf[a] < tf[b];
-        for (int s = 0; s < S - 1; ++s) {
-            float x = pf[(size_t)a * (S - 1) + s], y = pf[(size_t)b * (S - 1) + s];
+        for (int s = 0; s < ncols; ++s) {
+            float x = pf[(size_t)a * ncols + s], y = pf[(size_t)b * ncols + s];
             if (x != y) return x < y;
         }
         return false;
     });
-    std::vector<double> P((size_t)n * (S - 1)), T((size_t)n);
-    std::vector<int8_t> L((size_t)n);
+    out->n = n;
+    out->P.assign((size_t)n * ncols, 0.0);
+    out->T.assign((size_t)n, 0.0);
+    out->L.assign((size_t)n, 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t o2 = ord[(size_t)i];
-        for (int s = 0; s < S - 1; ++s) P[(size_t)i * (S - 1) + s] = pf[(size_t)o2 * (S - 1) + s];
-        T[(size_t)i] = tf[(size_t)o2];
-        L[(size_t)i] = lab[(size_t)o2];
+        for (int s = 0; s < ncols; ++s) out->P[(size_t)i * ncols + s] = pf[(size_t)o2 * ncols + s];
+        out->T[(size_t)i] = tf[(size_t)o2];
+        out->L[(size_t)i] = lab[(size_t)o2];
     }
+    return DADE_OK;
+}
+
+dade_status check_fit_args(const dade_index* idx, const float* Tq, int64_t nt, int32_t K, int32_t nprobe,
+                           double target_recall, int64_t label1_cap) {
+    if (!idx || !Tq) return fail(DADE_EINVAL, "null argument");
+    if (nt < 1) return fail(DADE_EINVAL, "need training queries");
+    if (K < 1 || K > kMaxK) return fail(DADE_EINVAL, "K out of range");
+    if (nprobe < 1 || nprobe > std::min(idx->nlist, 1024)) return fail(DADE_EINVAL, "nprobe out of range");
+    if (!(target_recall > 0 && target_recall <= 1)) return fail(DADE_EINVAL, "target_recall in (0, 1]");
+    if (label1_cap < 1) return fail(DADE_EINVAL, "label1_cap must be >= 1");
+    return DADE_OK;
+}
+
+}  // namespace
+
+extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int64_t nt, int32_t K,
+                                           int32_t nprobe, int32_t delta_d, double target_recall,
+                                           uint64_t seed, int64_t label1_cap, float* m1_out,
+                                           float* beta_out) {
+    clear_error();
+    DADE_TRY(check_fit_args(idx, Tq, nt, K, nprobe, target_recall, label1_cap));
+    if (delta_d != 8 && delta_d != 16 && delta_d != 32) return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32");
+    const int S = (int)ceil_div(idx->Dpad, delta_d);
+    std::vector<float> m1f((size_t)std::max(1, S - 1), 0.f), btf((size_t)std::max(1, S - 1), -INFINITY);
+    if (S <= 1) return install_table_public(idx, delta_d, S, m1f.data(), btf.data());
+    Samples sm;
+    DADE_TRY(replay_samples(idx, Tq, nt, K, nprobe, delta_d, seed, label1_cap, DADE_EST_LEARNED, S - 1, &sm));
     std::vector<double> m1d((size_t)S - 1), btd((size_t)S - 1);
-    DADE_TRY(fit_tables(P.data(), T.data(), L.data(), n, S, target_recall, 100, m1d.data(), btd.data()));
+    DADE_TRY(fit_tables(sm.P.data(), sm.T.data(), sm.L.data(), sm.n, S, target_recall, 100, m1d.data(), btd.data()));
     for (int s = 0; s < S - 1; ++s) {
         m1f[(size_t)s] = (float)m1d[(size_t)s];
         btf[(size_t)s] = (float)btd[(size_t)s];
@@ -154,5 +178,31 @@ extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int
     DADE_TRY(install_table_public(idx, delta_d, S, m1f.data(), btf.data()));
     if (m1_out) std::copy(m1f.begin(), m1f.begin() + (S - 1), m1_out);
     if (beta_out) std::copy(btf.begin(), btf.begin() + (S - 1), beta_out);
+    return DADE_OK;
+}
+
+extern "C" dade_status dade_pq_fit_correction(dade_index* idx, const float* Tq, int64_t nt, int32_t K, int32_t nprobe,
+                                              double target_recall, uint64_t seed, int64_t label1_cap, float* out3) {
+    clear_error();
+    DADE_TRY(check_fit_args(idx, Tq, nt, K, nprobe, target_recall, label1_cap));
+    if (idx->pq_m <= 0) return fail(DADE_ESTATE, "the index has no product quantiser");
+    Samples sm;
+    DADE_TRY(replay_samples(idx, Tq, nt, K, nprobe, 16, seed, label1_cap, DADE_EST_PQ, 2, &sm));
+    std::vector<double> dis((size_t)sm.n), err((size_t)sm.n);
+    for (int64_t i = 0; i < sm.n; ++i) {
+        dis[(size_t)i] = sm.P[(size_t)i * 2];
+        err[(size_t)i] = sm.P[(size_t)i * 2 + 1];
+    }
+    double th[3];
+    DADE_TRY(fit_pq_host(dis.data(), err.data(), sm.T.data(), sm.L.data(), sm.n, target_recall, 100, th));
+    idx->pq_m1 = (float)th[0];
+    idx->pq_m3 = (float)th[1];
+    idx->pq_beta = (float)th[2];
+    idx->pq_has_table = true;
+    if (out3) {
+        out3[0] = idx->pq_m1;
+        out3[1] = idx->pq_m3;
+        out3[2] = idx->pq_beta;
+    }
     return DADE_OK;
 }

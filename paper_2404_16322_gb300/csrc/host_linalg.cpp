@@ -310,6 +310,129 @@ dade_status fit_tables(const double* partials, const double* tau, const int8_t* 
 }
 
 // ---------------------------------------------------------------------------
+// OPQ-L's classifier (Section V-B "Approximate Distances": the asymmetric
+// distance, the threshold and the quantisation error as features; one
+// classifier): full-batch Newton logistic regression on
+// (dis'/tau_bar, tau/tau_bar, e/sqrt(tau_bar)) with ridge 1e-8 on the
+// weights, step halving, <= 50 iterations, max|gradient| < 1e-10; then
+// m1 = -w1/w2, m3 = -w3 sqrt(tau_bar)/w2 (w2 < 0 required) and beta' the
+// largest value keeping label-0 recall >= target_recall.
+namespace {
+
+bool solve_n(int n, std::vector<double> M /* n x (n + 1) */, double* x) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(M[r * (n + 1) + c]) > fabs(M[piv * (n + 1) + c])) piv = r;
+        if (M[piv * (n + 1) + c] == 0) return false;
+        for (int j = 0; j <= n; ++j) std::swap(M[c * (n + 1) + j], M[piv * (n + 1) + j]);
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = M[r * (n + 1) + c] / M[c * (n + 1) + c];
+            for (int j = c; j <= n; ++j) M[r * (n + 1) + j] -= f * M[c * (n + 1) + j];
+        }
+    }
+    for (int i = 0; i < n; ++i) x[i] = M[i * (n + 1) + n] / M[i * (n + 1) + i];
+    return true;
+}
+
+// mean cross-entropy + ridge/2 |w|^2 of sigmoid(A theta), gradient and Hessian;
+// A is n x k (the last column the bias)
+void loss_grad_k(const std::vector<double>& A, const std::vector<double>& y, int k, const double* th, double ridge,
+                 double* loss, double* g, double* H) {
+    const int64_t n = (int64_t)y.size();
+    double L = 0;
+    std::vector<double> G((size_t)k, 0.0), HH((size_t)k * k, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const double* a = &A[(size_t)i * k];
+        double z = 0;
+        for (int u = 0; u < k; ++u) z += a[u] * th[u];
+        L += (z > 0 ? z + log1p(exp(-z)) : log1p(exp(z))) - y[i] * z;
+        const double p = z >= 0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z));
+        const double r = p - y[i], w = p * (1 - p);
+        for (int u = 0; u < k; ++u) {
+            G[u] += r * a[u];
+            for (int v = 0; v < k; ++v) HH[u * k + v] += w * a[u] * a[v];
+        }
+    }
+    const double inv = 1.0 / (double)n;
+    double reg = 0;
+    for (int u = 0; u + 1 < k; ++u) reg += th[u] * th[u];
+    *loss = L * inv + 0.5 * ridge * reg;
+    for (int u = 0; u < k; ++u) g[u] = G[u] * inv + (u + 1 < k ? ridge * th[u] : 0.0);
+    for (int u = 0; u < k * k; ++u) H[u] = HH[u] * inv;
+    for (int u = 0; u + 1 < k; ++u) H[u * k + u] += ridge;
+}
+
+}  // namespace
+
+dade_status fit_pq_host(const double* dis, const double* err, const double* tau, const int8_t* label, int64_t n,
+                        double target_recall, int32_t min_label0, double* out3) {
+    out3[0] = 0.0;
+    out3[1] = 0.0;
+    out3[2] = -INFINITY;
+    int64_t n0 = 0, n1 = 0;
+    double tsum = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        (label[i] == 0 ? n0 : n1)++;
+        tsum += tau[i];
+    }
+    if (n0 < min_label0 || n1 == 0) return DADE_OK;
+    const double tb = tsum / (double)n, sq = sqrt(tb);
+    constexpr int k = 4;
+    std::vector<double> A((size_t)n * k), y((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        A[(size_t)i * k + 0] = dis[i] / tb;
+        A[(size_t)i * k + 1] = tau[i] / tb;
+        A[(size_t)i * k + 2] = err[i] / sq;
+        A[(size_t)i * k + 3] = 1.0;
+        y[(size_t)i] = label[i] ? 1.0 : 0.0;
+    }
+    const double ridge = 1e-8, tol = 1e-10;
+    double th[k] = {0, 0, 0, 0}, loss, g[k], H[k * k];
+    loss_grad_k(A, y, k, th, ridge, &loss, g, H);
+    auto gmax = [](const double* v) {
+        double m = 0;
+        for (int u = 0; u < k; ++u) m = std::max(m, fabs(v[u]));
+        return m;
+    };
+    for (int it = 0; it < 50 && gmax(g) >= tol; ++it) {
+        std::vector<double> M((size_t)k * (k + 1));
+        for (int i = 0; i < k; ++i) {
+            for (int j = 0; j < k; ++j) M[i * (k + 1) + j] = H[i * k + j];
+            M[i * (k + 1) + k] = g[i];
+        }
+        double step[k];
+        if (!solve_n(k, M, step)) break;
+        double t = 1.0, cand[k], l2, g2[k], H2[k * k];
+        while (true) {
+            for (int u = 0; u < k; ++u) cand[u] = th[u] - t * step[u];
+            loss_grad_k(A, y, k, cand, ridge, &l2, g2, H2);
+            if (l2 <= loss || gmax(g2) < gmax(g) || t < 1e-10) break;
+            t *= 0.5;
+        }
+        memcpy(th, cand, sizeof cand);
+        loss = l2;
+        memcpy(g, g2, sizeof g2);
+        memcpy(H, H2, sizeof H2);
+    }
+    const double w1 = th[0], w2 = th[1], w3 = th[2];
+    if (!(w2 < 0)) return DADE_OK;
+    const double m1 = -w1 / w2, m3 = -w3 * sq / w2;
+    std::vector<double> v;
+    v.reserve((size_t)n0);
+    for (int64_t i = 0; i < n; ++i)
+        if (label[i] == 0) v.push_back(tau[i] - m1 * dis[i] - m3 * err[i]);
+    std::sort(v.begin(), v.end());
+    int64_t f = (int64_t)floor((1.0 - target_recall) * (double)v.size());
+    if (f > (int64_t)v.size() - 1) f = (int64_t)v.size() - 1;
+    out3[0] = m1;
+    out3[1] = m3;
+    out3[2] = v[(size_t)f];
+    return DADE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Haar-random rotation (the random projection of ADS, Section III "Distance
 // Estimation"): a D x D standard Gaussian matrix (Box-Muller on counter-based
 // SplitMix64 uniforms of (seed, index)), its Householder QR in FP64

@@ -398,6 +398,18 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
                 unsigned long long row = atomicAdd(ca.n_rows, 1ull);
                 if ((int64_t)row >= ca.row_cap) continue;
                 const int64_t pos = (int64_t)un.t * kT + c;
+                if (ca.pq_m > 0) {
+                    // OPQ-L rows: the asymmetric distance and the quantisation error
+                    const int64_t slot = slot_l + pos;
+                    const float* t = ca.pq_lut + (int64_t)q * ca.pq_m * 256;
+                    float dis = 0.f;
+                    for (int j = 0; j < ca.pq_m; ++j) dis += t[j * 256 + ca.pq_codes[(int64_t)j * ix.total_slots + slot]];
+                    ca.partials[(int64_t)row * 2] = dis;
+                    ca.partials[(int64_t)row * 2 + 1] = ca.pq_err[slot];
+                    ca.tau[row] = tau;
+                    ca.label[row] = lab1 ? 1 : 0;
+                    continue;
+                }
                 const E* xs = reinterpret_cast<const E*>(ix.slab) + ebase + pos * kBlock;
                 float p = 0.f;
                 for (int k = 0; k + 1 < S; ++k) {

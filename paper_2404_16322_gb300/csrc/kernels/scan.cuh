@@ -64,6 +64,20 @@ cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStre
 cudaError_t launch_wave_scan(const IndexView& ix, const WaveView& wv, int w, bool full,
                              int delta_d, const float* m1, const float* beta, int S,
                              cudaStream_t st);
+// OPQ-L: the product-quantisation codes of every slot (subspace-major), the
+// quantisation errors, the per-query tables and the learned test.
+struct PQView {
+    const uint8_t* codes;     // m x total_slots
+    const float* err;         // total_slots
+    const float* lut;         // B x m x 256
+    int64_t total_slots;
+    int32_t m;
+    float m1, m3, beta;       // prune iff m1 dis' + m3 e + beta > tau
+};
+// The wave scan of OPQ-L (scan_pq.cu): one test on the asymmetric distance,
+// then the exact distance.
+cudaError_t launch_pq_scan(const IndexView& ix, const WaveView& wv, int w, const PQView& pv, cudaStream_t st);
+
 // The RES variants of launch_wave_scan (scan_res.cu), and the per-query RES
 // terms res_q[b][s] = sum_{i >= d_s} q'_i^2 - m 2 sqrt(sum_{i >= d_s} q'_i^2 var_i),
 // d_s = min((s + 1) delta_d, D), for s < S - 1.

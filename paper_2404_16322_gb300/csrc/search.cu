@@ -40,6 +40,7 @@ struct Carve {
 
 struct Plan {
     WaveView wv{};
+    float* pq_lut = nullptr;   // B x m x 256 (OPQ-L)
     float* scores = nullptr;
     float* qnorm = nullptr;
     char* zero_begin = nullptr;
@@ -109,6 +110,7 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     v.top_id = c.take<int64_t>((size_t)B * Kmax);
     v.tau = c.take<float>((size_t)B);
     v.res_q = v.res_stride > 0 ? c.take<float>((size_t)B * v.res_stride) : nullptr;
+    pl->pq_lut = o.estimator == DADE_EST_PQ ? c.take<float>((size_t)B * idx->pq_m * 256) : nullptr;
     // zero-initialised block
     c.off = (size_t)round_up((int64_t)c.off, 256);
     size_t z0 = c.off;
@@ -133,13 +135,21 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
     if (o.mode != DADE_SCAN_PRUNE && o.mode != DADE_SCAN_FULL) return fail(DADE_EINVAL, "bad mode");
     if (o.first_wave < 0) return fail(DADE_EINVAL, "first_wave < 0");
     if (o.wave_growth_log2 < 0 || o.wave_growth_log2 > 30) return fail(DADE_EINVAL, "wave_growth_log2 must be in [0, 30]");
-    if (o.estimator != DADE_EST_LEARNED && o.estimator != DADE_EST_RES) return fail(DADE_EINVAL, "bad estimator");
+    if (o.estimator != DADE_EST_LEARNED && o.estimator != DADE_EST_RES && o.estimator != DADE_EST_PQ)
+        return fail(DADE_EINVAL, "bad estimator");
+    if (o.estimator == DADE_EST_PQ) {
+        if (idx->pq_m <= 0) return fail(DADE_ESTATE, "the index has no product quantiser (dade_pq_train / dade_pq_set)");
+        if (o.mode == DADE_SCAN_PRUNE && !idx->pq_has_table)
+            return fail(DADE_ESTATE, "no OPQ-L correction (dade_pq_fit_correction / dade_pq_set_correction)");
+        if (o.mode == DADE_SCAN_PRUNE && (o.final_test || o.test_steps))
+            return fail(DADE_ENOTIMPL, "OPQ-L has one test: no final_test or test_steps");
+    }
     if (o.test_steps < 0) return fail(DADE_EINVAL, "test_steps < 0");
     if (o.test_steps > 0 && o.final_test && o.mode == DADE_SCAN_PRUNE)
         return fail(DADE_ENOTIMPL, "test_steps with final_test");
     if (o.estimator == DADE_EST_RES && !(o.res_m >= 0.f && o.res_m < INFINITY))
         return fail(DADE_EINVAL, "res_m must be finite and >= 0");
-    if (o.mode == DADE_SCAN_PRUNE) {
+    if (o.mode == DADE_SCAN_PRUNE && o.estimator != DADE_EST_PQ) {
         if (delta_d != 8 && delta_d != 16 && delta_d != 32)
             return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32 (got %d)", delta_d);
         int S = (int)ceil_div(idx->Dpad, delta_d);
@@ -206,9 +216,11 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     ix.dtype = idx->dtype;
 
     const bool full = o.mode == DADE_SCAN_FULL;
-    const int S = (int)ceil_div(idx->Dpad, delta_d > 0 ? delta_d : idx->Dpad);
+    const bool pq = o.estimator == DADE_EST_PQ;
+    // OPQ-L has one test whatever delta_d is (S = 2: one test, then the exact distance)
+    const int S = pq ? 2 : (int)ceil_div(idx->Dpad, delta_d > 0 ? delta_d : idx->Dpad);
     const float *m1 = nullptr, *beta = nullptr;
-    if (!full && S > 1 && !v.est) {
+    if (!full && S > 1 && !v.est && !pq) {
         const CorrectionTable& tb = idx->tables.at(delta_d);
         m1 = tb.m1_dev;
         beta = tb.beta_dev;
@@ -224,6 +236,9 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     DADE_CUDA_TRY(launch_tc_dot(Q, idx->D, idx->mean_dev.as<float>(), idx->R_dev.as<float>(), idx->Dpad,
                                 const_cast<float*>(v.qrot), idx->Dpad, B, idx->Dpad, idx->D, v.status, st));
     DADE_CUDA_TRY(launch_prepare_queries(Q, B, idx->D, idx->Dpad, const_cast<float*>(v.qpad), st));
+    if (pq)
+        DADE_CUDA_TRY(launch_pq_lut(v.qrot, B, idx->Dpad, idx->pq_perm_dev.as<int32_t>(), idx->pq_cb_dev.as<float>(),
+                                    idx->pq_m, idx->pq_ds, pl.pq_lut, st));
     if (v.est)
         DADE_CUDA_TRY(launch_res_terms(v.qrot, B, idx->D, idx->Dpad, idx->var_dev.as<float>(), delta_d, S, o.res_m,
                                        const_cast<float*>(v.res_q), st));
@@ -251,7 +266,16 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     DADE_CUDA_TRY(launch_build_units(ix, v, st));
     // 4-5. waves
     for (int w = 0; w < v.n_waves; ++w) {
-        if (collect) DADE_CUDA_TRY(launch_collect(ix, v, w, delta_d, S, *collect, collect->query_offset, st));
+        if (collect) {
+            CollectArgs ca = *collect;
+            if (pq) {
+                ca.pq_m = idx->pq_m;
+                ca.pq_codes = idx->pq_codes_dev.as<uint8_t>();
+                ca.pq_err = idx->pq_err_dev.as<float>();
+                ca.pq_lut = pl.pq_lut;
+            }
+            DADE_CUDA_TRY(launch_collect(ix, v, w, delta_d, S, ca, collect->query_offset, st));
+        }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (timed) {
             DADE_CUDA_TRY(cudaEventCreate(&e0));
@@ -261,7 +285,13 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
         // wave 0 has tau = +inf for every query (no frozen tau): every
         // candidate's exact distance, through the full-scan kernel
         const bool exact_wave = full || S <= 1 || (w == 0 && o.tau_dev == nullptr);
-        DADE_CUDA_TRY(launch_wave_scan(ix, v, w, exact_wave, delta_d, m1, beta, S, st));
+        if (pq && !exact_wave) {
+            PQView pv{idx->pq_codes_dev.as<uint8_t>(), idx->pq_err_dev.as<float>(), pl.pq_lut, idx->total_slots,
+                      idx->pq_m, idx->pq_m1, idx->pq_m3, idx->pq_beta};
+            DADE_CUDA_TRY(launch_pq_scan(ix, v, w, pv, st));
+        } else {
+            DADE_CUDA_TRY(launch_wave_scan(ix, v, w, exact_wave, delta_d, m1, beta, S, st));
+        }
         if (timed) {
             DADE_CUDA_TRY(cudaEventRecord(e1, st));
             std::lock_guard<std::mutex> lk(tm.mu);

@@ -141,3 +141,23 @@ def test_library_ads_table_reproduces_the_oracle_ads_test(lib, tiny):
         assert ads[2][:, 1].sum() > 0
     with pytest.raises(Exception):
         lib.dade_ads_table(128, 16, -1.0)
+
+
+def test_library_pq_fit_matches_oracle_on_the_same_samples(lib):
+    # OPQ-L's three-feature classifier: the library's host FP64 fit and the
+    # oracle's on identical samples (a boundary that needs the error feature)
+    from oracle import fit
+    rng = np.random.default_rng(8)
+    n = 5000
+    tau = rng.uniform(1.0, 2.0, n)
+    dis = rng.uniform(0.0, 4.0, n)
+    err = rng.uniform(0.0, 1.0, n)
+    noise = rng.normal(0.0, 0.2, n)
+    lab = (dis - 1.5 * err + noise > tau).astype(np.int8)
+    m1o, m3o, bo, info = fit.fit_pq_correction(dis, err, tau, lab, r=0.995)
+    m1l, m3l, bl = lib.dade_pq_fit_samples(dis, err, tau, lab, target_recall=0.995)
+    assert info["enabled"]
+    assert abs(m1l - m1o) <= 1e-6 * abs(m1o) and abs(m3l - m3o) <= 1e-6 * abs(m3o)
+    assert abs(bl - bo) <= 1e-6 * max(1.0, abs(bo))
+    # too few label-0 samples: disabled
+    assert lib.dade_pq_fit_samples(dis[:50], err[:50], tau[:50], np.ones(50, np.int8))[2] == -np.inf
