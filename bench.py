@@ -276,20 +276,23 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------- main arm
-def compare_estimators(G, X, Q, gt, idx, mean, R, nlist, K, slabs, maxp, nps, steps, warmup):
+def compare_estimators(G, X, Q, T, gt, idx, mean, R, nlist, K, slabs, maxp, nps, steps, warmup):
     """The other estimators of the paper on the same data and buckets, each
     autotuned to the same recall target and timed like the main line:
       res: the Gaussian-bound test of Section IV-C on the PCA index, m = 8
            (the paper's multiplier for SIFT- and GIST-like data);
       ads: ADS (Section III) -- a Haar-random rotation of the same buckets
            (centroids mapped through the rotations) and the scaled test with
-           eps0 = 2.1, Delta_d = 32 (the paper's ADS setting)."""
+           eps0 = 2.1, Delta_d = 32 (the paper's ADS setting);
+      opq: OPQ-L (Section V-B) -- m = D/4 subspaces (D/8 for D = 960, the
+           paper's settings) of 256 centroids on the same index, the
+           three-feature classifier fitted on the training queries."""
     from paper_2404_16322_gb300 import autotune
     D = X.shape[1]
     esz = {"f32": 4, "bf16": 2, "fp8": 1}[slabs]
     out = {}
 
-    def measure(run, best):
+    def measure(run, best, per_candidate_bytes=0, exact_reads_slab=True):
         total, per = run.time(best["nprobe"], best["delta_d"], "prune", steps, warmup,
                               first_wave=best["first_wave"], growth=best["growth"], final_test=best["final_test"])
         run.run(best["nprobe"], best["delta_d"], "prune", stats=True, first_wave=best["first_wave"],
@@ -301,7 +304,8 @@ def compare_estimators(G, X, Q, gt, idx, mean, R, nlist, K, slabs, maxp, nps, st
                 "delta_d": best["delta_d"], "first_wave": best["first_wave"], "wave_growth_log2": best["growth"],
                 "final_test": best["final_test"], "recall@10": best["recall"],
                 "scanned_dims_ratio": float(st[:, 3].sum() / (st[:, 0].sum() * D)),
-                "bytes_per_query": float((pruned_dims * esz + st[:, 2] * (D * esz + D * 4)).sum() / run.B)}
+                "bytes_per_query": float((pruned_dims * esz + st[:, 2] * (D * esz * exact_reads_slab + D * 4)
+                                          + st[:, 0] * per_candidate_bytes).sum() / run.B)}
 
     run = autotune.Bench(G, idx, Q, K, maxp, DELTAS, estimator="res", res_m=8.0)
     best, _ = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, nprobes=nps, mode="prune")
@@ -319,6 +323,19 @@ def compare_estimators(G, X, Q, gt, idx, mean, R, nlist, K, slabs, maxp, nps, st
     out["ads"] = dict(measure(run, best), eps0=2.1)
     del run
     ads_idx.close()
+
+    m = D // 8 if D == 960 else D // 4
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(7)
+    sample = X[np.sort(rng.choice(len(X), min(len(X), 65536 if D <= 256 else 32768), replace=False))]
+    G.dade_pq_train(idx, sample, m, iters=10, seed=1)
+    G.dade_pq_fit_correction(idx, T, K, min(64, nlist), target_recall=0.995, seed=1)
+    train_s = time.perf_counter() - t0
+    run = autotune.Bench(G, idx, Q, K, maxp, (16,), estimator="pq")
+    best, _ = autotune.autotune(run, gt, TARGET_RECALL, 10, (16,), nprobes=nps, mode="prune")
+    out["opq"] = dict(measure(run, best, per_candidate_bytes=m, exact_reads_slab=False), m=m,
+                      train_and_fit_s=train_s)
+    del run
     return out
 
 
@@ -490,13 +507,14 @@ def main():
 
     estimators = None
     if not args.no_estimators:
-        estimators = compare_estimators(G, X, Q, gt, idx, mean, R, nlist, K, slabs, maxp, nps, args.steps,
+        estimators = compare_estimators(G, X, Q, T, gt, idx, mean, R, nlist, K, slabs, maxp, nps, args.steps,
                                         args.warmup)
         estimators["learned"] = {"value": value / world, "unit": "queries/s", "nprobe": bd["nprobe"],
                                  "delta_d": bd["delta_d"], "recall@10": bd["recall"], "scanned_dims_ratio": scan_ratio,
                                  "bytes_per_query": dade_bytes}
         estimators["speedup_learned_vs_ads"] = value / world / estimators["ads"]["value"]
         estimators["speedup_learned_vs_res"] = value / world / estimators["res"]["value"]
+        estimators["speedup_learned_vs_opq"] = value / world / estimators["opq"]["value"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -127,8 +127,9 @@ def autotune(bench: Bench, gt: np.ndarray, target: float = 0.95, k_recall: int =
                     break
     ok = [t for t in tried if t["recall"] >= target]
     best = min(ok, key=lambda t: t["ms"]) if ok else max(tried, key=lambda t: t["recall"])
-    if mode == "prune":
+    if mode == "prune" and bench.estimator != "pq":
         # the test on the completed distance changes no result, only the time
+        # (OPQ-L has a single test and no such variant)
         b = best
         _, per = bench.time(b["nprobe"], b["delta_d"], mode, reps, warmup, b["first_wave"], growth=b["growth"],
                             final_test=True)
