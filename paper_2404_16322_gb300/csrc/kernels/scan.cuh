@@ -51,7 +51,7 @@ struct WaveView {
     int64_t* top_id;          // B x Kmax
     int32_t* top_n;           // B
     float* tau;               // B: the K-th distance (+inf while fewer than K)
-    int32_t* work;            // 2 x n_waves work counters (scan, collect)
+    int32_t* work;            // 2 x n_waves work counters (scan, collect), then an 8-byte counter
     int32_t* status;          // device status word
     int64_t* stats;           // B x 4 or null
     unsigned long long* staged_bytes;  // bytes staged by the scan, or null

@@ -11,11 +11,13 @@
 // subspace j holds rotated dims perm[j*ds .. (j+1)*ds), 256 centroids each.
 //
 // Kernels: encoding of every slot's stored vector (codes and e), the
-// per-query tables, and the wave scan.  The scan is query-major: a CTA
-// stages one query's table (m x 256 floats) in shared memory and walks the
-// candidates of its buckets in the wave, 128 at a time; codes are stored
-// subspace-major so that a chunk's code for one subspace is one coalesced
-// 128-byte read.
+// per-query tables, and the wave scan.  The scan is query-major: a work item
+// is (query, run of up to rpi consecutive probe ranks of the wave, rpi chosen
+// so that there are a few items per CTA); a
+// CTA stages the query's table (m x 256 floats) in shared memory and walks
+// the candidates of the item's buckets, kPqThreads at a time; codes are
+// stored subspace-major so that a chunk's code for one subspace is one
+// coalesced read.
 #include "scan_steps.cuh"
 
 namespace dade {
@@ -90,29 +92,34 @@ __global__ void pq_lut_kernel(const float* __restrict__ qrot, int64_t B, int32_t
     lut[id] = d;
 }
 
-// One CTA per query of the wave (persistent over the batch): its table in
-// shared memory, then every candidate of the buckets at its probe ranks of
-// wave w, 128 per chunk.
-__global__ void __launch_bounds__(kScanThreads) pq_scan_kernel(IndexView ix, WaveView wv, int w, PQView pv) {
+constexpr int kPqThreads = 256;
+
+// Persistent over the wave's work items (query b, probe ranks
+// [r0 + rpi c, r0 + rpi (c + 1)) clipped to the wave and nprobe).
+__global__ void __launch_bounds__(kPqThreads) pq_scan_kernel(IndexView ix, WaveView wv, int w, PQView pv, int rpi) {
     extern __shared__ __align__(16) float s_lut[];
     __shared__ unsigned long long s_st[4];
-    __shared__ int s_b;
+    __shared__ int64_t s_item;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nlut = pv.m * 256;
     const int r0 = w == 0 ? 0 : (int)min((int64_t)wv.first_wave << min(wv.wave_shift * (w - 1), 30), (int64_t)1 << 30);
     const int r1 = (int)min((int64_t)wv.first_wave << min(wv.wave_shift * w, 30), (int64_t)1 << 30);
+    const int nch = (min(r1, wv.P) - r0 + rpi - 1) / rpi;  // items per query in this wave
+    const int64_t n_items = nch > 0 ? wv.B * nch : 0;
     const bool want_stats = wv.stats != nullptr;
     for (;;) {
-        if (tid == 0) s_b = atomicAdd(&wv.work[w], 1);
+        if (tid == 0) s_item = atomicAdd((unsigned long long*)&wv.work[2 * wv.n_waves], 1ull);
         if (tid < 4) s_st[tid] = 0ull;
         __syncthreads();
-        const int64_t b = s_b;
-        if (b >= wv.B) break;
+        const int64_t item = s_item;
+        if (item >= n_items) break;
+        const int64_t b = item / nch;
+        const int ch = (int)(item % nch);
         const int np = wv.nprobe[b];
         const int K = wv.K[b];
-        const int rb = r0, re = min(r1, np);
+        const int rb = r0 + ch * rpi, re = min(min(rb + rpi, r1), np);
         if (K > 0 && np > 0 && rb < re) {
-            for (int i = tid; i < nlut; i += kScanThreads) s_lut[i] = pv.lut[b * nlut + i];
+            for (int i = tid; i < nlut; i += kPqThreads) s_lut[i] = pv.lut[b * nlut + i];
             __syncthreads();
             const float tau = wv.tau[b];
             const float* qp = wv.qpad + b * ix.Dpad;
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(kScanThreads) pq_scan_kernel(IndexView ix, Wav
                 const int64_t s0 = ix.list_slot[l];
                 const int64_t npad = ix.list_slot[l + 1] - s0;
                 const int n = ix.list_size[l];
-                for (int c0 = 0; c0 < n; c0 += kScanThreads) {
+                for (int c0 = 0; c0 < n; c0 += kPqThreads) {
                     const int c = c0 + tid;
                     const bool valid = c < n;
                     const int64_t slot = s0 + c;
@@ -185,10 +192,18 @@ cudaError_t launch_pq_scan(const IndexView& ix, const WaveView& wv, int w, const
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pq_scan_kernel, kScanThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pq_scan_kernel, kPqThreads, smem);
     if (e != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>((int64_t)sms * std::max(per, 1), std::max<int64_t>(wv.B, 1));
-    pq_scan_kernel<<<(unsigned)grid, kScanThreads, smem, st>>>(ix, wv, w, pv);
+    // the item counter (one 64-bit word after the 2 x n_waves scan and
+    // collect counters) starts at zero for every wave
+    e = cudaMemsetAsync(wv.work + 2 * wv.n_waves, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (int64_t)sms * std::max(per, 1);
+    const int r0 = wave_begin(w, wv.first_wave, wv.wave_shift);
+    const int nranks = std::max(0, std::min(wave_begin(w + 1, wv.first_wave, wv.wave_shift), (int)wv.P) - r0);
+    const int rpi = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(nranks, 1),
+                                                                ceil_div(wv.B * nranks, 4 * grid)));
+    pq_scan_kernel<<<(unsigned)grid, kPqThreads, smem, st>>>(ix, wv, w, pv, rpi);
     return cudaGetLastError();
 }
 

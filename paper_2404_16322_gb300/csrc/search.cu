@@ -119,7 +119,7 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     v.cand_off = c.take<int64_t>((size_t)nw * (B + 1));
     v.cand_cnt = c.take<int32_t>((size_t)B);
     v.top_n = c.take<int32_t>((size_t)B);
-    v.work = c.take<int32_t>((size_t)2 * nw);
+    v.work = c.take<int32_t>((size_t)2 * nw + 4);  // + one 8-byte item counter of the OPQ-L scan
     pl->status_internal = c.take<int32_t>(1);
     pl->zero_begin = base ? base + z0 : nullptr;
     pl->zero_bytes = c.off - z0;
