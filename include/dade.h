@@ -293,6 +293,9 @@ typedef struct {
  * dade_pq_fit_samples: that host FP64 fit alone on caller samples.
  * dade_pq_set_correction / dade_pq_get: install / read the classifier; read
  * m, and the codes (N x m, input-row order) and e (N) of the stored vectors.
+ * dade_index_save keeps the quantiser and its classifier (the codes are
+ * recomputed from the stored vectors at load); dade_index_shard does not
+ * carry them.
  * Errors: DADE_EINVAL, DADE_ESTATE (no quantiser), DADE_ENOMEM, DADE_ECUDA.
  * ---------------------------------------------------------------------- */
 dade_status dade_pq_train(dade_index* idx, const float* X_host, int64_t n, int32_t m, int32_t iters,

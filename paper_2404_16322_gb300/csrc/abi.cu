@@ -148,7 +148,7 @@ struct Reader {
 };
 
 const char kMagic[8] = {'D', 'A', 'D', 'E', 'I', 'D', 'X', '1'};
-const uint32_t kVersion = 3;
+const uint32_t kVersion = 4;
 
 }  // namespace
 
@@ -276,6 +276,18 @@ extern "C" dade_status dade_index_save(const dade_index* idx, const char* path) 
         w.put(kv.second.m1.data(), sizeof(float) * kv.second.m1.size());
         w.put(kv.second.beta.data(), sizeof(float) * kv.second.beta.size());
     }
+    // OPQ-L quantiser (the codes are recomputed from the slabs at load)
+    int32_t pm = idx->pq_m;
+    w.pod(pm);
+    if (pm > 0) {
+        w.put(idx->pq_perm.data(), sizeof(int32_t) * idx->pq_perm.size());
+        w.put(idx->pq_cb.data(), sizeof(float) * idx->pq_cb.size());
+        int32_t ht = idx->pq_has_table ? 1 : 0;
+        w.pod(ht);
+        w.pod(idx->pq_m1);
+        w.pod(idx->pq_m3);
+        w.pod(idx->pq_beta);
+    }
     uint64_t h = w.fnv.h;
     bool ok = w.ok && fwrite(&h, sizeof h, 1, f) == 1;
     ok = (fclose(f) == 0) && ok;
@@ -356,6 +368,20 @@ extern "C" dade_status dade_index_load(const char* path, dade_index** out) {
         r.get(beta.data(), sizeof(float) * (S - 1));
         DADE_TRY(install_table(idx.get(), dd, S, m1.data(), beta.data()));
     }
+    int32_t pm = 0, pq_ht = 0;
+    std::vector<int32_t> pq_perm;
+    std::vector<float> pq_cb;
+    float pq_c[3] = {0.f, 0.f, -INFINITY};
+    r.pod(pm);
+    if (!r.ok || pm < 0 || (pm > 0 && (D % pm != 0 || D / pm > 64))) return fail(DADE_EIO, "%s: bad quantiser", path);
+    if (pm > 0) {
+        pq_perm.resize((size_t)D);
+        pq_cb.resize((size_t)pm * 256 * (D / pm));
+        r.get(pq_perm.data(), sizeof(int32_t) * D);
+        r.get(pq_cb.data(), sizeof(float) * pq_cb.size());
+        r.pod(pq_ht);
+        for (float& c : pq_c) r.pod(c);
+    }
     uint64_t want = r.fnv.h, got = 0;
     if (!r.ok || fread(&got, sizeof got, 1, f) != 1 || got != want) return fail(DADE_EIO, "%s: checksum mismatch", path);
     // rotation, mean, centroids on the device
@@ -382,6 +408,10 @@ extern "C" dade_status dade_index_load(const char* path, dade_index** out) {
     DADE_TRY(idx->var_dev.alloc(sizeof(float) * Dp));
     DADE_CUDA_TRY(cudaMemcpy(idx->var_dev.p, idx->var.data(), sizeof(float) * Dp, cudaMemcpyHostToDevice));
     DADE_TRY(build_residual_norms(idx.get()));
+    if (pm > 0) {
+        DADE_TRY(dade_pq_set(idx.get(), pm, pq_perm.data(), pq_cb.data()));
+        if (pq_ht) DADE_TRY(dade_pq_set_correction(idx.get(), pq_c[0], pq_c[1], pq_c[2]));
+    }
     *out = idx.release();
     return DADE_OK;
 }

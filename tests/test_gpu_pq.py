@@ -133,3 +133,22 @@ def test_pq_host_errors(G, pre):
         G.dade_pq_set(pre["idx"], np.zeros(pre["X"].shape[1], np.int32), pre["cb"].astype(np.float32))
     with pytest.raises(_lib.DadeError):
         H.gpu_search(G, pre["idx"], pre["Q"][:4], 10, 8, 16, estimator="pq", final_test=True)
+
+
+def test_pq_survives_save_and_load(G, pre, tmp_path):
+    s = pre
+    G.dade_pq_set_correction(s["idx"], 1.0, -2.0, 0.0)
+    p = str(tmp_path / "pq.dade")
+    G.dade_index_save(s["idx"], p)
+    idx2 = G.dade_index_load(p)
+    try:
+        m, c3, codes, err = G.dade_pq_get(idx2, codes=True)
+        _, c3a, codes_a, err_a = G.dade_pq_get(s["idx"], codes=True)
+        assert m == M and c3 == c3a
+        assert np.array_equal(codes, codes_a) and np.array_equal(err, err_a)
+        pr = s["oidx"].probe(s["Q"], 8)
+        a = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, estimator="pq", want=("stats",))
+        b = H.gpu_search(G, idx2, s["Q"], 10, 8, 16, probe_in=pr, estimator="pq", want=("stats",))
+        assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["stats"], b["stats"])
+    finally:
+        idx2.close()
