@@ -6,12 +6,17 @@
   sizes the oracle finishes in seconds, with the oracle's rotation, buckets
   and tables on both sides (pre-rotated: strict id parity).
 * SIFT-shaped 1M x 128, 10k queries, nprobe 64, K 100, Delta_d 16, first
-  wave 4 -- the configuration bench.py times -- checked on sampled queries
-  through properties that hold at any size: returned distances are the exact
-  distances of the returned ids (integer data: bit-exact in FP32), results
-  are sorted and unique, the pruned search returns every candidate of the
-  full scan that beats the full scan's K-th, and recall@10 against brute
-  force on the sample."""
+  wave 8 and one later wave -- the configuration bench.py selects and times
+  -- checked on sampled queries through properties that hold at any size:
+  returned distances are the exact distances of the returned ids (integer
+  data: bit-exact in FP32), results are sorted and unique, every result of
+  the pruned search that beats the full scan's K-th is in the full scan's
+  result, and recall@10 against brute force on the sample.
+* GIST-shaped 1M x 960 with BF16 slabs, 1,000 queries, nprobe 128, first
+  wave 16 (the GIST-shaped bench configuration), and the 10M x 96 vMF-like
+  set with BF16 slabs and a batch of 512 requests with K in [1, 100] and
+  nprobe in [8, 256], checked the same way (distances within 1e-5 of
+  FP64)."""
 import numpy as np
 import pytest
 
@@ -90,8 +95,8 @@ def sift_full(G):
 
 def test_sift_full_size_in_the_benchmark_configuration(G, sift_full):
     X, Q, idx = sift_full["X"], sift_full["Q"], sift_full["idx"]
-    pr = H.gpu_search(G, idx, Q, 100, 64, 16, first_wave=4, want=("stats",))
-    fu = H.gpu_search(G, idx, Q, 100, 64, 0, mode="full", first_wave=4)
+    pr = H.gpu_search(G, idx, Q, 100, 64, 16, first_wave=8, growth=30, want=("stats",))
+    fu = H.gpu_search(G, idx, Q, 100, 64, 0, mode="full", first_wave=8, growth=30)
     assert pr["status"] == 0 and fu["status"] == 0
     sample = np.random.default_rng(5).choice(len(Q), 24, replace=False)
     Xd = X.astype(np.float64)
@@ -116,3 +121,77 @@ def test_sift_full_size_in_the_benchmark_configuration(G, sift_full):
     assert np.mean(hits) >= 0.9
     st = pr["stats"]
     assert st[:, 1].sum() > 0.5 * st[:, 0].sum()  # most candidates are pruned
+
+
+
+def _check_sampled(X, Q, pr, fu, K, sample, exact_bits=False):
+    """Properties of the pruned (pr) and full-scan (fu) results on sampled
+    queries; returns the brute-force recall@10 of the pruned search."""
+    hits = []
+    for b in sample:
+        k = int(K[b])
+        q = Q[b].astype(np.float64)
+        for out in (pr, fu):
+            ids, dd = out["ids"][b][:k], out["dists"][b][:k]
+            v = ids >= 0
+            assert len(set(ids[v].tolist())) == v.sum() and np.all(np.diff(dd[v]) >= 0)
+            assert np.all(out["ids"][b][k:] == -1)
+            ex = ((X[ids[v]].astype(np.float64) - q) ** 2).sum(1)
+            if exact_bits:
+                assert np.array_equal(dd[v].astype(np.float64), ex)
+            else:
+                assert np.all(np.abs(dd[v] - ex) <= 1e-5 * np.maximum(ex, 1e-3 * np.median(ex)))
+        kth = (fu["dists"][b][k - 1], fu["ids"][b][k - 1])
+        better_p = {i for i, x in zip(pr["ids"][b][:k], pr["dists"][b][:k]) if i >= 0 and (x, i) < kth}
+        assert better_p <= set(fu["ids"][b][:k].tolist())
+        if k >= 10:
+            dall = np.empty(len(X))
+            for c0 in range(0, len(X), 1 << 20):
+                xc = X[c0:c0 + (1 << 20)].astype(np.float64)
+                dall[c0:c0 + len(xc)] = ((xc - q) ** 2).sum(1)
+            gt = np.lexsort((np.arange(len(X)), dall))[:10]
+            hits.append(len(set(gt.tolist()) & set(pr["ids"][b][:10].tolist())) / 10)
+    return float(np.mean(hits)) if hits else 1.0
+
+
+def test_gist_full_size_in_the_benchmark_configuration(G):
+    X, Q, T, cfg = synth.workload("gist1m")
+    mean, R, _ = G.dade_train_rotation(X, sample_n=200_000, seed=1)
+    idx = G.ivf_build(X, mean, R, cfg["nlist"], kmeans_iters=10, seed=1, dtype="bf16")
+    try:
+        G.dade_fit_correction(idx, T, 100, 64, 16, target_recall=0.995, seed=1)
+        pr = H.gpu_search(G, idx, Q, 100, 128, 16, first_wave=16, growth=30, want=("stats",))
+        fu = H.gpu_search(G, idx, Q, 100, 128, 0, mode="full", first_wave=16, growth=30)
+        assert pr["status"] == 0 and fu["status"] == 0
+        sample = np.random.default_rng(6).choice(len(Q), 12, replace=False)
+        rec = _check_sampled(X, Q, pr, fu, np.full(len(Q), 100), sample)
+        assert rec >= 0.9
+        st = pr["stats"]
+        assert st[:, 3].sum() < 0.3 * st[:, 0].sum() * X.shape[1]   # well under a full scan's dims
+    finally:
+        idx.close()
+
+
+def test_vmf_10m_full_size_uneven_requests(G):
+    X, Q, T, cfg = synth.workload("vmf10m")
+    mean, R, _ = G.dade_train_rotation(X, sample_n=1_000_000, seed=1)
+    idx = G.ivf_build(X, mean, R, cfg["nlist"], kmeans_iters=10, seed=1, dtype="bf16")
+    try:
+        G.dade_fit_correction(idx, T, 100, 64, 16, target_recall=0.995, seed=1)
+        # one batch of 512 uneven requests (the candidate buffer of a batch
+        # grows with the batch times the largest buckets' sizes)
+        Qb = Q[:512]
+        rng = np.random.default_rng(10)
+        K = rng.integers(1, 101, len(Qb)).astype(np.int32)
+        npb = rng.integers(8, 257, len(Qb)).astype(np.int32)
+        pr = H.gpu_search(G, idx, Qb, K, npb, 16, max_K=100, max_nprobe=256, first_wave=8, growth=30,
+                          want=("stats",))
+        fu = H.gpu_search(G, idx, Qb, K, npb, 0, mode="full", max_K=100, max_nprobe=256, first_wave=8, growth=30)
+        assert pr["status"] == 0 and fu["status"] == 0
+        sample = np.random.default_rng(7).choice(len(Qb), 8, replace=False)
+        rec = _check_sampled(X, Qb, pr, fu, K, sample)
+        assert rec >= 0.8
+        st = pr["stats"]
+        assert st[:, 1].sum() > 0.3 * st[:, 0].sum()
+    finally:
+        idx.close()
