@@ -91,3 +91,37 @@ def test_two_ranks_gather_and_merge_equal_unsharded():
     # the two shards found disjoint candidates
     s0, s1 = set(ids_all[0][ids_all[0] >= 0].tolist()), set(ids_all[1][ids_all[1] >= 0].tolist())
     assert not (s0 & s1)
+
+
+def _failing_rank(rank, world, port, out):
+    # rank 1 fails before the exchange (a shard that cannot search); rank 0
+    # must see an error from the gather within the group's timeout, not hang
+    import datetime
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    from paper_2404_16322_gb300 import shard
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)
+    t0 = time.time()
+    try:
+        shard.gather_parts(torch.zeros((4, 10), dtype=torch.int64), torch.zeros((4, 10)))
+        out.put(("no error", time.time() - t0))
+    except Exception as e:  # the backend's error type differs across versions
+        out.put((type(e).__name__, time.time() - t0))
+
+
+def test_a_failed_rank_surfaces_as_an_error_on_the_others():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29700 + os.getpid() % 1000
+    ps = [ctx.Process(target=_failing_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    what, secs = q.get(timeout=120)
+    for p in ps:
+        p.join(timeout=60)
+    assert what != "no error"
+    assert secs < 60
+    assert ps[1].exitcode == 3
