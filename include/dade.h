@@ -254,7 +254,8 @@ typedef struct {
                              /* straight to the exact distance.                  */
     int32_t estimator;       /* PRUNE mode: dade_estimator (0: learned tables;  */
                              /* DADE_EST_PQ: OPQ-L, see dade_pq_train; it      */
-                             /* ignores delta_d, final_test and test_steps)    */
+                             /* ignores delta_d and refuses final_test and     */
+                             /* test_steps with DADE_ENOTIMPL)                 */
     float res_m;             /* DADE_EST_RES: the multiplier m of sigma, >= 0   */
                              /* (larger m prunes less; the paper's default 8)  */
     int32_t test_steps;      /* PRUNE mode: only the first test_steps steps are */
