@@ -9,11 +9,8 @@ import numpy as np
 from oracle import fit, ivf, pq, search
 
 
-def test_eigen_allocation_by_hand():
-    # variances 8, 4, 2, 1 into 2 subspaces of 2: round 1 deals 8 -> s0, 4 -> s1;
-    # round 2 deals 2 to the smaller product (s1: 4) and 1 to s0:
-    # s0 = {0, 3}, s1 = {1, 2}, products 8 and 8
-    assert list(pq.eigen_allocation(np.array([8.0, 4.0, 2.0, 1.0]), 2)) == [0, 3, 1, 2]
+def test_eigen_allocation_scale_free_and_balanced():
+    # the hand-worked example is tests/golden/opq_allocation_example.json;
     # a scale change of every variance changes nothing
     assert list(pq.eigen_allocation(np.array([8.0, 4.0, 2.0, 1.0]) * 1e-3, 2)) == [0, 3, 1, 2]
     # balance on a decaying spectrum: pairing the larger values of a round with

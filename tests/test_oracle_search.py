@@ -22,37 +22,6 @@ def _worked_index(order_b=(3, 2, 4)):
     return idx
 
 
-def test_worked_example_by_hand():
-    """Hand evaluation with m1 = 1.75, beta = 0 (prune iff 1.75 dis'_1 > tau),
-    then the test on the completed distance: prune iff dis'_2 > 1.001 tau
-    (FP64 storage: no quantisation error).
-
-    Probe order: list 0 = {0, 1}, then list 1 = {3, 2, 4}.
-    SEQUENTIAL: 0 -> dis 2 (tau inf); 1 -> dis 4, queue full, tau = 4;
-      3: 1.75 > 4? no; 3 > 4.004? no -> dis 3 enters, tau = 3;
-      2: 3.5 > 3 -> pruned; 4: 7 > 3 -> pruned.  Result (0, 2), (3, 3);
-      pruned 2, exact 3; dims 4 + 4 + 4 + 2 + 2 = 16.
-    WAVES (first wave 1): wave 0 = list 0 at tau inf -> 2, 4, tau = 4;
-      wave 1 at tau 4: 3 -> no, 3 <= 4.004 (dis 3); 2: 3.5 > 4? no, but
-      11 > 4.004 -> pruned at d = D; 4: 7 > 4 -> pruned.  Same result;
-      pruned 2, exact 3, dims 4 + 4 + 4 + 4 + 2 = 18.
-    FROZEN tau = 3.5: 0: 1.75 > 3.5? no, 2 <= 3.5035 -> 2; 1: 7 > 3.5
-      pruned; 3 -> 3; 2: 3.5 > 3.5? no, 11 > 3.5035 -> pruned at d = D;
-      4 pruned.  Result (0,2),(3,3); pruned 3, exact 2, dims 16.
-    """
-    idx = _worked_index()
-    Q = np.zeros((1, 4), dtype=np.float32)
-    probes = np.array([[0, 1]], dtype=np.int32)
-    m1, beta = np.array([1.75]), np.array([0.0])
-    for mode, tau, st_exp in [("sequential", None, [5, 2, 3, 16]), ("waves", None, [5, 2, 3, 18]),
-                              ("frozen", np.array([3.5]), [5, 3, 2, 16])]:
-        ids, d, st = search.search(idx, Q, probes, 2, 2, 2, m1, beta, mode=mode, tau=tau,
-                                   final_rel=search.FINAL_REL)
-        assert list(ids[0]) == [0, 3], mode
-        assert list(d[0]) == [2.0, 3.0], mode
-        assert list(st[0][:4]) == st_exp, mode
-
-
 def test_worked_example_ties_and_padding():
     # ids 1 and 4 are both at distance 4: with K = 3 and no pruning the third
     # entry is id 1 (lower id wins the tie); with K = 7 the tail is padded.
@@ -269,30 +238,6 @@ def test_final_test_never_changes_the_result(rotated, dtype):
                 assert b[2][:, 2].sum() < a[2][:, 2].sum()
 
 
-def test_res_worked_example_by_hand():
-    """RES (Section IV-C, Algorithm 2) on two vectors, D = 4, Delta_d = 2,
-    identity rotation, frozen tau = 2, query q = (1, 0, 1, 0).
-    sigma_i^2 over the two vectors (1/N): dims 0 and 2 have values {1, 3}
-    and {2, 0}: variance 1; dims 1 and 3: 0.
-    After dims [0, 2): sigma = 2 sqrt(q_2^2 * 1) = 2.
-      x0 = (1, 0, 2, 0): dis'_1 = 0, ||x_r||^2 = 4, ||q_r||^2 = 1 -> C1 - C2 = 5; dis = 1.
-      x1 = (3, 0, 0, 0): dis'_1 = 4, ||x_r||^2 = 0, ||q_r||^2 = 1 -> C1 - C2 = 5; dis = 5.
-    m = 1: 5 - 2 = 3 > 2: both pruned (x0 is lost: the bound fails at m = 1).
-    m = 2: 5 - 4 = 1 <= 2: both get exact distances; x0 (1) is kept, x1 (5) is not.
-    m = 1.4: 2.2 > 2: both pruned."""
-    X = np.array([[1, 0, 2, 0], [3, 0, 0, 0]], dtype=np.float32)
-    idx = search.OracleIndex(X, np.zeros(4), np.eye(4), np.zeros((1, 4)), np.zeros(2, np.int32), dtype="f64")
-    assert np.array_equal(idx.var, [1.0, 0.0, 1.0, 0.0])
-    Q = np.array([[1, 0, 1, 0]], dtype=np.float32)
-    pr = np.zeros((1, 1), np.int32)
-    for m, ids_exp, st_exp in [(1.0, [-1, -1], [2, 2, 0, 4]), (2.0, [0, -1], [2, 0, 2, 8]),
-                               (1.4, [-1, -1], [2, 2, 0, 4])]:
-        ids, d, st = search.search(idx, Q, pr, 1, 2, 2, None, None, mode="frozen", tau=np.array([2.0]),
-                                   estimator="res", res_m=m)
-        assert list(ids[0]) == ids_exp, m
-        assert list(st[0][:4]) == st_exp, m
-
-
 def test_res_estimate_is_exact_for_a_query_at_the_origin(small):
     # q = 0: ||q_r||^2 = 0 and sigma = 0, so C1 - C2 = ||x||^2 = dis at every
     # step and RES prunes exactly the candidates with dis > tau: the results
@@ -335,29 +280,6 @@ def test_res_loss_rate_follows_the_gaussian_error_model(m):
     want = 1 - 0.5 * (1 + erf(m / sqrt(2)))
     got = lost / len(Q)
     assert abs(got - want) < 4 * sqrt(want * (1 - want) / len(Q)) + 0.01, (got, want)
-
-
-def test_ads_worked_example_by_hand():
-    """ADS (Section III: dis' = (D/d) dis'_s over a random rotation, pruned iff
-    dis' > (1 + eps) tau, eps = eps0 / sqrt(d)) on two vectors, D = 4,
-    Delta_d = 2, identity rotation, frozen tau = 3, q = (1, 0, 1, 0).
-    After dims [0, 2) (d = 2): x0 = (1, 0, 2, 0): dis'_1 = 0, dis' = 0, dis = 1;
-    x1 = (3, 0, 0, 0): dis'_1 = 4, dis' = 8, dis = 5.
-      eps0 = 0:         8 > 3: x1 pruned; x0 kept.
-      eps0 = sqrt(2):   eps = 1, (1 + eps) tau = 6 < 8: x1 pruned.
-      eps0 = 2 sqrt(2): eps = 2, 9 >= 8: x1 gets its exact distance (5 > 3: dropped).
-    A dropped D/d factor (dis' = 4) would keep x1 at eps0 = sqrt(2); eps0 / d in
-    place of eps0 / sqrt(d) (eps = sqrt(2), 7.24 < 8) would prune it at 2 sqrt(2)."""
-    X = np.array([[1, 0, 2, 0], [3, 0, 0, 0]], dtype=np.float32)
-    idx = search.OracleIndex(X, np.zeros(4), np.eye(4), np.zeros((1, 4)), np.zeros(2, np.int32), dtype="f64")
-    Q = np.array([[1, 0, 1, 0]], dtype=np.float32)
-    pr = np.zeros((1, 1), np.int32)
-    for e0, st_exp in [(0.0, [2, 1, 1, 6]), (np.sqrt(2), [2, 1, 1, 6]), (2 * np.sqrt(2), [2, 0, 2, 8])]:
-        ids, d, st = search.search(idx, Q, pr, 1, 2, 2, None, None, mode="frozen", tau=np.array([3.0]),
-                                   estimator="ads", ads_eps0=e0)
-        assert list(ids[0]) == [0, -1], e0
-        assert d[0, 0] == 1.0
-        assert list(st[0][:4]) == st_exp, e0
 
 
 def test_ads_estimate_is_unbiased_over_random_rotations():
