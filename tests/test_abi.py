@@ -161,3 +161,26 @@ def test_library_pq_fit_matches_oracle_on_the_same_samples(lib):
     assert abs(bl - bo) <= 1e-6 * max(1.0, abs(bo))
     # too few label-0 samples: disabled
     assert lib.dade_pq_fit_samples(dis[:50], err[:50], tau[:50], np.ones(50, np.int8))[2] == -np.inf
+
+
+def test_library_random_rotation_sizes(lib):
+    for D in (1, 2, 7, 960):
+        R = lib.dade_random_rotation(D, seed=11)
+        assert R.shape == (D, D)
+        assert np.abs(R @ R.T - np.eye(D)).max() < 1e-11
+    with pytest.raises(Exception):
+        lib.dade_random_rotation(0)
+
+
+def test_library_ads_table_edges(lib):
+    # D not a multiple of delta_d: the last tested step covers min(s dd, D)
+    m1, beta = lib.dade_ads_table(100, 32, 2.1)
+    assert m1.shape == (3,) and np.all(beta == 0)
+    d = np.array([32, 64, 96], dtype=np.float64)
+    assert np.allclose(m1, (100 / d) / (1 + 2.1 / np.sqrt(d)), rtol=1e-6)
+    # one step only: no test
+    m1, beta = lib.dade_ads_table(16, 32, 2.1)
+    assert m1.shape == (0,)
+    # eps0 = 0: the plain scaled estimate against tau
+    m1, _ = lib.dade_ads_table(64, 16, 0.0)
+    assert np.allclose(m1, [4.0, 2.0, 4.0 / 3.0], rtol=1e-6)

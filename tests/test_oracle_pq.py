@@ -116,3 +116,35 @@ def test_three_feature_fit_keeps_label0_recall_and_uses_the_error():
     assert m3 < 0 and abs(m3 / m1 + 1.5) < 0.5
     pruned1 = (m1 * dis[lab == 1] + m3 * err[lab == 1] + bp > tau[lab == 1]).mean()
     assert pruned1 > 0.8
+
+
+def test_encode_breaks_ties_to_the_lower_centroid():
+    # two identical centroids in a subspace: the lower index wins every tie
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((50, 4))
+    perm = np.arange(4)
+    cb = rng.standard_normal((2, pq.KSUB, 2))
+    cb[0, 7] = cb[0, 200] = [0.0, 0.0]        # a duplicate pair in subspace 0
+    X[:, :2] = 0.0                             # every row is nearest to it
+    codes = pq.encode(X, perm, cb)
+    assert np.all(codes[:, 0] == 7)
+
+
+def test_opq_rows_follow_the_classifier_on_every_stored_precision():
+    # the single test reads the codes and errors it is given, whatever the
+    # slab precision of the index (the estimate is the table, not the slab)
+    X, perm, cb = _small(seed=8, n=1500)
+    D = X.shape[1]
+    rng = np.random.default_rng(3)
+    C, a, _ = ivf.kmeans(X.astype(np.float64), rng.choice(len(X), 6, replace=False), 3)
+    Q = (rng.standard_normal((5, D)) * np.linspace(2.0, 0.3, D)).astype(np.float32)
+    out = []
+    for dt in ("f32", "bf16"):
+        idx = search.OracleIndex(X, np.zeros(D), np.eye(D), C, a, dtype=dt)
+        codes = pq.encode(X.astype(np.float64), perm, cb)
+        err = pq.quantisation_error(X.astype(np.float64), codes, perm, cb)
+        T = pq.lut(idx.rotate_queries(Q), perm, cb)
+        pr = idx.probe(idx.rotate_queries(Q), 3)
+        out.append(search.search(idx, Q, pr, 3, 10, 16, None, None, estimator="pq",
+                                 pq=dict(codes=codes, err=err, lut=T, m1=1.0, m3=-1.0, beta=0.0)))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
