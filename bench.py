@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-estimators", action="store_true",
                     help="skip the RES and ADS comparison lines")
-    ap.add_argument("--cpu-sample-queries", type=int, default=400)
+    ap.add_argument("--cpu-sample-queries", type=int, default=1000)
     ap.add_argument("--workload", default="sift1m", choices=sorted(WORKLOAD_INFO),
                     help="sift1m (the benchmark line) or gist1m")
     ap.add_argument("--slabs", default=None, choices=["f32", "bf16", "fp8"],
@@ -205,70 +205,116 @@ def peaks():
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_baseline(cfg_full, nprobe, delta_d, K, n_queries, steps=1, first_wave=1, growth=1, final_test=False,
-                    name="sift1m", dtype="f32"):
-    """The oracle (plain FP64 C loop, all host threads) on a bounded sample of
-    the workload: a 100k-vector instance of the same mixture with the same
-    bucket size (nlist 410, ~244 vectors per bucket), the same nprobe, K and
-    Delta_d, its own PCA, k-means (2 Lloyd iterations) and fitted tables."""
-    import synth
-    from oracle import fit, ivf, pca, search
-    spec = synth.WORKLOADS[name]["spec"]
-    N = 100_000
-    nlist = max(1, round(N / (cfg_full["N"] / cfg_full["nlist"])))
-    X = spec.sample(N, synth.mixtures.SEED_DATA)
-    Q = spec.sample(n_queries * max(1, steps), synth.mixtures.SEED_QUERIES)
-    T = spec.sample(200, synth.mixtures.SEED_TRAIN)
-    mu, R, _ = pca.train_rotation(X)
-    Xr = pca.rotate(X, mu, R)
-    init = np.random.default_rng(1).choice(N, nlist, replace=False)
-    C, a, _ = ivf.kmeans(Xr, init, 2)
-    oidx = search.OracleIndex(X, mu, R, C, a, dtype=dtype)
-    S = search.n_steps(oidx.D, delta_d)
-    prt = oidx.probe(oidx.rotate_queries(T), nprobe)
-    rows = search.collect(oidx, T, prt, nprobe, K, delta_d)
-    top, _, _ = search.search(oidx, T, prt, nprobe, K, delta_d, *search.disabled_tables(S))
-    P, tau, lab = fit.label_rows(rows, top, cap=200_000)
-    m1, beta, _ = fit.fit_correction(P, tau, lab, oidx.D, delta_d, min_label0=20)
-    del rows, P
+def time_oracle(oidx, m1, beta, nprobe, delta_d, K, steps, first_wave, growth, final_test):
+    """Times the oracle (plain FP64 C loop, every host thread) on batches of
+    queries, probing included; returns (threads, seconds per batch)."""
+    from oracle import search
     threads = search.max_threads()
     search.set_threads(threads)
     times = []
-    for s in range(max(1, steps)):
-        q = Q[s * n_queries:(s + 1) * n_queries]
+    for q in steps:
         t0 = time.perf_counter()
         pr = oidx.probe(oidx.rotate_queries(q), nprobe)  # probing is part of the query
-        search.search(oidx, q, pr, nprobe, K, delta_d, m1, beta, first_wave=first_wave, growth=growth,
+        search.search(oidx, q, pr, nprobe, K, delta_d, np.asarray(m1, np.float64), np.asarray(beta, np.float64),
+                      first_wave=first_wave, growth=max(1, growth),
                       final_rel=search.FINAL_REL if final_test else np.inf)
         times.append(time.perf_counter() - t0)
-    qps = n_queries / float(np.median(times))
-    sample = (f"oracle FP64 C loop on {n_queries} queries per step against a {N}-vector {name}-shaped instance "
-              f"(nlist {nlist}, ~{N // nlist}/bucket like the full 1M/4096), nprobe {nprobe}, K {K}, "
-              f"delta_d {delta_d}, first wave {first_wave}, growth 2^{growth}; probing included")
-    return dict(value=qps, unit="queries/s", cores=threads, kind="oracle", sample=sample), times
+    return threads, times
+
+
+def oracle_on_library_index(G, idx, X, Q, mean, R, slabs, nprobe, delta_d, K, n_queries, first_wave, growth,
+                            final_test, name):
+    """The oracle on the same inputs as the GPU line: the library's index
+    (rotation, centroids, bucket assignment, fitted tables) over the same
+    rows, searched for the first n_queries of the same batch."""
+    from oracle import search
+    oidx = search.OracleIndex(X, mean, R, G.dade_index_centroids(idx).astype(np.float64),
+                              G.dade_index_assignment(idx), dtype=slabs)
+    m1, beta = G.dade_get_correction(idx, delta_d)
+    q = Q[:n_queries]
+    threads, times = time_oracle(oidx, m1, beta, nprobe, delta_d, K, [q], first_wave, growth, final_test)
+    del oidx
+    sample = (f"oracle FP64 C loop on the first {len(q)} of the {len(Q)} queries against the same "
+              f"{len(X)}-vector {name}-shaped index as the GPU line (the library's rotation, centroids, "
+              f"assignment and fitted tables; {slabs} slabs emulated), nprobe {nprobe}, K {K}, delta_d {delta_d}, "
+              f"first wave {first_wave}, growth 2^{max(1, growth)}; probing included")
+    return dict(value=len(q) / float(np.median(times)), unit="queries/s", cores=threads, kind="oracle",
+                sample=sample)
+
+
+def blas_kmeans(Xr, nlist, iters, seed, sample_n):
+    """Buckets for the reference arm's index, from the oracle-rotated rows:
+    Lloyd k-means on a seeded sample (norm-expansion distances by BLAS),
+    then every row to its nearest centroid (input preparation, not timed)."""
+    rng = np.random.default_rng(seed)
+    S = Xr[np.sort(rng.choice(len(Xr), min(sample_n, len(Xr)), replace=False))]
+    C = S[rng.choice(len(S), nlist, replace=False)].copy()
+
+    def nearest(A):
+        out = np.empty(len(A), np.int64)
+        cn = (C * C).sum(1)
+        for a in range(0, len(A), 65536):
+            blk = A[a:a + 65536]
+            out[a:a + len(blk)] = np.argmin(cn[None, :] - 2.0 * (blk @ C.T), axis=1)
+        return out
+
+    for _ in range(iters):
+        a = nearest(S)
+        cnt = np.bincount(a, minlength=nlist)
+        sums = np.zeros_like(C)
+        np.add.at(sums, a, S)
+        nz = cnt > 0
+        C[nz] = sums[nz] / cnt[nz, None]
+    return C, nearest(Xr).astype(np.int32)
 
 
 def reference_arm(args):
+    """The oracle as the reference arm: the same SIFT-shaped workload (the
+    1M rows, nlist 4096, nprobe 64, K 100, Delta_d 16, first wave 8 and one
+    later wave -- the GPU arm's tuned configuration), an index prepared on
+    the host (the oracle's FP64 PCA, buckets by a BLAS k-means, tables by
+    the oracle's replay and fit on 300 training queries), then steps of a
+    bounded sample of 1,000 queries each, timed."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import synth
-    cfg = dict(synth.WORKLOADS["sift1m"])
-    n_q = 40
+    from oracle import fit, pca, search
     t0 = time.perf_counter()
-    # the configuration the GPU arm's autotuner selects on this workload
-    # (nprobe 64, Delta_d 16, first wave 8, one later wave)
-    cb, times = oracle_baseline(cfg, 64, 16, 100, n_q, steps=args.steps + args.warmup, first_wave=8, growth=30)
+    X, Q, T, cfg = synth.workload("sift1m")
+    nlist, K, nprobe, dd, fw, gw = cfg["nlist"], cfg["K"], 64, 16, 8, 30
+    rng = np.random.default_rng(1)
+    mu, R, _ = pca.train_rotation(X[np.sort(rng.choice(len(X), 200_000, replace=False))])
+    Xr = pca.rotate(X, mu, R)
+    C, a = blas_kmeans(Xr, nlist, 4, 1, 200_000)
+    del Xr
+    oidx = search.OracleIndex(X, mu, R, C, a, dtype="f32")
+    Tq = T[:300]
+    prt = oidx.probe(oidx.rotate_queries(Tq), nprobe)
+    rows = search.collect(oidx, Tq, prt, nprobe, K, dd)
+    S = search.n_steps(oidx.D, dd)
+    top, _, _ = search.search(oidx, Tq, prt, nprobe, K, dd, *search.disabled_tables(S))
+    P, tau, lab = fit.label_rows(rows, top, cap=500_000)
+    m1, beta, _ = fit.fit_correction(P, tau, lab, oidx.D, dd)
+    del rows, P
+    n_q = 1000
+    nsteps = args.steps + args.warmup
+    batches = [Q[(s * n_q) % len(Q):(s * n_q) % len(Q) + n_q] for s in range(nsteps)]
+    threads, times = time_oracle(oidx, m1, beta, nprobe, dd, K, batches, fw, gw, False)
     wall = time.perf_counter() - t0
     timed = times[args.warmup:] or times
     ms = 1000.0 * float(np.mean(timed))
     value = n_q / (ms / 1000.0)
-    cb["value"] = value
+    sample = (f"oracle FP64 C loop, {n_q} queries per step of the 10,000-query batch, against the full "
+              f"{len(X)}-vector sift1m-shaped set (nlist {nlist}; the oracle's PCA, buckets by BLAS k-means on a "
+              f"200k sample, tables fitted by the oracle on 300 training queries), nprobe {nprobe}, K {K}, "
+              f"delta_d {dd}, first wave {fw}, growth 2^{gw}; probing included")
+    cb = dict(value=value, unit="queries/s", cores=threads, kind="oracle", sample=sample)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "sift1m-shaped sample (see cpu_baseline.sample)", "nprobe": 64, "K": 100,
-                       "delta_d": 16, "first_wave": 8, "wave_growth_log2": 30},
+            "config": {"workload": WORKLOAD_INFO["sift1m"]["desc"].format(N=len(X)) + f"; {n_q} queries per step",
+                       "nprobe": nprobe, "K": K, "delta_d": dd, "first_wave": fw, "wave_growth_log2": gw},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
@@ -518,10 +564,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = oracle_baseline(cfg, bd["nprobe"], bd["delta_d"], K,
-                                 args.cpu_sample_queries if D <= 256 else max(20, args.cpu_sample_queries // 10),
-                                 first_wave=bd["first_wave"], growth=max(1, bd["growth"]),
-                                 final_test=bd["final_test"], name=args.workload, dtype=slabs)
+        cpu = oracle_on_library_index(G, idx, X, Q, mean, R, slabs, bd["nprobe"], bd["delta_d"], K,
+                                      args.cpu_sample_queries if D <= 256 else max(20, args.cpu_sample_queries // 5),
+                                      bd["first_wave"], bd["growth"], bd["final_test"], args.workload)
 
     launches = 12 + 2 * n_waves(bd["nprobe"], bd["first_wave"], bd["growth"])
     line = {

@@ -102,7 +102,10 @@ dade_status dade_ads_table(int32_t D, int32_t delta_d, double eps0, float* m1_ou
 /* ------------------------------------------------------------------------
  * ivf_build -- rotate the database and build the IVF index (Section II-A).
  *
- * X_host: N x D FP32 rows; mean[D], R[D x D] FP64 from dade_train_rotation
+ * X: N x D FP32 rows in host memory or in device memory of the current
+ * device (told apart with cudaPointerGetAttributes; device rows are read in
+ * place, host rows are copied up once); mean[D], R[D x D] FP64 from
+ * dade_train_rotation
  * (or any orthogonal matrix).  The rows are rotated on the device,
  * x' = R (x - mean), clustered into nlist buckets by Lloyd k-means in the
  * rotated space (kmeans_iters iterations from a seeded sample of nlist
@@ -118,7 +121,8 @@ dade_status dade_ads_table(int32_t D, int32_t delta_d, double eps0, float* m1_ou
  * Inside a bucket, vectors keep increasing row order.  params->centroids
  * (nlist x D rotated-space FP32, host) replaces k-means when non-NULL;
  * params->assign (N bucket ids, host) also replaces the assignment.
- * Errors: DADE_EINVAL, DADE_ENOMEM, DADE_ECUDA.  *out is set only on success.
+ * Errors: DADE_EINVAL (also: X in another device's memory), DADE_ENOMEM,
+ * DADE_ECUDA.  *out is set only on success.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int32_t nlist;
@@ -130,7 +134,7 @@ typedef struct {
     const int64_t* ids;      /* optional, host, N                         */
 } dade_build_params;
 
-dade_status ivf_build(const float* X_host, int64_t N, int32_t D, const double* mean,
+dade_status ivf_build(const float* X, int64_t N, int32_t D, const double* mean,
                       const double* R, const dade_build_params* params, dade_index** out);
 
 /* ------------------------------------------------------------------------
@@ -156,6 +160,14 @@ dade_status ivf_build(const float* X_host, int64_t N, int32_t D, const double* m
  * label-0 samples or no label-1 sample are disabled.
  * Errors: DADE_EINVAL, DADE_ENOMEM, DADE_ECUDA.
  *
+ * dade_fit_collect returns the samples dade_fit_correction would fit on
+ * (same arguments, same replay, labels and thinning), for inspection: up
+ * to max_rows rows sorted by (query, id) into partials (n x (S-1) FP32:
+ * dis'_1..dis'_{S-1} at the stored precision), tau (n), label (n: 0 or 1),
+ * query (n: index into train_q_host) and id (n), all host, caller-owned;
+ * *n_rows receives the row count (also when it exceeds max_rows, which
+ * returns DADE_EINVAL so that the caller can retry with more room).
+ *
  * dade_fit_samples runs the host FP64 fit alone on caller samples:
  * partials (n x (S-1)), tau (n), label (n: 0 or 1); outputs S - 1 doubles.
  *
@@ -166,6 +178,11 @@ dade_status dade_fit_correction(dade_index* idx, const float* train_q_host, int6
                                 int32_t K, int32_t nprobe, int32_t delta_d,
                                 double target_recall, uint64_t seed, int64_t label1_cap,
                                 float* m1_out, float* beta_out);
+
+dade_status dade_fit_collect(dade_index* idx, const float* train_q_host, int64_t nt, int32_t K, int32_t nprobe,
+                             int32_t delta_d, uint64_t seed, int64_t label1_cap, int64_t max_rows, int64_t* n_rows,
+                             float* partials_host, float* tau_host, int8_t* label_host, int64_t* query_host,
+                             int64_t* id_host);
 
 dade_status dade_fit_samples(const double* partials, const double* tau, const int8_t* label,
                              int64_t n, int32_t D, int32_t delta_d, double target_recall,
@@ -216,7 +233,11 @@ dade_status dade_get_correction(const dade_index* idx, int32_t delta_d, float* m
  * off = out_offsets_dev (B + 1 int64 prefix of K) or, when it is NULL,
  * off_b = b * max_K.  Fewer than K results pad with id -1 and +inf.
  * The call is asynchronous: it enqueues work and returns.  It performs no
- * host synchronisation; with opts->workspace given it allocates nothing.
+ * host synchronisation.  With opts->workspace given it allocates nothing;
+ * without, it uses scratch that the index keeps per stream (allocated
+ * stream-ordered with cudaMallocAsync when a stream first needs more, kept
+ * until dade_index_free), so searches of one index on distinct streams may
+ * run concurrently, and a stream that has warmed up allocates no more.
  * Errors found on the host return at once (DADE_EINVAL, DADE_ESTATE when
  * delta_d has no table in PRUNE mode, DADE_ECUDA on a launch failure).
  * Errors found on the device (K or nprobe out of range, a timed-out wait)
@@ -338,7 +359,10 @@ dade_status dade_search(const dade_index* idx, const float* Q_dev, int64_t B,
  *    nprobe 64 fit on a 1M-vector index with 4096 buckets).
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) once for that device; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process, so do not use this entry point after a cudaDeviceReset of
+ *    that device.
+ *  - Invalid arguments return the same status and message as dade_search.
  *  - Every call uses the same array, which keeps the previous call's
  *    contents; each call clears what must start at zero.  Calls whose work
  *    overlaps on the GPU race on the array: serialise them (one stream, or
@@ -392,6 +416,13 @@ dade_status dade_merge_topk(int32_t n_parts, int64_t B, int32_t max_K, const int
  * nlist x D rotated-space centroids to the host; dade_index_assignment the
  * bucket of each input row (N int32, host); dade_index_list_sizes the
  * nlist bucket sizes (int64, host).
+ * dade_index_stored copies to the host the stored rotated vectors (the
+ * values the estimate reads: FP32 slabs as stored, BF16 widened, FP8 codes
+ * times their per-dimension scale; Section V-B's "Approximate Distances" at
+ * the storage precision) of the input rows [row0, row0 + nrows), row-major
+ * nrows x D FP32 in out_host (caller-owned).  For inspecting the
+ * quantisation; it allocates a temporary device buffer of nrows x D floats
+ * and synchronises.  Errors: DADE_EINVAL (range), DADE_ENOMEM, DADE_ECUDA.
  * dade_index_save writes a versioned binary file (header, rotation, mean,
  * centroids, buckets, slabs, original vectors, ids, quantisation error
  * norms (BF16 / FP8), correction tables, and an FNV-1a checksum);
@@ -413,6 +444,7 @@ dade_status dade_index_info_get(const dade_index* idx, dade_index_info* out);
 dade_status dade_index_centroids(const dade_index* idx, float* centroids_host);
 dade_status dade_index_assignment(const dade_index* idx, int32_t* assign_host);
 dade_status dade_index_list_sizes(const dade_index* idx, int64_t* sizes_host);
+dade_status dade_index_stored(const dade_index* idx, int64_t row0, int64_t nrows, float* out_host);
 dade_status dade_index_save(const dade_index* idx, const char* path);
 dade_status dade_index_load(const char* path, dade_index** out);
 void dade_index_free(dade_index* idx);

@@ -58,8 +58,9 @@ def sample_uniform(seed: int, query: np.ndarray, ids: np.ndarray) -> np.ndarray:
     return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
-def label_rows(rows: dict, topk_ids: np.ndarray, seed: int = 0, cap: int = 500_000):
-    """Label replay rows; returns (partials, tau, label) of the kept rows."""
+def label_rows(rows: dict, topk_ids: np.ndarray, seed: int = 0, cap: int = 500_000, keys: bool = False):
+    """Label replay rows; returns (partials, tau, label) of the kept rows
+    (with keys: also their query index and candidate id)."""
     tau, dis = rows["tau"], rows["dis"]
     finite = np.isfinite(tau)
     in_top = (np.asarray(topk_ids)[rows["query"]] == rows["id"][:, None]).any(axis=1)
@@ -70,6 +71,8 @@ def label_rows(rows: dict, topk_ids: np.ndarray, seed: int = 0, cap: int = 500_0
         u = sample_uniform(seed, rows["query"], rows["id"])
         lab1 &= u < cap / n1
     keep = lab0 | lab1
+    if keys:
+        return rows["partials"][keep], tau[keep], lab1[keep].astype(np.int8), rows["query"][keep], rows["id"][keep]
     return rows["partials"][keep], tau[keep], lab1[keep].astype(np.int8)
 
 

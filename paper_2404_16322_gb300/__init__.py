@@ -14,11 +14,11 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["dade_train_rotation", "dade_random_rotation", "dade_ads_table", "ivf_build", "dade_fit_correction", "dade_fit_samples",
+__all__ = ["dade_train_rotation", "dade_random_rotation", "dade_ads_table", "ivf_build", "dade_fit_correction", "dade_fit_collect", "dade_fit_samples",
            "dade_set_correction", "dade_get_correction", "dade_search", "dade_search_noalloc",
            "dade_search_workspace_size",
            "dade_index_info_get", "dade_index_centroids", "dade_index_assignment",
-           "dade_index_list_sizes", "dade_index_save", "dade_index_load", "dade_index_free",
+           "dade_index_list_sizes", "dade_index_stored", "dade_index_save", "dade_index_load", "dade_index_free",
            "dade_stage_timing", "dade_stage_timing_read", "dade_last_error", "Index", "library",
            "n_steps", "dade_shard_owners", "dade_index_shard", "dade_merge_topk", "dade_pq_train", "dade_pq_set",
            "dade_pq_fit_correction", "dade_pq_fit_samples", "dade_pq_set_correction", "dade_pq_get"]
@@ -116,7 +116,15 @@ def dade_ads_table(D: int, delta_d: int, eps0: float = 2.1):
 
 def ivf_build(X, mean, R, nlist: int, kmeans_iters: int = 10, seed: int = 0, dtype: str = "f32",
               centroids=None, assign=None, ids=None) -> Index:
-    X = _host(X, np.float32)
+    """X: (N, D) float32 rows, a NumPy array (host) or a contiguous CUDA
+    tensor on the current device (read in place)."""
+    if not isinstance(X, np.ndarray) and hasattr(X, "is_cuda") and X.is_cuda:
+        import torch
+        assert X.dtype == torch.float32 and X.is_contiguous() and X.dim() == 2
+        xp = X.data_ptr()
+    else:
+        X = _host(X, np.float32)
+        xp = X.ctypes.data
     N, D = X.shape
     mean = _host(mean, np.float64)
     R = _host(R, np.float64)
@@ -125,7 +133,7 @@ def ivf_build(X, mean, R, nlist: int, kmeans_iters: int = 10, seed: int = 0, dty
     i = None if ids is None else _host(ids, np.int64)
     p = L.BuildParams(int(nlist), int(kmeans_iters), int(seed), L.SLAB[dtype], _ptr(c), _ptr(a), _ptr(i))
     out = ctypes.c_void_p()
-    _check(library().ivf_build(X.ctypes.data, N, D, mean.ctypes.data, R.ctypes.data, ctypes.byref(p),
+    _check(library().ivf_build(xp, N, D, mean.ctypes.data, R.ctypes.data, ctypes.byref(p),
                                ctypes.byref(out)))
     return Index(out.value)
 
@@ -141,6 +149,26 @@ def dade_fit_correction(idx: Index, T, K: int, nprobe: int, delta_d: int, target
                                          int(delta_d), float(target_recall), int(seed), int(label1_cap),
                                          m1.ctypes.data, beta.ctypes.data))
     return m1[:S - 1], beta[:S - 1]
+
+
+def dade_fit_collect(idx: Index, T, K: int, nprobe: int, delta_d: int, seed: int = 0, label1_cap: int = 500_000,
+                     max_rows: int | None = None) -> dict:
+    """The samples dade_fit_correction fits on, sorted by (query, id):
+    dict(partials[n, S-1], tau[n], label[n], query[n], id[n])."""
+    T = _host(T, np.float32)
+    S = n_steps(dade_index_info_get(idx)["D"], delta_d)
+    cap = int(max_rows) if max_rows is not None else len(T) * int(K) + int(label1_cap) + 4096
+    n = ctypes.c_int64(0)
+    P = np.empty((cap, max(S - 1, 1)), np.float32)
+    tau = np.empty(cap, np.float32)
+    lab = np.empty(cap, np.int8)
+    qi = np.empty(cap, np.int64)
+    ii = np.empty(cap, np.int64)
+    _check(library().dade_fit_collect(idx.ptr, T.ctypes.data, len(T), int(K), int(nprobe), int(delta_d), int(seed),
+                                      int(label1_cap), cap, ctypes.byref(n), P.ctypes.data, tau.ctypes.data,
+                                      lab.ctypes.data, qi.ctypes.data, ii.ctypes.data))
+    m = n.value
+    return dict(partials=P[:m, :S - 1], tau=tau[:m], label=lab[:m], query=qi[:m], id=ii[:m])
 
 
 def dade_fit_samples(partials, tau, label, D: int, delta_d: int, target_recall: float = 0.995,
@@ -322,6 +350,16 @@ def dade_index_list_sizes(idx: Index):
     info = dade_index_info_get(idx)
     out = np.empty(info["nlist"], np.int64)
     _check(library().dade_index_list_sizes(idx.ptr, out.ctypes.data))
+    return out
+
+
+def dade_index_stored(idx: Index, row0: int = 0, nrows: int | None = None):
+    """Stored rotated vectors (slab precision, decoded to FP32) of input rows
+    [row0, row0 + nrows): (nrows, D) host array."""
+    info = dade_index_info_get(idx)
+    nrows = info["N"] - int(row0) if nrows is None else int(nrows)
+    out = np.empty((nrows, info["D"]), np.float32)
+    _check(library().dade_index_stored(idx.ptr, int(row0), nrows, out.ctypes.data))
     return out
 
 

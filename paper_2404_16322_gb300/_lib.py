@@ -56,6 +56,8 @@ SIGNATURES = {
                                  ctypes.POINTER(c_vp)]),
     "dade_fit_correction": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_f64, c_u64, c_i64,
                                            c_vp, c_vp]),
+    "dade_fit_collect": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_u64, c_i64, c_i64,
+                                        ctypes.POINTER(c_i64), c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dade_fit_samples": (ctypes.c_int, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_f64, c_i32, c_vp, c_vp]),
     "dade_set_correction": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),
     "dade_get_correction": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),
@@ -68,6 +70,7 @@ SIGNATURES = {
     "dade_index_centroids": (ctypes.c_int, [c_vp, c_vp]),
     "dade_index_assignment": (ctypes.c_int, [c_vp, c_vp]),
     "dade_index_list_sizes": (ctypes.c_int, [c_vp, c_vp]),
+    "dade_index_stored": (ctypes.c_int, [c_vp, c_i64, c_i64, c_vp]),
     "dade_index_save": (ctypes.c_int, [c_vp, c_cp]),
     "dade_index_load": (ctypes.c_int, [c_cp, ctypes.POINTER(c_vp)]),
     "dade_index_free": (None, [c_vp]),

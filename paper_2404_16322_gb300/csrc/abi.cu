@@ -208,6 +208,43 @@ extern "C" dade_status dade_index_list_sizes(const dade_index* idx, int64_t* out
     return DADE_OK;
 }
 
+extern "C" dade_status dade_index_stored(const dade_index* idx, int64_t row0, int64_t nrows, float* out) {
+    clear_error();
+    if (!idx || (!out && nrows > 0)) return fail(DADE_EINVAL, "null argument");
+    if (row0 < 0 || nrows < 0 || row0 > idx->N || nrows > idx->N - row0)
+        return fail(DADE_EINVAL, "rows [%lld, %lld) outside [0, %lld)", (long long)row0,
+                    (long long)(row0 + nrows), (long long)idx->N);
+    if (nrows == 0) return DADE_OK;
+    // slot of input row i: its bucket's first slot plus its rank among the
+    // bucket's earlier rows (rows are laid out in input order per bucket)
+    std::vector<int64_t> rank((size_t)idx->nlist, 0), base((size_t)nrows), npad((size_t)nrows);
+    for (int64_t i = 0; i < row0 + nrows; ++i) {
+        const int l = idx->assign[(size_t)i];
+        const int64_t k = rank[(size_t)l]++;
+        if (i < row0) continue;
+        const int64_t s0 = idx->list_slot[(size_t)l];
+        base[(size_t)(i - row0)] = s0 * idx->Dpad + k * kBlock;
+        npad[(size_t)(i - row0)] = idx->list_slot[(size_t)l + 1] - s0;
+    }
+    int cur = 0;
+    DADE_CUDA_TRY(cudaGetDevice(&cur));
+    DADE_CUDA_TRY(cudaSetDevice(idx->device));
+    struct Restore {
+        int d;
+        ~Restore() { cudaSetDevice(d); }
+    } restore{cur};
+    DevBuf b, n, o;
+    DADE_TRY(b.alloc(sizeof(int64_t) * nrows));
+    DADE_TRY(n.alloc(sizeof(int64_t) * nrows));
+    DADE_TRY(o.alloc(sizeof(float) * nrows * idx->D));
+    DADE_CUDA_TRY(cudaMemcpy(b.p, base.data(), sizeof(int64_t) * nrows, cudaMemcpyHostToDevice));
+    DADE_CUDA_TRY(cudaMemcpy(n.p, npad.data(), sizeof(int64_t) * nrows, cudaMemcpyHostToDevice));
+    DADE_CUDA_TRY(launch_stored_gather(idx->slab_dev.p, idx->dtype, idx->scale_dev.as<float>(), b.as<int64_t>(),
+                                       n.as<int64_t>(), nrows, idx->D, o.as<float>(), 0));
+    DADE_CUDA_TRY(cudaMemcpy(out, o.p, sizeof(float) * nrows * idx->D, cudaMemcpyDeviceToHost));
+    return DADE_OK;
+}
+
 extern "C" dade_status dade_set_correction(dade_index* idx, int32_t delta_d, const float* m1,
                                            const float* beta) {
     clear_error();

@@ -124,12 +124,28 @@ extern "C" dade_status ivf_build(const float* X, int64_t N, int32_t D, const dou
         DADE_CUDA_TRY(cudaMemcpy(idx->R_dev.p, Rf.data(), sizeof(float) * Rf.size(), cudaMemcpyHostToDevice));
         DADE_CUDA_TRY(cudaMemcpy(idx->mean_dev.p, mf.data(), sizeof(float) * mf.size(), cudaMemcpyHostToDevice));
     }
+    // X in device memory of this device is read in place; host rows are
+    // copied up (pageable or pinned)
+    bool x_on_device = false;
+    {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, X) == cudaSuccess &&
+            (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)) {
+            if (pa.device != idx->device)
+                return fail(DADE_EINVAL, "X is in the memory of device %d, the current device is %d", pa.device,
+                            idx->device);
+            x_on_device = true;
+        }
+        cudaGetLastError();
+    }
     DevBuf x_dev, xr_dev, amin;
-    DADE_TRY(x_dev.alloc(sizeof(float) * N * D));
+    if (!x_on_device) DADE_TRY(x_dev.alloc(sizeof(float) * N * D));
     DADE_TRY(xr_dev.alloc(sizeof(float) * N * Dp));
     DADE_TRY(amin.alloc(sizeof(unsigned long long) * N));
-    DADE_CUDA_TRY(cudaMemcpyAsync(x_dev.p, X, sizeof(float) * N * D, cudaMemcpyHostToDevice, st));
-    DADE_CUDA_TRY(launch_tc_dot(x_dev.as<float>(), D, idx->mean_dev.as<float>(), idx->R_dev.as<float>(), Dp,
+    if (!x_on_device)
+        DADE_CUDA_TRY(cudaMemcpyAsync(x_dev.p, X, sizeof(float) * N * D, cudaMemcpyHostToDevice, st));
+    const float* xd = x_on_device ? X : x_dev.as<float>();
+    DADE_CUDA_TRY(launch_tc_dot(xd, D, idx->mean_dev.as<float>(), idx->R_dev.as<float>(), Dp,
                                 xr_dev.as<float>(), Dp, N, Dp, D, nullptr, st));
 
     // centroids (rotated space)
@@ -202,7 +218,7 @@ extern "C" dade_status ivf_build(const float* X, int64_t N, int32_t D, const dou
                                       cudaMemcpyHostToDevice, st));
         LayoutArgs la;
         la.xrot = xr_dev.as<float>();
-        la.x = x_dev.as<float>();
+        la.x = xd;
         la.slot_row = srow.as<int32_t>();
         la.slot_list = slist.as<int32_t>();
         la.list_slot = idx->list_slot_dev.as<int64_t>();

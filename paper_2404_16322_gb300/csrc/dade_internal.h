@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -79,6 +81,40 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Scratch of the dade_search calls that pass no workspace: one buffer per
+// stream, so that searches of one index on different streams never share
+// or free each other's scratch.  A buffer grows stream-ordered (the old one
+// is released with cudaFreeAsync on the same stream, after the kernels that
+// use it), and a search holds its stream's lock while it enqueues.
+struct StreamWorkspaces {
+    struct Buf {
+        std::mutex mu;
+        void* p = nullptr;
+        size_t bytes = 0;
+    };
+    std::mutex mu;
+    std::map<cudaStream_t, std::unique_ptr<Buf>> by_stream;
+    Buf* of(cudaStream_t st) {
+        std::lock_guard<std::mutex> lk(mu);
+        std::unique_ptr<Buf>& b = by_stream[st];
+        if (!b) b.reset(new Buf);
+        return b.get();
+    }
+    // Release a stream's buffer, ordered after its queued work (before the
+    // caller destroys that stream).
+    void drop(cudaStream_t st) {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = by_stream.find(st);
+        if (it == by_stream.end()) return;
+        if (it->second->p) cudaFreeAsync(it->second->p, st);
+        by_stream.erase(it);
+    }
+    ~StreamWorkspaces() {
+        for (auto& kv : by_stream)
+            if (kv.second->p) cudaFree(kv.second->p);
+    }
+};
+
 }  // namespace dade
 
 struct dade_index {
@@ -120,9 +156,8 @@ struct dade_index {
     bool pq_has_table = false;
     float pq_m1 = 0.f, pq_m3 = 0.f, pq_beta = -INFINITY;
     std::map<int, dade::CorrectionTable> tables;  // by delta_d
-    // internal scratch used when the caller gives no workspace
-    mutable dade::DevBuf ws;
-    mutable dade::DevBuf status;
+    // internal scratch used when the caller gives no workspace, per stream
+    mutable dade::StreamWorkspaces ws;
 };
 
 namespace dade {
@@ -181,6 +216,8 @@ struct LayoutArgs {
 };
 cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st);
 cudaError_t launch_quant_error(const LayoutArgs& a, cudaStream_t st);
+cudaError_t launch_stored_gather(const void* slab, int dtype, const float* scale, const int64_t* base,
+                                 const int64_t* npad, int64_t nrows, int32_t D, float* out, cudaStream_t st);
 cudaError_t launch_dim_var(const float* xrot, int64_t N, int32_t Dpad, float* var, cudaStream_t st);
 cudaError_t launch_residual_norms(const void* slab, int dtype, const float* scale, const int64_t* list_slot,
                                   int nlist, int64_t total_slots, int32_t Dpad, float* sfx, cudaStream_t st);
@@ -203,6 +240,8 @@ dade_status search_impl(const dade_index* idx, const float* Q_dev, int64_t B,
                         const dade_search_opts& opts, int64_t* ids_dev, float* dists_dev,
                         const int64_t* out_offsets_dev, cudaStream_t st,
                         const struct CollectArgs* collect);
+// Host-side argument checks of dade_search (status and message as it returns them).
+dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& opts);
 size_t workspace_bytes(const dade_index* idx, int64_t B, int32_t delta_d,
                        const dade_search_opts& opts, const struct CollectArgs* collect);
 
@@ -233,6 +272,8 @@ struct CollectArgs {
     const float* pq_lut;
     float* tau;               // row_cap
     int8_t* label;            // row_cap
+    int64_t* query;           // row_cap or null: training-query index of each row
+    int64_t* id;              // row_cap or null: id of each row's candidate
 };
 
 }  // namespace dade

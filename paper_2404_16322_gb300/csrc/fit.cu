@@ -29,16 +29,22 @@ struct Samples {
     int64_t n = 0;
     std::vector<double> P, T;
     std::vector<int8_t> L;
+    std::vector<int64_t> Qi, Id;  // training query and candidate id of each row (if keys were asked for)
 };
 
 dade_status replay_samples(dade_index* idx, const float* Tq, int64_t nt, int32_t K, int32_t nprobe, int32_t delta_d,
-                           uint64_t seed, int64_t label1_cap, int32_t estimator, int ncols, Samples* out) {
+                           uint64_t seed, int64_t label1_cap, int32_t estimator, int ncols, Samples* out,
+                           bool keys = false) {
     cudaStream_t st;
     DADE_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     struct G {
+        dade_index* idx;
         cudaStream_t s;
-        ~G() { cudaStreamDestroy(s); }
-    } guard{st};
+        ~G() {
+            idx->ws.drop(s);  // the replays' scratch on this stream
+            cudaStreamDestroy(s);
+        }
+    } guard{idx, st};
 
     const int64_t Bc = std::min<int64_t>(nt, 4096);
     const int D = idx->D;
@@ -101,13 +107,19 @@ dade_status replay_samples(dade_index* idx, const float* Tq, int64_t nt, int32_t
     const double n1 = (double)counts[0];
     ca.keep_rate = n1 > (double)label1_cap ? (double)label1_cap / n1 : 1.0;
     ca.row_cap = nt * K + label1_cap + (int64_t)(6.0 * sqrt((double)label1_cap)) + 1024;
-    DevBuf rp, rt, rl;
+    DevBuf rp, rt, rl, rq, ri;
     DADE_TRY(rp.alloc(sizeof(float) * ca.row_cap * ncols));
     DADE_TRY(rt.alloc(sizeof(float) * ca.row_cap));
     DADE_TRY(rl.alloc(sizeof(int8_t) * ca.row_cap));
     ca.partials = rp.as<float>();
     ca.tau = rt.as<float>();
     ca.label = rl.as<int8_t>();
+    if (keys) {
+        DADE_TRY(rq.alloc(sizeof(int64_t) * ca.row_cap));
+        DADE_TRY(ri.alloc(sizeof(int64_t) * ca.row_cap));
+        ca.query = rq.as<int64_t>();
+        ca.id = ri.as<int64_t>();
+    }
     DADE_TRY(replay(1));   // (C) emit samples
     DADE_CUDA_TRY(cudaMemcpy(counts, cnt.p, sizeof counts, cudaMemcpyDeviceToHost));
     int32_t dev_status = 0;
@@ -119,6 +131,13 @@ dade_status replay_samples(dade_index* idx, const float* Tq, int64_t nt, int32_t
     DADE_CUDA_TRY(cudaMemcpy(pf.data(), rp.p, sizeof(float) * pf.size(), cudaMemcpyDeviceToHost));
     DADE_CUDA_TRY(cudaMemcpy(tf.data(), rt.p, sizeof(float) * tf.size(), cudaMemcpyDeviceToHost));
     DADE_CUDA_TRY(cudaMemcpy(lab.data(), rl.p, sizeof(int8_t) * lab.size(), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> qk, ik;
+    if (keys) {
+        qk.resize((size_t)n);
+        ik.resize((size_t)n);
+        DADE_CUDA_TRY(cudaMemcpy(qk.data(), rq.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost));
+        DADE_CUDA_TRY(cudaMemcpy(ik.data(), ri.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost));
+    }
     // rows arrive in atomic order: sort them so the fit is reproducible
     std::vector<int64_t> ord((size_t)n);
     std::iota(ord.begin(), ord.end(), 0);
@@ -135,11 +154,19 @@ dade_status replay_samples(dade_index* idx, const float* Tq, int64_t nt, int32_t
     out->P.assign((size_t)n * ncols, 0.0);
     out->T.assign((size_t)n, 0.0);
     out->L.assign((size_t)n, 0);
+    if (keys) {
+        out->Qi.assign((size_t)n, 0);
+        out->Id.assign((size_t)n, 0);
+    }
     for (int64_t i = 0; i < n; ++i) {
         int64_t o2 = ord[(size_t)i];
         for (int s = 0; s < ncols; ++s) out->P[(size_t)i * ncols + s] = pf[(size_t)o2 * ncols + s];
         out->T[(size_t)i] = tf[(size_t)o2];
         out->L[(size_t)i] = lab[(size_t)o2];
+        if (keys) {
+            out->Qi[(size_t)i] = qk[(size_t)o2];
+            out->Id[(size_t)i] = ik[(size_t)o2];
+        }
     }
     return DADE_OK;
 }
@@ -178,6 +205,42 @@ extern "C" dade_status dade_fit_correction(dade_index* idx, const float* Tq, int
     DADE_TRY(install_table_public(idx, delta_d, S, m1f.data(), btf.data()));
     if (m1_out) std::copy(m1f.begin(), m1f.begin() + (S - 1), m1_out);
     if (beta_out) std::copy(btf.begin(), btf.begin() + (S - 1), beta_out);
+    return DADE_OK;
+}
+
+extern "C" dade_status dade_fit_collect(dade_index* idx, const float* Tq, int64_t nt, int32_t K, int32_t nprobe,
+                                        int32_t delta_d, uint64_t seed, int64_t label1_cap, int64_t max_rows,
+                                        int64_t* n_rows, float* partials, float* tau, int8_t* label, int64_t* query,
+                                        int64_t* id) {
+    clear_error();
+    DADE_TRY(check_fit_args(idx, Tq, nt, K, nprobe, 0.5, label1_cap));
+    if (delta_d != 8 && delta_d != 16 && delta_d != 32) return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32");
+    if (!n_rows) return fail(DADE_EINVAL, "null n_rows");
+    const int S = (int)ceil_div(idx->Dpad, delta_d);
+    if (S <= 1) {
+        *n_rows = 0;
+        return DADE_OK;
+    }
+    Samples sm;
+    DADE_TRY(replay_samples(idx, Tq, nt, K, nprobe, delta_d, seed, label1_cap, DADE_EST_LEARNED, S - 1, &sm, true));
+    *n_rows = sm.n;
+    if (sm.n > max_rows) return fail(DADE_EINVAL, "the replay kept %lld rows; max_rows is %lld", (long long)sm.n,
+                                     (long long)max_rows);
+    if (sm.n > 0 && (!partials || !tau || !label || !query || !id)) return fail(DADE_EINVAL, "null output");
+    std::vector<int64_t> ord((size_t)sm.n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+        if (sm.Qi[(size_t)a] != sm.Qi[(size_t)b]) return sm.Qi[(size_t)a] < sm.Qi[(size_t)b];
+        return sm.Id[(size_t)a] < sm.Id[(size_t)b];
+    });
+    for (int64_t i = 0; i < sm.n; ++i) {
+        const size_t o2 = (size_t)ord[(size_t)i];
+        for (int s = 0; s < S - 1; ++s) partials[i * (S - 1) + s] = (float)sm.P[o2 * (S - 1) + s];
+        tau[i] = (float)sm.T[o2];
+        label[i] = sm.L[o2];
+        query[i] = sm.Qi[o2];
+        id[i] = sm.Id[o2];
+    }
     return DADE_OK;
 }
 

@@ -153,7 +153,36 @@ __global__ void scale_kernel(float* v, int32_t Dpad) {
     }
 }
 
+// Stored rotated values of a set of slots, decoded to FP32 (row r: slot
+// elements from base[r], blocks npad[r] * 8 apart).
+__global__ void stored_gather_kernel(const void* slab, int dtype, const float* scale, const int64_t* base,
+                                     const int64_t* npad, int64_t nrows, int32_t D, float* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows * D) return;
+    const int64_t r = i / D;
+    const int d = (int)(i % D);
+    const int64_t e = base[r] + ((int64_t)(d / kBlock) * npad[r]) * kBlock + d % kBlock;
+    float v;
+    if (dtype == DADE_SLAB_F32) {
+        v = static_cast<const float*>(slab)[e];
+    } else if (dtype == DADE_SLAB_BF16) {
+        v = __bfloat162float(static_cast<const __nv_bfloat16*>(slab)[e]);
+    } else {
+        const __nv_fp8_storage_t c = static_cast<const __nv_fp8_storage_t*>(slab)[e];
+        v = __half2float(__half(__nv_cvt_fp8_to_halfraw(c, __NV_E4M3))) * scale[d];
+    }
+    out[i] = v;
+}
+
 }  // namespace
+
+cudaError_t launch_stored_gather(const void* slab, int dtype, const float* scale, const int64_t* base,
+                                 const int64_t* npad, int64_t nrows, int32_t D, float* out, cudaStream_t st) {
+    const int64_t n = nrows * D;
+    if (n == 0) return cudaSuccess;
+    stored_gather_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(slab, dtype, scale, base, npad, nrows, D, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st) {
     int64_t n = a.total_slots * (a.Dpad / kBlock);

@@ -398,6 +398,8 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
                 unsigned long long row = atomicAdd(ca.n_rows, 1ull);
                 if ((int64_t)row >= ca.row_cap) continue;
                 const int64_t pos = (int64_t)un.t * kT + c;
+                if (ca.query) ca.query[row] = qoff + q;
+                if (ca.id) ca.id[row] = id;
                 if (ca.pq_m > 0) {
                     // OPQ-L rows: the asymmetric distance and the quantisation error
                     const int64_t slot = slot_l + pos;

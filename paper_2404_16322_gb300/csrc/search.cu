@@ -126,6 +126,8 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     return c.off + 256;
 }
 
+}  // namespace
+
 dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o) {
     if (!idx) return fail(DADE_EINVAL, "null index");
     if (B < 0 || B > (int64_t)1 << 24) return fail(DADE_EINVAL, "B out of range: %lld", (long long)B);
@@ -159,8 +161,6 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
     return DADE_OK;
 }
 
-}  // namespace
-
 size_t workspace_bytes(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o,
                        const CollectArgs*) {
     Plan pl;
@@ -177,16 +177,28 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     Plan pl;
     size_t need = carve(idx, B, delta_d, o, nullptr, &pl);
     char* base;
+    std::unique_lock<std::mutex> ws_lock;
     if (o.workspace) {
         if (o.workspace_bytes < need)
             return fail(DADE_EINVAL, "workspace too small: %zu < %zu bytes", o.workspace_bytes, need);
         base = static_cast<char*>(o.workspace);
     } else {
-        if (idx->ws.bytes < need) {
-            idx->ws.release();
-            DADE_TRY(idx->ws.alloc(need));
+        // this stream's own scratch, held until every launch is enqueued
+        StreamWorkspaces::Buf* wb = idx->ws.of(st);
+        ws_lock = std::unique_lock<std::mutex>(wb->mu);
+        if (wb->bytes < need) {
+            if (wb->p) DADE_CUDA_TRY(cudaFreeAsync(wb->p, st));
+            wb->p = nullptr;
+            wb->bytes = 0;
+            cudaError_t e = cudaMallocAsync(&wb->p, need, st);
+            if (e != cudaSuccess) {
+                wb->p = nullptr;
+                cudaGetLastError();
+                return fail(DADE_ENOMEM, "cudaMallocAsync(%zu) failed: %s", need, cudaGetErrorString(e));
+            }
+            wb->bytes = need;
         }
-        base = idx->ws.as<char>();
+        base = static_cast<char*>(wb->p);
     }
     base = reinterpret_cast<char*>(round_up(reinterpret_cast<int64_t>(base), 256));
     carve(idx, B, delta_d, o, base, &pl);

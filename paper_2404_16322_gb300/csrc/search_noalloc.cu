@@ -19,8 +19,10 @@ namespace {
 constexpr size_t kNoAllocBytes = size_t(64) << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of the array, looked up once per device.  In host code the
-// array's name is only a host-side stand-in, never a device address.
+// Device address of the array, looked up once per device and kept for the
+// life of the process (so not valid across a cudaDeviceReset of that
+// device).  In host code the array's name is only a host-side stand-in,
+// never a device address.
 std::mutex g_mu;
 std::map<int, void*> g_addr;
 
@@ -49,10 +51,9 @@ extern "C" dade_status dade_search_noalloc(const dade_index* idx, const float* Q
     if (!opts) return dade::fail(DADE_EINVAL, "opts is required (max_K, max_nprobe)");
     if (opts->workspace)
         return dade::fail(DADE_EINVAL, "dade_search_noalloc uses its own fixed scratch; opts->workspace must be NULL");
-    if (!idx) return dade::fail(DADE_EINVAL, "null index");
     dade_search_opts o = *opts;
-    const size_t need = dade_search_workspace_size(idx, B, delta_d, &o);
-    if (need == 0 && B > 0) return dade::fail(DADE_EINVAL, "invalid search arguments");
+    DADE_TRY(dade::check_args(idx, B, delta_d, o));  // the same status and message as dade_search
+    const size_t need = dade::workspace_bytes(idx, B, delta_d, o, nullptr);
     if (need > kNoAllocBytes)
         return dade::fail(DADE_EINVAL,
                           "this search needs %zu bytes of scratch but dade_search_noalloc holds %zu; "

@@ -7,13 +7,16 @@
   and tables on both sides (pre-rotated: strict id parity).
 * SIFT-shaped 1M x 128, 10k queries, nprobe 64, K 100, Delta_d 16, first
   wave 8 and one later wave -- the configuration bench.py selects and times
-  -- checked on sampled queries through properties that hold at any size:
+  -- against the oracle on 1,000 queries (the oracle given the library's
+  rotation, centroids, assignment and tables), and on sampled queries
+  through properties that hold at any size:
   returned distances are the exact distances of the returned ids (integer
   data: bit-exact in FP32), results are sorted and unique, every result of
   the pruned search that beats the full scan's K-th is in the full scan's
   result, and recall@10 against brute force on the sample.
 * GIST-shaped 1M x 960 with BF16 slabs, 1,000 queries, nprobe 128, first
-  wave 16 (the GIST-shaped bench configuration), and the 10M x 96 vMF-like
+  wave 16 (the GIST-shaped bench configuration) against the oracle in the
+  same way, and the 10M x 96 vMF-like
   set with BF16 slabs and a batch of 512 requests with K in [1, 100] and
   nprobe in [8, 256], checked the same way (distances within 1e-5 of
   FP64)."""
@@ -41,9 +44,9 @@ def _oracle_search(inp, Q, K, nprobe, delta_d, amb="exact", final_rel=np.inf):
     oidx = inp["oidx"]
     P = int(np.max(nprobe))
     pr = oidx.probe(oidx.rotate_queries(Q), P)
-    ids, d, st = search.search(oidx, Q, pr, nprobe, K, delta_d, inp["m1"].astype(np.float64),
-                               inp["beta"].astype(np.float64), amb=H.AMB[amb], final_rel=final_rel)
-    return ids, d, st, pr
+    ids, d, st, ad = search.search(oidx, Q, pr, nprobe, K, delta_d, inp["m1"].astype(np.float64),
+                                   inp["beta"].astype(np.float64), amb=H.AMB[amb], final_rel=final_rel, with_amb=True)
+    return ids, d, st, pr, ad
 
 
 def test_gist_shaped_bf16_slabs(G):
@@ -54,9 +57,9 @@ def test_gist_shaped_bf16_slabs(G):
     idx = H.build_gpu(G, None, inp, 64, dtype="bf16", delta_d=32)
     Qr = inp["rot"](Q)
     for final in (False, True):
-        ids, d, st, pr = _oracle_search(inp, Qr, 100, 8, 32, final_rel=search.FINAL_REL if final else np.inf)
+        ids, d, st, pr, ad = _oracle_search(inp, Qr, 100, 8, 32, final_rel=search.FINAL_REL if final else np.inf)
         out = H.gpu_search(G, idx, Qr, 100, 8, 32, probe_in=pr, final_test=final, want=("stats",))
-        parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, 100, amb=st[:, 4], min_strict=0.9)
+        parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, 100, amb_d=ad)
         un = st[:, 4] == 0
         assert np.array_equal(out["stats"][un], st[un, :4])
         assert st[:, 1].sum() > 0
@@ -74,10 +77,10 @@ def test_vmf_shaped_fp8_slabs_uneven_requests(G):
     K = rng.integers(1, 101, len(Q)).astype(np.int32)
     npb = rng.integers(8, 17, len(Q)).astype(np.int32)
     for final in (False, True):
-        ids, d, st, pr = _oracle_search(inp, Qr, K, npb, 16, final_rel=search.FINAL_REL if final else np.inf)
+        ids, d, st, pr, ad = _oracle_search(inp, Qr, K, npb, 16, final_rel=search.FINAL_REL if final else np.inf)
         out = H.gpu_search(G, idx, Qr, K, npb, 16, probe_in=pr, max_K=100, max_nprobe=16, final_test=final,
                            want=("stats",))
-        parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, K, amb=st[:, 4], min_strict=0.9)
+        parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, K, amb_d=ad)
         un = st[:, 4] == 0
         assert np.array_equal(out["stats"][un], st[un, :4])
     idx.close()
@@ -89,8 +92,75 @@ def sift_full(G):
     mean, R, _ = G.dade_train_rotation(X, sample_n=1_000_000, seed=1)
     idx = G.ivf_build(X, mean, R, cfg["nlist"], kmeans_iters=10, seed=1, dtype="f32")
     G.dade_fit_correction(idx, T, 100, 64, 16, target_recall=0.995, seed=1)
-    yield dict(X=X, Q=Q, idx=idx)
+    yield dict(X=X, Q=Q, idx=idx, mean=mean, R=R)
     idx.close()
+
+
+def _library_oracle(G, idx, X, mean, R, dtype):
+    """An oracle index on the library's instance: its rotation (mean, R),
+    centroids and bucket assignment.  The oracle rotates, stores, estimates,
+    tests and merges on its own in FP64; its rounding model allows the
+    device's rotation to stray by H.FLIP_EPS * ||x'|| per coordinate."""
+    C = G.dade_index_centroids(idx).astype(np.float64)
+    a = G.dade_index_assignment(idx)
+    return search.OracleIndex(X, mean, R, C, a, dtype=dtype, flip_eps=H.FLIP_EPS)
+
+
+def _rotation_within_model(G, idx, oidx, qrot, Q, rows):
+    """The device's rotated queries and (FP32 slabs) stored vectors stray
+    from the FP64 rotation by less than the oracle's model assumes."""
+    qr = oidx.rotate_queries(Q)
+    q_err = np.abs(qrot - qr).max(axis=1) / np.linalg.norm(qr, axis=1)
+    assert q_err.max() < H.FLIP_EPS, q_err.max()
+    if oidx.dtype == "f32":
+        xs = G.dade_index_stored(idx, rows.start, len(rows)).astype(np.float64)
+        xr = oidx.Xs[rows]
+        dev = np.abs(xs - xr)
+        assert np.all(dev <= oidx.Xdev[rows]), (dev / oidx.Xdev[rows]).max()
+    return float(q_err.max())
+
+
+def _probes_within_near_ties(oidx, Q, probes, P):
+    """The device's probe lists equal the FP64 ones except where centroid
+    distances tie within 1e-5; returns the fraction of identical lists."""
+    Qr = oidx.rotate_queries(Q)
+    own = oidx.probe(Qr, P)
+    same = np.all(own == probes, axis=1)
+    for b in np.flatnonzero(~same):
+        d = ((oidx.C - Qr[b]) ** 2).sum(1)
+        kth = d[own[b, P - 1]]
+        for l in set(own[b].tolist()) ^ set(probes[b].tolist()):
+            assert abs(d[l] - kth) <= 1e-5 * kth, (b, l)
+    return float(same.mean())
+
+
+def test_sift_full_size_matches_the_oracle(G, sift_full):
+    """The benchmarked configuration (1M x 128 integer data, nlist 4096,
+    nprobe 64, K 100, Delta_d 16, first wave 8 then one wave) against the
+    oracle on 1,000 queries of the 10,000-query batch, given the library's
+    rotation, centroids, assignment and fitted tables.  Exact distances are
+    integers (exact in FP32), so ids are compared at every rank below each
+    query's first uncertain candidate, ties included, and distances bit for
+    bit; work counters agree wherever no candidate is uncertain."""
+    X, Q, idx = sift_full["X"], sift_full["Q"], sift_full["idx"]
+    nq = 1000
+    out = H.gpu_search(G, idx, Q, 100, 64, 16, first_wave=8, growth=30, want=("stats", "probes", "qrot"))
+    assert out["status"] == 0
+    oidx = _library_oracle(G, idx, X, sift_full["mean"], sift_full["R"], "f32")
+    q_err = _rotation_within_model(G, idx, oidx, out["qrot"][:nq], Q[:nq], range(0, 20_000))
+    same = _probes_within_near_ties(oidx, Q[:nq], out["probes"][:nq], 64)
+    m1, beta = G.dade_get_correction(idx, 16)
+    ids, d, st, ad = search.search(oidx, Q[:nq], out["probes"][:nq], 64, 100, 16, m1.astype(np.float64),
+                                   beta.astype(np.float64), first_wave=8, growth=30, amb=H.AMB["f32"],
+                                   with_amb=True, qdev_eps=H.FLIP_EPS)
+    checked, total = parity.check(out["ids"][:nq], out["dists"][:nq], ids, d, X, Q[:nq], 100, amb_d=ad,
+                                  exact_ties=True)
+    un = st[:, 4] == 0
+    assert np.array_equal(out["stats"][:nq, 0], st[:, 0])
+    assert np.array_equal(out["stats"][:nq][un], st[un, :4])
+    assert st[:, 1].sum() > 0.5 * st[:, 0].sum()
+    print(f"SIFT_PARITY ranks_checked={checked}/{total} queries_certain={un.mean():.3f} "
+          f"probe_lists_identical={same:.3f} rotation_err={q_err:.2e}")
 
 
 def test_sift_full_size_in_the_benchmark_configuration(G, sift_full):
@@ -155,12 +225,17 @@ def _check_sampled(X, Q, pr, fu, K, sample, exact_bits=False):
 
 
 def test_gist_full_size_in_the_benchmark_configuration(G):
+    """GIST-shaped 1M x 960 with BF16 slabs, the benchmarked configuration
+    (nprobe 128, K 100, Delta_d 16, first wave 16 then one wave), all 1,000
+    queries against the oracle given the library's rotation, centroids,
+    assignment and tables (the oracle bounds where the device's BF16 values
+    may round to the neighbouring value), plus the sampled properties."""
     X, Q, T, cfg = synth.workload("gist1m")
     mean, R, _ = G.dade_train_rotation(X, sample_n=200_000, seed=1)
     idx = G.ivf_build(X, mean, R, cfg["nlist"], kmeans_iters=10, seed=1, dtype="bf16")
     try:
         G.dade_fit_correction(idx, T, 100, 64, 16, target_recall=0.995, seed=1)
-        pr = H.gpu_search(G, idx, Q, 100, 128, 16, first_wave=16, growth=30, want=("stats",))
+        pr = H.gpu_search(G, idx, Q, 100, 128, 16, first_wave=16, growth=30, want=("stats", "probes", "qrot"))
         fu = H.gpu_search(G, idx, Q, 100, 128, 0, mode="full", first_wave=16, growth=30)
         assert pr["status"] == 0 and fu["status"] == 0
         sample = np.random.default_rng(6).choice(len(Q), 12, replace=False)
@@ -168,6 +243,20 @@ def test_gist_full_size_in_the_benchmark_configuration(G):
         assert rec >= 0.9
         st = pr["stats"]
         assert st[:, 3].sum() < 0.3 * st[:, 0].sum() * X.shape[1]   # well under a full scan's dims
+        oidx = _library_oracle(G, idx, X, mean, R, "bf16")
+        q_err = _rotation_within_model(G, idx, oidx, pr["qrot"], Q, range(0))
+        same = _probes_within_near_ties(oidx, Q, pr["probes"], 128)
+        m1, beta = G.dade_get_correction(idx, 16)
+        ids, d, ost, ad = search.search(oidx, Q, pr["probes"], 128, 100, 16, m1.astype(np.float64),
+                                        beta.astype(np.float64), first_wave=16, growth=30, amb=H.AMB["f32"],
+                                        with_amb=True, qdev_eps=H.FLIP_EPS)
+        del oidx
+        checked, total = parity.check(pr["ids"], pr["dists"], ids, d, X, Q, 100, amb_d=ad)
+        un = ost[:, 4] == 0
+        assert np.array_equal(st[:, 0], ost[:, 0])
+        assert np.array_equal(st[un], ost[un, :4])
+        print(f"GIST_PARITY ranks_checked={checked}/{total} queries_certain={un.mean():.3f} "
+              f"probe_lists_identical={same:.3f} rotation_err={q_err:.2e}")
     finally:
         idx.close()
 

@@ -50,14 +50,16 @@ def _oracle_res(s, K, nprobe, delta_d, m, first_wave=1, growth=1, final_rel=np.i
     oidx = s["inp"]["oidx"]
     P = int(np.max(nprobe))
     pr = oidx.probe(oidx.rotate_queries(s["Q"]), P)
-    ids, d, st = search.search(oidx, s["Q"], pr, nprobe, K, delta_d, None, None, first_wave=first_wave,
-                               growth=growth, amb=AMB_RES, final_rel=final_rel, estimator="res", res_m=m)
-    return ids, d, st, pr
+    ids, d, st, ad = search.search(oidx, s["Q"], pr, nprobe, K, delta_d, None, None, first_wave=first_wave,
+                                   growth=growth, amb=AMB_RES, final_rel=final_rel, estimator="res", res_m=m,
+                                   with_amb=True)
+    return ids, d, (st, ad), pr
 
 
-def _check(s, out, ids, d, st, K=10, min_strict=0.85):
+def _check(s, out, ids, d, st, K=10):
+    st, ad = st
     assert out["status"] == 0
-    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], K, amb=st[:, 4], min_strict=min_strict)
+    parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], K, amb_d=ad)
     un = st[:, 4] == 0
     assert np.array_equal(out["stats"][:, 0], st[:, 0])
     assert np.array_equal(out["stats"][un], st[un, :4])
@@ -70,7 +72,7 @@ def test_res_matches_oracle(G, pre, m):
                        want=("stats",))
     _check(pre, out, ids, d, st)
     if m <= 2.0:
-        assert st[:, 1].sum() > 0  # the test does prune at these multipliers
+        assert st[0][:, 1].sum() > 0  # the test does prune at these multipliers
 
 
 def test_res_smaller_multiplier_prunes_more(G, pre):
@@ -102,7 +104,7 @@ def test_res_ragged_K_and_nprobe(G, pre):
     ids, d, st, pr = _oracle_res(pre, K, npb, 16, 2.0)
     out = H.gpu_search(G, pre["idx"], pre["Q"], K, npb, 16, probe_in=pr, max_K=20, max_nprobe=16,
                        estimator="res", res_m=2.0)
-    parity.check(out["ids"], out["dists"], ids, d, pre["X"], pre["Q"], K, amb=st[:, 4], min_strict=0.85)
+    parity.check(out["ids"], out["dists"], ids, d, pre["X"], pre["Q"], K, amb_d=st[1])
 
 
 @pytest.mark.parametrize("dtype,delta_d", [("f32", 8), ("f32", 32), ("bf16", 8), ("bf16", 16), ("fp8", 16)])
@@ -112,11 +114,11 @@ def test_res_slab_precisions_and_step_widths(G, dtype, delta_d):
         amb_band = {"f32": AMB_RES, "bf16": AMB_RES, "fp8": AMB_RES}[dtype]
         oidx = s["inp"]["oidx"]
         pr = oidx.probe(oidx.rotate_queries(s["Q"]), 8)
-        ids, d, st = search.search(oidx, s["Q"], pr, 8, 10, delta_d, None, None, amb=amb_band,
-                                   estimator="res", res_m=1.0)
+        ids, d, st, ad = search.search(oidx, s["Q"], pr, 8, 10, delta_d, None, None, amb=amb_band,
+                                       estimator="res", res_m=1.0, with_amb=True)
         out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, delta_d, probe_in=pr, estimator="res", res_m=1.0,
                            want=("stats",))
-        _check(s, out, ids, d, st, min_strict=0.8)
+        _check(s, out, ids, d, (st, ad))
     finally:
         s["idx"].close()
 
