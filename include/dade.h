@@ -284,7 +284,23 @@ typedef struct {
                              /* exact distance (the same results as a table    */
                              /* whose later steps are disabled).  0: all S - 1. */
                              /* Not with final_test (DADE_ENOTIMPL).           */
+    int32_t scan_kernel;     /* PRUNE mode with the learned test (tables, ADS):  */
+                             /* dade_scan_kernel: which kernel runs the waves   */
+                             /* whose tau is finite.  0 (auto) = tensor cores.  */
 } dade_search_opts;
+
+/* The estimate-and-prune kernels of the learned test.  DADE_KERNEL_TENSOR:
+ * per work unit (a tile of 128 candidates of a bucket against up to 128
+ * queries probing it) the partial distances of every pair come from one
+ * tcgen05 contraction per step, dis' = ||q||^2 + ||x||^2 - 2 <q, x> over the
+ * dims so far (split TF32, FP32 accumulation), and the CUDA cores test them;
+ * DADE_KERNEL_CUDA: the FP32 kernel that accumulates (q_j - x_j)^2 per pair
+ * (16 queries per unit, survivors compacted in shared memory after every
+ * step).  Both test every pair after every step and give the same results
+ * up to the rounding of the partial distances (a decision within that
+ * rounding of its threshold may differ).  The final test, RES and OPQ-L
+ * always use the CUDA-core kernels. */
+typedef enum { DADE_KERNEL_AUTO = 0, DADE_KERNEL_CUDA = 1, DADE_KERNEL_TENSOR = 2 } dade_scan_kernel;
 
 /* ------------------------------------------------------------------------
  * OPQ-L (Section V-B "Approximate Distances"): the approximate distance is

@@ -136,6 +136,8 @@ typedef struct {
     double amb;
     const double* xdev;
     const double* qdev;  /* D: the same for the rotated query, or NULL */
+    double norm_eps;     /* the other side computes dis' as ||q||^2 + ||x~||^2 - 2 <q, x~> over the d dims
+                            so far: slack norm_eps * max(d, 16) * (||q||^2 + ||x~||^2) */
 } rounding;
 
 /* Decision of one test for the oracle's own tau (returns 1 = prune) and
@@ -160,7 +162,8 @@ static int estimate_and_test(const double* qr, const double* qdev, const double*
                              int* uncertain, const res_terms* res)
 {
     const double tau = tau3[0], tlo = tau3[1], thi = tau3[2];
-    double p = 0.0, f = 0.0;
+    double p = 0.0, f = 0.0, qn = 0.0, xn = 0.0;
+    const double ne = rd ? rd->norm_eps : 0.0;
     double band = 0.0;
     if (rd && rd->amb > 0.0) {
         double tb = isfinite(thi) ? thi : tlo;
@@ -185,9 +188,13 @@ static int estimate_and_test(const double* qr, const double* qdev, const double*
                 double e = (xdev ? xdev[j] : 0.0) + (qdev ? qdev[j] : 0.0);
                 f += 2.0 * fabs(t) * e + e * e;
             }
+            if (ne > 0.0) {
+                qn += qr[j] * qr[j];
+                xn += xs[j] * xs[j];
+            }
         }
         if (partials) partials[s - 1] = p;
-        double L, w = 1.0, c = 1.0, fl = f;
+        double L, w = 1.0, c = 1.0, fl = f + ne * (double)(j1 > 16 ? j1 : 16) * (qn + xn);
         if (res && res->kind == 1) {
             L = p + res->rx[j1] + res->rq[j1] - res->m * 2.0 * sqrt(res->sg[j1]);
             fl = f + res->rx[D + 1 + j1];
@@ -235,7 +242,7 @@ static int64_t wave_end(int64_t b, int first_wave, int g)
 
 typedef struct {
     int32_t D, dd, S, P, Kmax, mode, first_wave, growth;
-    double amb, final_rel;
+    double amb, norm_eps, final_rel;
     const double* xerr;
     int32_t est;            /* 0: learned tables, 1: RES, 2: ADS, 3: OPQ-L */
     double est_param;       /* RES: m; ADS: eps0; OPQ-L: m3 */
@@ -277,7 +284,7 @@ static int visit(const oracle_args* a, int64_t b, int64_t pos, const double* tau
     const double* qr = a->Qr + b * a->D;
     int pruned;
     int steps;
-    rounding rd = {a->amb, a->Xdev, a->Qdev ? a->Qdev + b * a->D : NULL};
+    rounding rd = {a->amb, a->Xdev, a->Qdev ? a->Qdev + b * a->D : NULL, a->norm_eps};
     *unc = 0;
     if (a->est == 3) {
         const double* t = a->pq_lut + b * (int64_t)a->pq_m * 256;
@@ -443,7 +450,7 @@ static void search_one(const oracle_args* a, int64_t b)
 }
 
 int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, int32_t Kmax,
-                  int32_t mode, int32_t first_wave, int32_t growth, double amb, double final_rel,
+                  int32_t mode, int32_t first_wave, int32_t growth, double amb, double norm_eps, double final_rel,
                   int32_t est, double est_param, const double* var,
                   int32_t pq_m, const uint8_t* pq_codes, const double* pq_err, const double* pq_lut,
                   const double* Qr, const double* Qdev, const float* Q, const double* Xs, const double* Xdev, const uint8_t* unc_rows,
@@ -453,11 +460,11 @@ int oracle_search(int64_t B, int32_t D, int32_t delta_d, int32_t S, int32_t P, i
                   int64_t* out_ids, double* out_d, int64_t* stats, double* amb_d)
 {
     if (delta_d <= 0 || S < 1 || first_wave < 1 || growth < 1 || mode < 0 || mode > 2 || !(final_rel >= 0.0) ||
-        !(amb >= 0.0) || est < 0 || est > 3 || (est == 1 && (!var || !(est_param >= 0.0))) ||
+        !(amb >= 0.0) || !(norm_eps >= 0.0) || est < 0 || est > 3 || (est == 1 && (!var || !(est_param >= 0.0))) ||
         (est == 2 && !(est_param >= 0.0 && est_param < INFINITY)) ||
         (est == 3 && (pq_m < 1 || !pq_codes || !pq_err || !pq_lut || !m1 || !beta)))
         return 1;
-    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, final_rel, xerr, est, est_param,
+    oracle_args a = {D, delta_d, S, P, Kmax, mode, first_wave, growth, amb, norm_eps, final_rel, xerr, est, est_param,
                      pq_m, pq_codes, pq_err, pq_lut, var, Qr, Qdev, Q, Xs, Xdev, unc_rows, X, ids, list_off, members, probes,
                      nprobe, K, m1, beta, tau_in, out_ids, out_d, stats, amb_d};
 #pragma omp parallel for schedule(dynamic, 1)

@@ -133,7 +133,7 @@ class OracleIndex:
 def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode="waves",
            first_wave: int = 1, tau=None, amb: float = 0.0, growth: int = 1, final_rel: float = np.inf,
            estimator: str = "learned", res_m: float = 8.0, ads_eps0: float = 2.1, pq=None, with_amb=False,
-           uncertain_rows=None, qdev_eps=None):
+           uncertain_rows=None, qdev_eps=None, norm_eps: float = 0.0):
     """Returns (ids[B, Kmax], dists[B, Kmax], stats[B, 5]) where stats holds
     candidates visited, candidates pruned, exact distances taken, dims
     scanned, and candidates whose decision another rounding could flip:
@@ -146,7 +146,9 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
     may represent otherwise (e.g. a product-quantisation code decided at a
     near tie); every decision on them counts as uncertain.  qdev_eps: the
     other side's rotated query may differ from this one's by up to
-    qdev_eps * ||q'|| plus one FP32 unit per coordinate.  final_rel: the slack of the
+    qdev_eps * ||q'|| plus one FP32 unit per coordinate.  norm_eps: the
+    other side computes dis' as ||q||^2 + ||x~||^2 - 2 <q, x~> (over the d
+    dims so far), within norm_eps * max(d, 16) * (||q||^2 + ||x~||^2).  final_rel: the slack of the
     test on the completed rotated distance (FINAL_REL), or inf for no test.
     estimator "res": the Gaussian-bound test with multiplier res_m; "ads":
     the ADS test with parameter ads_eps0 (for both, m1 and beta are unused;
@@ -195,7 +197,8 @@ def search(idx: OracleIndex, Q, probes, nprobe, K, delta_d: int, m1, beta, mode=
     rc = lib.oracle_search(
         ctypes.c_int64(B), ctypes.c_int32(idx.D), ctypes.c_int32(delta_d), ctypes.c_int32(S),
         ctypes.c_int32(P), ctypes.c_int32(Kmax), ctypes.c_int32(MODES[mode]),
-        ctypes.c_int32(first_wave), ctypes.c_int32(growth), ctypes.c_double(amb), ctypes.c_double(final_rel),
+        ctypes.c_int32(first_wave), ctypes.c_int32(growth), ctypes.c_double(amb), ctypes.c_double(norm_eps),
+        ctypes.c_double(final_rel),
         ctypes.c_int32(est), ctypes.c_double(est_param), _p(idx.var),
         ctypes.c_int32(pq_m), None if pq_codes is None else _p(pq_codes), None if pq_err is None else _p(pq_err),
         None if pq_lut is None else _p(pq_lut),

@@ -20,6 +20,7 @@ STATUS = {0: "DADE_OK", 1: "DADE_EINVAL", 2: "DADE_ENOMEM", 3: "DADE_ECUDA", 4: 
 SLAB = {"f32": 0, "bf16": 1, "fp8": 2}
 MODE = {"prune": 0, "full": 1}
 ESTIMATOR = {"learned": 0, "res": 1, "pq": 2}
+SCAN_KERNEL = {"auto": 0, "cuda": 1, "tensor": 2}
 
 
 class BuildParams(ctypes.Structure):
@@ -33,7 +34,7 @@ class SearchOpts(ctypes.Structure):
                 ("qrot_out_dev", c_vp), ("stats_dev", c_vp), ("status_dev", c_vp),
                 ("workspace", c_vp), ("workspace_bytes", c_sz), ("wave_growth_log2", c_i32),
                 ("final_test", c_i32), ("estimator", c_i32), ("res_m", ctypes.c_float),
-                ("test_steps", c_i32)]
+                ("test_steps", c_i32), ("scan_kernel", c_i32)]
 
 
 class IndexInfo(ctypes.Structure):

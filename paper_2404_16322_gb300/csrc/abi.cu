@@ -105,6 +105,26 @@ dade_status build_residual_norms(dade_index* idx) {
     return DADE_OK;
 }
 
+dade_status build_tc_operands(dade_index* idx) {
+    const int nl = idx->nlist;
+    idx->tile_base.assign((size_t)nl + 1, 0);
+    for (int l = 0; l < nl; ++l)
+        idx->tile_base[(size_t)l + 1] = idx->tile_base[(size_t)l] + ceil_div(idx->list_size[(size_t)l], kTcRows);
+    const int64_t ntiles = idx->tile_base[(size_t)nl];
+    idx->tc_parts = idx->dtype == DADE_SLAB_BF16 ? 1 : 2;
+    DADE_TRY(idx->tile_base_dev.alloc(sizeof(int64_t) * (nl + 1)));
+    DADE_CUDA_TRY(cudaMemcpy(idx->tile_base_dev.p, idx->tile_base.data(), sizeof(int64_t) * (nl + 1),
+                             cudaMemcpyHostToDevice));
+    DADE_TRY(idx->tcslab_dev.alloc(sizeof(float) * 1024 * (size_t)std::max<int64_t>(1, ntiles) * idx->nb *
+                                   idx->tc_parts));
+    DADE_CUDA_TRY(launch_tc_slab(idx->slab_dev.p, idx->dtype, idx->scale_dev.as<float>(),
+                                 idx->list_slot_dev.as<int64_t>(), idx->list_size_dev.as<int32_t>(),
+                                 idx->tile_base_dev.as<int64_t>(), nl, idx->Dpad, idx->tc_parts, ntiles,
+                                 idx->tcslab_dev.as<float>(), 0));
+    DADE_CUDA_TRY(cudaDeviceSynchronize());
+    return DADE_OK;
+}
+
 dade_status install_table_public(dade_index* idx, int delta_d, int S, const float* m1, const float* beta) {
     return install_table(idx, delta_d, S, m1, beta);
 }
@@ -183,7 +203,7 @@ extern "C" dade_status dade_index_info_get(const dade_index* idx, dade_index_inf
     out->device_bytes = (int64_t)(idx->slab_dev.bytes + idx->orig_dev.bytes + idx->ids_dev.bytes +
                                   idx->cent_dev.bytes + idx->R_dev.bytes + idx->eps_dev.bytes + idx->var_dev.bytes +
                                   idx->sfx_dev.bytes + idx->pq_codes_dev.bytes + idx->pq_err_dev.bytes +
-                                  idx->pq_cb_dev.bytes + idx->pq_perm_dev.bytes);
+                                  idx->pq_cb_dev.bytes + idx->pq_perm_dev.bytes + idx->tcslab_dev.bytes);
     return DADE_OK;
 }
 
@@ -445,6 +465,7 @@ extern "C" dade_status dade_index_load(const char* path, dade_index** out) {
     DADE_TRY(idx->var_dev.alloc(sizeof(float) * Dp));
     DADE_CUDA_TRY(cudaMemcpy(idx->var_dev.p, idx->var.data(), sizeof(float) * Dp, cudaMemcpyHostToDevice));
     DADE_TRY(build_residual_norms(idx.get()));
+    DADE_TRY(build_tc_operands(idx.get()));
     if (pm > 0) {
         DADE_TRY(dade_pq_set(idx.get(), pm, pq_perm.data(), pq_cb.data()));
         if (pq_ht) DADE_TRY(dade_pq_set_correction(idx.get(), pq_c[0], pq_c[1], pq_c[2]));

@@ -244,6 +244,7 @@ extern "C" dade_status ivf_build(const float* X, int64_t N, int32_t D, const dou
         DADE_CUDA_TRY(cudaStreamSynchronize(st));
     }
     DADE_TRY(build_residual_norms(idx.get()));
+    DADE_TRY(build_tc_operands(idx.get()));
     *out = idx.release();
     return DADE_OK;
 }

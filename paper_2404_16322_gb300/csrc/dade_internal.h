@@ -37,6 +37,7 @@ void clear_error();
 constexpr int kBlock = 8;        // dimensions per layout block
 constexpr int kListAlign = 32;   // bucket sizes are padded to a multiple of this
 constexpr int kMaxK = 1024;
+constexpr int kTcRows = 128;     // candidates per tile of the tensor-core scan (MMA M)
 constexpr int kMaxD = 4096;
 // Relative slack of the test on the completed rotated distance (a candidate
 // is reranked iff dis'_S <= (sqrt(tau) + e_x)^2 (1 + kFinalRel)): covers the
@@ -146,6 +147,13 @@ struct dade_index {
     dade::DevBuf var_dev;      // Dpad FP32: variance of each rotated dimension (RES)
     dade::DevBuf sfx_dev;      // (nb + 1) x total_slots FP32: residual norms from block b on (RES)
     std::vector<float> var;    // host copy of var_dev
+    // tensor-core scan operand: per bucket tile of kTcRows candidates, per
+    // 8-dim block, the stored values' TF32 parts (tc_parts of them: 1 for
+    // BF16, else 2) in 4 KB canonical-layout chunks
+    int32_t tc_parts = 0;
+    std::vector<int64_t> tile_base;    // nlist + 1: first tile of each bucket
+    dade::DevBuf tile_base_dev;
+    dade::DevBuf tcslab_dev;
     // OPQ-L: product quantisation of the stored rotated vectors
     int32_t pq_m = 0, pq_ds = 0;
     std::vector<int32_t> pq_perm;      // D: rotated dims of subspace j at [j*ds, (j+1)*ds)
@@ -216,6 +224,11 @@ struct LayoutArgs {
 };
 cudaError_t launch_layout(const LayoutArgs& a, cudaStream_t st);
 cudaError_t launch_quant_error(const LayoutArgs& a, cudaStream_t st);
+cudaError_t launch_tc_slab(const void* slab, int dtype, const float* scale, const int64_t* list_slot,
+                           const int32_t* list_size, const int64_t* tile_base, int nlist, int32_t Dpad, int parts,
+                           int64_t ntiles, float* out, cudaStream_t st);
+// The tensor-core scan's operand copy of idx's slabs (tc_slab_kernel).
+dade_status build_tc_operands(dade_index* idx);
 cudaError_t launch_stored_gather(const void* slab, int dtype, const float* scale, const int64_t* base,
                                  const int64_t* npad, int64_t nrows, int32_t D, float* out, cudaStream_t st);
 cudaError_t launch_dim_var(const float* xrot, int64_t N, int32_t Dpad, float* var, cudaStream_t st);

@@ -174,7 +174,70 @@ __global__ void stored_gather_kernel(const void* slab, int dtype, const float* s
     out[i] = v;
 }
 
+// The stored slabs as the tensor-core scan's operand: per tile of kTcRows
+// candidates of a bucket and per 8-dim block, the TF32 parts of the stored
+// values (hi = tf32(x~), mid = tf32(x~ - hi); only hi for BF16, which TF32
+// holds exactly) in the canonical K-major layout without swizzle, each part
+// one 4 KB chunk: element (row r, dim j) at float (r / 8) * 64 + (j / 4) * 32
+// + (r % 8) * 4 + j % 4 (8-row x 16-byte core matrices; the two K halves 128
+// bytes apart, 8-row groups 256 bytes apart).  Chunks ordered (tile, block,
+// part), so a step's blocks are one contiguous range.
+__global__ void tc_slab_kernel(const void* slab, int dtype, const float* scale, const int64_t* list_slot,
+                               const int32_t* list_size, const int64_t* tile_base, int nlist, int32_t Dpad,
+                               int parts, int64_t ntiles, float* out) {
+    const int nb = Dpad / kBlock;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntiles * nb * kTcRows) return;
+    const int64_t T = i / ((int64_t)nb * kTcRows);
+    const int b = (int)((i / kTcRows) % nb);
+    const int r = (int)(i % kTcRows);
+    int lo = 0, hi_ = nlist;  // bucket of tile T: tile_base[l] <= T < tile_base[l + 1]
+    while (hi_ - lo > 1) {
+        const int mid = (lo + hi_) >> 1;
+        if (tile_base[mid] <= T) lo = mid; else hi_ = mid;
+    }
+    const int l = lo;
+    const int64_t row = (T - tile_base[l]) * kTcRows + r;
+    const int64_t s0 = list_slot[l];
+    const int64_t npad = list_slot[l + 1] - s0;
+    float* o = out + ((T * nb + b) * parts) * 1024 + (r >> 3) * 64 + (r & 7) * 4;
+#pragma unroll
+    for (int j = 0; j < kBlock; ++j) {
+        float x = 0.f;
+        if (row < list_size[l]) {
+            const int64_t e = s0 * Dpad + ((int64_t)b * npad + row) * kBlock + j;
+            if (dtype == DADE_SLAB_F32) {
+                x = static_cast<const float*>(slab)[e];
+            } else if (dtype == DADE_SLAB_BF16) {
+                x = __bfloat162float(static_cast<const __nv_bfloat16*>(slab)[e]);
+            } else {
+                const __nv_fp8_storage_t c = static_cast<const __nv_fp8_storage_t*>(slab)[e];
+                x = __half2float(__half(__nv_cvt_fp8_to_halfraw(c, __NV_E4M3))) * scale[b * kBlock + j];
+            }
+        }
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+        const int off = (j >> 2) * 32 + (j & 3);
+        o[off] = __uint_as_float(h);
+        if (parts > 1) {
+            uint32_t m;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(m) : "f"(x - __uint_as_float(h)));
+            o[1024 + off] = __uint_as_float(m);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_tc_slab(const void* slab, int dtype, const float* scale, const int64_t* list_slot,
+                           const int32_t* list_size, const int64_t* tile_base, int nlist, int32_t Dpad, int parts,
+                           int64_t ntiles, float* out, cudaStream_t st) {
+    const int64_t n = ntiles * (Dpad / kBlock) * kTcRows;
+    if (n == 0) return cudaSuccess;
+    tc_slab_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(slab, dtype, scale, list_slot, list_size, tile_base,
+                                                               nlist, Dpad, parts, ntiles, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_stored_gather(const void* slab, int dtype, const float* scale, const int64_t* base,
                                  const int64_t* npad, int64_t nrows, int32_t D, float* out, cudaStream_t st) {

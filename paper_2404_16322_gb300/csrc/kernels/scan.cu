@@ -289,10 +289,12 @@ struct LoadUnits {
     const int32_t* cnt;
     const int32_t* size;
     int nlist;
+    int32_t qgroup[16];
     __device__ int32_t operator()(int seg, int64_t l) const {
         int c = cnt[(int64_t)seg * nlist + l];
         int s = size[l];
-        return c > 0 ? ((c + kG - 1) / kG) * ((s + kT - 1) / kT) : 0;
+        const int qg = qgroup[seg];
+        return c > 0 ? ((c + qg - 1) / qg) * ((s + kT - 1) / kT) : 0;
     }
 };
 struct LoadCap {
@@ -302,7 +304,8 @@ struct LoadCap {
 };
 
 // One thread per (wave, bucket): write the descriptors of the bucket's units
-// in this wave, in the order of unit_off (group-major, then tile).
+// in this wave, in the order of unit_off (group-major, then tile).  The cnt
+// queries probing the bucket form ceil(cnt / qgroup) groups of balanced size.
 __global__ void expand_units_kernel(IndexView ix, WaveView wv) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)wv.n_waves * ix.nlist) return;
@@ -311,14 +314,17 @@ __global__ void expand_units_kernel(IndexView ix, WaveView wv) {
     if (cnt == 0) return;
     const int nl = ix.list_size[l];
     const int ntile = (nl + kT - 1) / kT;
-    const int ng = (cnt + kG - 1) / kG;
+    const int qg = wv.qgroup[w];
+    const int ng = (cnt + qg - 1) / qg;
+    const int base = cnt / ng, rem = cnt % ng;
     int4* out = wv.units + wv.ubase[w] + wv.unit_off[(int64_t)w * (ix.nlist + 1) + l];
     const int item0 = wv.off_wl[e];
     for (int g = 0; g < ng; ++g) {
-        const int nq = min(kG, cnt - g * kG);
+        const int nq = base + (g < rem ? 1 : 0);
+        const int first = item0 + g * base + min(g, rem);
         for (int t = 0; t < ntile; ++t) {
             const int nt = min(kT, nl - t * kT);
-            out[g * ntile + t] = make_int4(l, t, item0 + g * kG, (nq << 16) | nt);
+            out[g * ntile + t] = make_int4(l, t, first, (nq << 16) | nt);
         }
     }
 }
@@ -455,9 +461,9 @@ cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStre
     count_kernel<<<gb, 128, 0, st>>>(ix, wv);
     const int64_t nwl = (int64_t)wv.n_waves * ix.nlist;
     seg_scan_kernel<<<1, 1024, 0, st>>>(LoadI32{wv.cnt_wl}, wv.off_wl, nwl, 0);
-    seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(LoadUnits{wv.cnt_wl, ix.list_size, ix.nlist},
-                                                 wv.unit_off, (int64_t)ix.nlist,
-                                                 (int64_t)ix.nlist + 1);
+    LoadUnits lu{wv.cnt_wl, ix.list_size, ix.nlist, {}};
+    for (int w = 0; w < 16; ++w) lu.qgroup[w] = wv.qgroup[w];
+    seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(lu, wv.unit_off, (int64_t)ix.nlist, (int64_t)ix.nlist + 1);
     seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(LoadCap{wv.cand_off, wv.B + 1}, wv.cand_off, wv.B,
                                                  wv.B + 1);
     scatter_kernel<<<gb, 128, 0, st>>>(ix, wv);

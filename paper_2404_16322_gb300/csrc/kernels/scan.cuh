@@ -19,8 +19,10 @@ struct IndexView {
     const float* scale;        // FP8 per-dimension scale (Dpad)
     const float* eps;          // per slot: quantisation error norm (null for FP32 slabs)
     const float* sfx;          // (nb + 1) x total_slots: sum of the stored x_i^2 over blocks >= b
+    const float* tcslab;       // tensor-core operand copy of the slabs (build_tc_operands)
+    const int64_t* tile_base;  // nlist + 1: first kTcRows-candidate tile of each bucket
     int64_t total_slots;
-    int32_t D, Dpad, nb, nlist, dtype;
+    int32_t D, Dpad, nb, nlist, dtype, tc_parts;
 };
 
 struct WaveView {
@@ -43,6 +45,8 @@ struct WaveView {
     int32_t* unit_off;        // n_waves x (nlist + 1): work units per wave, prefix
     int4* units;              // unit descriptors {bucket, tile, first item, nq << 16 | nt}
     int64_t ubase[16];        // first descriptor of each wave in `units`
+    int32_t qgroup[16];       // queries per unit at most, per wave (the queries probing a
+                              // bucket in a wave are split into balanced groups)
     int64_t* cand_off;        // n_waves x (B + 1): candidate capacity per query, prefix
     int32_t* cand_cnt;        // B: candidates appended in the current wave
     float* cand_d;            // candidate buffer (capacity of the largest wave)
@@ -85,6 +89,11 @@ cudaError_t launch_wave_scan_res(const IndexView& ix, const WaveView& wv, int w,
                                  cudaStream_t st);
 cudaError_t launch_res_terms(const float* qrot, int64_t B, int32_t D, int32_t Dpad, const float* var,
                              int delta_d, int S, float m, float* res_q, cudaStream_t st);
+// The tensor-core estimate-and-prune scan of the learned test (scan_tc.cu):
+// units of up to kTcRows candidates x 128 queries, nsteps tested steps.
+bool tc_scan_supported(int delta_d);
+cudaError_t launch_wave_scan_tc(const IndexView& ix, const WaveView& wv, int w, int delta_d, const float* m1,
+                                const float* beta, int nsteps, int parts, cudaStream_t st);
 cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStream_t st);
 cudaError_t launch_output(const WaveView& wv, int64_t* ids, float* dists,
                           const int64_t* offsets, cudaStream_t st);

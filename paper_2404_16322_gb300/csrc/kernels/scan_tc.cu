@@ -1,0 +1,471 @@
+// The estimate-and-prune wave scan on the tensor cores (tcgen05).
+//
+// Method (arXiv 2404.16322): a candidate's partial distance is accumulated
+// Delta_d rotated dimensions at a time (the loop of Algorithm 2) and after
+// each step the learned test m1_s dis'_s + beta_s > tau prunes it
+// (Section V-A; one classifier per step, Section V-B "Incremental
+// Correction"); survivors get the exact distance (Section II-A) and join the
+// result queue whose largest entry is tau (Section I).
+//
+// Here a work unit is (bucket l, tile of up to 128 candidates, group of up
+// to 128 queries probing l in the wave), and the partial distances of the
+// whole tile x group are one dense contraction per step:
+//   dis'_s(q, x) = ||q_{<d}||^2 + ||x_{<d}||^2 - 2 <q_{<d}, x_{<d}>,  d = s Delta_d,
+// with the cumulative dot product accumulated step by step in tensor memory
+// (M = 128 candidates, N = the group's queries rounded up to 16, K = 8 per
+// MMA, split TF32: the candidate values' parts hi + mid (mid = 0 for BF16,
+// which TF32 holds exactly) against the query values' parts hi + mid,
+// products hi.hi + hi.mid + mid.hi, FP32 accumulation).
+//  - The candidate operand comes from the index's pre-split copy
+//    (build_tc_operands): one cp.async.bulk per step, double buffered.
+//  - The query operand is gathered by the threads (thread i loads query i's
+//    step values, splits them, stores them in the canonical layout) while
+//    they also sum the squares of their query's values.
+//  - One thread issues the MMAs and commits to an mbarrier; every thread
+//    then reads its candidate's row of the accumulator (tcgen05.ld) and
+//    tests every (candidate, query) pair of the group:
+//      m1 dis' + beta - tau = m1 ||x||^2 + (m1 ||q||^2 + beta - tau) - 2 m1 <q, x>  > 0,
+//    keeping one alive bit per pair in registers.
+//  - After the last tested step the surviving pairs are listed per warp in
+//    shared memory and get the exact FP32 distance, one lane each.
+// Every device wait is bounded (about 2 s, then DADE_ETIMEOUT).
+#include "scan_steps.cuh"
+
+namespace dade {
+namespace {
+
+constexpr int kTcQ = 128;            // queries per unit at most (MMA N)
+constexpr int kChunkF = 1024;        // floats per 4 KB operand chunk (128 rows x 8 dims)
+constexpr uint32_t kTcLBO = 128;     // bytes between the two K halves of a chunk
+constexpr uint32_t kTcSBO = 256;     // bytes between 8-row groups
+
+// offset (floats) of element (row r, dim j) in a chunk
+__device__ __forceinline__ int chunk_off(int r, int j) { return (r >> 3) * 64 + (j >> 2) * 32 + (r & 7) * 4 + (j & 3); }
+
+// tcgen05 shared memory descriptor of a chunk: no swizzle, version 1.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kTcLBO >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((kTcSBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 32 or 16 accumulator columns of this warp's 32 lanes (one row per lane).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int j = 16; j < 32; ++j) v[j] = 0u;
+}
+
+// A bounded wait on an mbarrier, taken by lane 0 and shared with the warp
+// (so that the warp-collective tensor-memory loads stay converged).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int32_t* status, int lane) {
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(bar, parity, status) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+template <int NBLK, int PARTS>
+constexpr int tc_smem_bytes() {
+    // two candidate-operand buffers, one query-operand buffer, alignment slack
+    return (2 * NBLK * PARTS + 2 * NBLK) * 4096 + 1024;
+}
+
+template <int NBLK, int PARTS>
+__global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, WaveView wv, int w,
+                                                                  const float* __restrict__ m1,
+                                                                  const float* __restrict__ beta, int nsteps) {
+    static_assert(kScanThreads == kTcRows && kTcRows == kTcQ, "one thread per candidate row and per query row");
+    constexpr int ACH = NBLK * PARTS;  // chunks per candidate-operand buffer
+    constexpr int NW = kTcQ / 32;      // alive words per thread
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t bar_a[2];
+    __shared__ __align__(8) uint64_t bar_m;
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_unit, s_fail;
+    __shared__ int4 s_desc;
+    __shared__ int s_q[kTcQ];
+    __shared__ float s_tau[kTcQ];
+    __shared__ __align__(16) float s_a[2][kTcQ];
+    __shared__ unsigned s_st[kTcQ * 4];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~uintptr_t(1023));
+    float* abuf = reinterpret_cast<float*>(base);
+    float* bbuf = abuf + 2 * ACH * kChunkF;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(kTcQ)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bar_a[0], 1);
+        mbar_init(&bar_a[1], 1);
+        mbar_init(&bar_m, 1);
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_taddr;
+    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+
+    uint32_t ph_a = 0u, ph_m = 0u;  // parity to wait for: bit b for bar_a[b]; bar_m
+    const int total = wv.unit_off[(int64_t)w * (ix.nlist + 1) + ix.nlist];
+    const int4* units = wv.units + wv.ubase[w];
+    const int nb = ix.nb;
+    const bool want_stats = wv.stats != nullptr;
+    int next_u = 0;
+    int4 next_d = make_int4(0, 0, 0, 0);
+    if (tid == 0) {
+        next_u = atomicAdd(&wv.work[w], 1);
+        if (next_u < total) next_d = units[next_u];
+    }
+
+    for (;;) {
+        if (tid == 0) {
+            s_unit = next_u;
+            s_desc = next_d;
+            if (next_u < total) {
+                next_u = atomicAdd(&wv.work[w], 1);
+                if (next_u < total) next_d = units[next_u];
+            }
+        }
+        __syncthreads();
+        if (s_unit >= total || s_fail) break;
+        const Unit un = unpack_unit(s_desc);
+        const int l = un.l, t = un.t, nq = un.nq, nt = un.nt;
+        const int ncols = (nq + 15) & ~15;
+        const int64_t slot_l = ix.list_slot[l];
+        const int64_t npad = ix.list_slot[l + 1] - slot_l;
+        const int32_t slot0 = (int32_t)(slot_l + (int64_t)t * kTcRows);
+        const float* asrc = ix.tcslab + ((ix.tile_base[l] + t) * nb) * (int64_t)PARTS * kChunkF;
+        auto a_bytes = [nb](int k) { return (uint32_t)(min(NBLK, nb - k * NBLK) * PARTS * 4096); };
+        auto issue_a = [&](int k) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar_a[k & 1], a_bytes(k));
+            bulk_g2s(abuf + (k & 1) * ACH * kChunkF, asrc + (int64_t)k * NBLK * PARTS * kChunkF, a_bytes(k),
+                     &bar_a[k & 1]);
+            if (wv.staged_bytes) atomicAdd(wv.staged_bytes, (unsigned long long)a_bytes(k));
+        };
+        // the candidate operand of step k is copied while step k - 1 runs
+        if (tid == 0 && nsteps > 0) issue_a(0);
+        float tq = 0.f, qn = 0.f, xn = 0.f;
+        const float* qsrc = nullptr;
+        if (tid < nq) {
+            const int q = wv.items[un.item + tid];
+            tq = wv.tau[q];
+            s_q[tid] = q;
+            s_tau[tid] = tq;
+            qsrc = wv.qrot + (int64_t)q * ix.Dpad;
+        }
+        if (want_stats)
+            for (int i = tid; i < nq * 4; i += kScanThreads) s_st[i] = (i & 3) == 0 ? (unsigned)nt : 0u;
+        // alive bit j of word c4: the pair (this thread's candidate, query 32 c4 + j)
+        uint32_t alive[NW];
+#pragma unroll
+        for (int c4 = 0; c4 < NW; ++c4) {
+            const int lo = c4 * 32, n = min(32, max(0, nq - lo));
+            alive[c4] = (tid < nt && n > 0) ? (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) : 0u;
+        }
+        float qv[NBLK * kBlock];
+        auto load_q = [&](int k) {
+            const int b0 = k * NBLK, nbk = min(NBLK, nb - b0);
+#pragma unroll
+            for (int bb = 0; bb < NBLK; ++bb) {
+                float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
+                if (qsrc && bb < nbk) {
+                    u = __ldg(reinterpret_cast<const float4*>(qsrc + (b0 + bb) * kBlock));
+                    v = __ldg(reinterpret_cast<const float4*>(qsrc + (b0 + bb) * kBlock) + 1);
+                }
+                qv[bb * 8 + 0] = u.x; qv[bb * 8 + 1] = u.y; qv[bb * 8 + 2] = u.z; qv[bb * 8 + 3] = u.w;
+                qv[bb * 8 + 4] = v.x; qv[bb * 8 + 5] = v.y; qv[bb * 8 + 6] = v.z; qv[bb * 8 + 7] = v.w;
+            }
+        };
+        load_q(0);
+        int k = 0;
+        bool mma_failed = false;
+        for (; k < nsteps; ++k) {
+            const int b0 = k * NBLK, nbk = min(NBLK, nb - b0);
+            const float mk = m1[k], bk = beta[k];
+            // 1. the step's query operand, the query norms and the test constants
+            if (tid < nq) {
+#pragma unroll
+                for (int bb = 0; bb < NBLK; ++bb) {
+                    if (bb < nbk) {
+                        float h[8], m[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float x = qv[bb * 8 + j];
+                            h[j] = tf32_rna(x);
+                            m[j] = tf32_rna(x - h[j]);
+                            qn = fmaf(x, x, qn);
+                        }
+                        float* ch = bbuf + (bb * 2) * kChunkF + chunk_off(tid, 0);
+                        float* cm = ch + kChunkF;
+                        *reinterpret_cast<float4*>(ch) = make_float4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<float4*>(ch + 32) = make_float4(h[4], h[5], h[6], h[7]);
+                        *reinterpret_cast<float4*>(cm) = make_float4(m[0], m[1], m[2], m[3]);
+                        *reinterpret_cast<float4*>(cm + 32) = make_float4(m[4], m[5], m[6], m[7]);
+                    }
+                }
+                s_a[k & 1][tid] = fmaf(mk, qn, bk) - tq;
+            }
+            fence_proxy_async();
+            // 2. the candidate operand of the step has landed
+            const bool ok = warp_wait(&bar_a[k & 1], (ph_a >> (k & 1)) & 1u, wv.status, lane);
+            ph_a ^= 1u << (k & 1);
+            if (!ok && lane == 0) s_fail = 1;
+            uint32_t any = 0u;
+#pragma unroll
+            for (int c4 = 0; c4 < NW; ++c4) any |= alive[c4];
+            // every thread is done with step k - 1 here: its candidate buffer
+            // is free, and the tensor core has finished reading the operands
+            const int live = __syncthreads_or(any != 0u);
+            if (s_fail || !live) break;
+            // 3. the MMAs of the step, issued by one thread, and the copy of
+            //    the next step's candidate operand into the other buffer
+            if (tid == 0) {
+                if (k + 1 < nsteps) issue_a(k + 1);
+                tc_fence_after();
+                const uint32_t idesc = tc_idesc(ncols);
+                const uint32_t a0 = smem_u32(abuf + (k & 1) * ACH * kChunkF), bq = smem_u32(bbuf);
+#pragma unroll
+                for (int bb = 0; bb < NBLK; ++bb) {
+                    if (bb < nbk) {
+                        const uint32_t ah = a0 + (uint32_t)(bb * PARTS) * 4096u, am = ah + 4096u;
+                        const uint32_t bh = bq + (uint32_t)(bb * 2) * 4096u, bm = bh + 4096u;
+                        tc_mma(tmem, tc_desc(ah), tc_desc(bh), idesc, (k > 0 || bb > 0) ? 1u : 0u);
+                        tc_mma(tmem, tc_desc(ah), tc_desc(bm), idesc, 1u);
+                        if (PARTS > 1) tc_mma(tmem, tc_desc(am), tc_desc(bh), idesc, 1u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&bar_m))
+                             : "memory");
+            }
+            // 4. meanwhile: the next step's query values, this step's candidate norms
+            if (k + 1 < nsteps) load_q(k + 1);
+            if (tid < nt) {
+                const float* ar = abuf + (k & 1) * ACH * kChunkF + chunk_off(tid, 0);
+#pragma unroll
+                for (int bb = 0; bb < NBLK; ++bb) {
+                    if (bb < nbk) {
+                        const float* ch = ar + (bb * PARTS) * kChunkF;
+                        float4 h0 = *reinterpret_cast<const float4*>(ch), h1 = *reinterpret_cast<const float4*>(ch + 32);
+                        if (PARTS > 1) {
+                            const float4 m0 = *reinterpret_cast<const float4*>(ch + kChunkF);
+                            const float4 m1v = *reinterpret_cast<const float4*>(ch + kChunkF + 32);
+                            h0.x += m0.x; h0.y += m0.y; h0.z += m0.z; h0.w += m0.w;
+                            h1.x += m1v.x; h1.y += m1v.y; h1.z += m1v.z; h1.w += m1v.w;
+                        }
+                        xn = fmaf(h0.x, h0.x, xn); xn = fmaf(h0.y, h0.y, xn);
+                        xn = fmaf(h0.z, h0.z, xn); xn = fmaf(h0.w, h0.w, xn);
+                        xn = fmaf(h1.x, h1.x, xn); xn = fmaf(h1.y, h1.y, xn);
+                        xn = fmaf(h1.z, h1.z, xn); xn = fmaf(h1.w, h1.w, xn);
+                    }
+                }
+            }
+            const float xm = mk * xn, m2 = -2.f * mk;
+            const unsigned dims_k = (unsigned)min((k + 1) * NBLK * kBlock, ix.D);
+            // 5. the accumulator is complete (a warp whose wait gave up skips
+            //    the tests; the CTA leaves together at the next barrier)
+            const bool okm = warp_wait(&bar_m, ph_m, wv.status, lane);
+            ph_m ^= 1u;
+            if (!okm) {
+                mma_failed = true;
+                if (lane == 0) s_fail = 1;
+            }
+            tc_fence_after();
+            // 6. the tests of every (candidate, query) pair
+#pragma unroll
+            for (int c4 = 0; c4 < NW; ++c4) {
+                if (okm && c4 * 32 < ncols) {
+                    uint32_t v[32];
+                    if (ncols - c4 * 32 >= 32) tmem_ld32(tmem_row + (uint32_t)(c4 * 32), v);
+                    else tmem_ld16(tmem_row + (uint32_t)(c4 * 32), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    uint32_t newly = 0u;
+                    if (alive[c4]) {
+                        const float4* ap = reinterpret_cast<const float4*>(&s_a[k & 1][c4 * 32]);
+                        uint32_t prune = 0u;
+#pragma unroll
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 a4 = ap[j4];
+                            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int j = j4 * 4 + i;
+                                const float tv = fmaf(m2, __uint_as_float(v[j]), xm + av[i]);
+                                prune |= (tv > 0.f ? 1u : 0u) << j;
+                            }
+                        }
+                        newly = alive[c4] & prune;
+                        alive[c4] &= ~prune;
+                    }
+                    if (want_stats) {
+                        for (int j = 0; j < 32; ++j) {
+                            const int np = __popc(__ballot_sync(0xffffffffu, (newly >> j) & 1u));
+                            if (lane == 0 && np) {
+                                atomicAdd(&s_st[(c4 * 32 + j) * 4 + 1], (unsigned)np);
+                                atomicAdd(&s_st[(c4 * 32 + j) * 4 + 3], (unsigned)np * dims_k);
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+        }
+        // No copy is in flight here: the copy of step k + 1 is issued only
+        // after the barrier of step k has let the step run.  MMAs whose wait
+        // gave up get one more bounded wait before the CTA stops.
+        if (mma_failed) warp_wait(&bar_m, ph_m ^ 1u, nullptr, lane);
+        __syncthreads();
+        if (s_fail) break;
+        // 7. survivors: the exact distance from the original vector, one lane
+        //    each, listed per warp (the query buffer is free now)
+        uint16_t* list = reinterpret_cast<uint16_t*>(bbuf) + warp * 1024;
+        unsigned long long ex_bytes = 0;
+#pragma unroll
+        for (int c4 = 0; c4 < NW; ++c4) {
+            if (c4 * 32 >= ncols) continue;
+            uint32_t bits = alive[c4];
+            const int cnt = __popc(bits);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            if (tot == 0) continue;
+            int pos = incl - cnt;
+            while (bits) {
+                const int j = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                list[pos++] = (uint16_t)(((c4 * 32 + j) << 8) | tid);
+            }
+            __syncwarp();
+            for (int b = 0; b < tot; b += 32) {
+                const int i = b + lane;
+                const bool valid = i < tot;
+                const int key = valid ? list[i] : 0;
+                const int g = key >> 8, c = key & 255;
+                const int q = s_q[g];
+                float d = 0.f;
+                if (valid)
+                    d = exact_distance(ix.orig + slot_l * ix.Dpad + ((int64_t)t * kTcRows + c) * kBlock, npad,
+                                       wv.qpad + (int64_t)q * ix.Dpad, nb);
+                append_any(wv, w, q, valid && d <= s_tau[g], d, slot0 + c, lane);
+                if (want_stats && valid) {
+                    atomicAdd(&s_st[g * 4 + 2], 1u);
+                    atomicAdd(&s_st[g * 4 + 3], (unsigned)ix.D);
+                }
+            }
+            ex_bytes += (unsigned long long)tot * ix.Dpad * sizeof(float);
+            __syncwarp();
+        }
+        if (wv.staged_bytes && lane == 0 && ex_bytes) atomicAdd(wv.staged_bytes, ex_bytes);
+        __syncthreads();
+        if (want_stats)
+            for (int i = tid; i < nq * 4; i += kScanThreads)
+                if (s_st[i])
+                    atomicAdd((unsigned long long*)&wv.stats[(int64_t)s_q[i >> 2] * 4 + (i & 3)],
+                              (unsigned long long)s_st[i]);
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcQ) : "memory");
+    }
+}
+
+template <int NBLK, int PARTS>
+cudaError_t launch_tc_t(const IndexView& ix, const WaveView& wv, int w, const float* m1, const float* beta,
+                        int nsteps, cudaStream_t st) {
+    static int grid = 0, smem = 0;
+    auto kern = tc_scan_kernel<NBLK, PARTS>;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        // each CTA holds kTcQ of the SM's 512 tensor-memory columns for its
+        // whole life: request enough shared memory that at most
+        // 512 / kTcQ CTAs are resident on an SM, so that no allocation waits
+        int bytes = tc_smem_bytes<NBLK, PARTS>();
+        for (;;) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kScanThreads, bytes);
+            if (e != cudaSuccess) return e;
+            if (per <= 512 / kTcQ) break;
+            bytes += 8192;
+        }
+        smem = bytes;
+        // the occupancy query can report fewer resident CTAs than registers and
+        // shared memory allow (it does not know how much tensor memory a CTA
+        // takes); the scan is persistent, so a launch of 512 / kTcQ CTAs per
+        // SM is safe either way: CTAs that are not resident start later and
+        // find the work taken
+        grid = sms * (512 / kTcQ);
+    }
+    kern<<<grid, kScanThreads, smem, st>>>(ix, wv, w, m1, beta, nsteps);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_scan_supported(int delta_d) { return delta_d == 8 || delta_d == 16 || delta_d == 32; }
+
+cudaError_t launch_wave_scan_tc(const IndexView& ix, const WaveView& wv, int w, int delta_d, const float* m1,
+                                const float* beta, int nsteps, int parts, cudaStream_t st) {
+    if (parts == 1) {
+        if (delta_d == 8) return launch_tc_t<1, 1>(ix, wv, w, m1, beta, nsteps, st);
+        if (delta_d == 16) return launch_tc_t<2, 1>(ix, wv, w, m1, beta, nsteps, st);
+        if (delta_d == 32) return launch_tc_t<4, 1>(ix, wv, w, m1, beta, nsteps, st);
+    } else {
+        if (delta_d == 8) return launch_tc_t<1, 2>(ix, wv, w, m1, beta, nsteps, st);
+        if (delta_d == 16) return launch_tc_t<2, 2>(ix, wv, w, m1, beta, nsteps, st);
+        if (delta_d == 32) return launch_tc_t<4, 2>(ix, wv, w, m1, beta, nsteps, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dade

@@ -17,8 +17,11 @@
 //    kept except terms below 2^-22 of the result, and a product by an exact
 //    TF32 b (such as a permutation matrix) is exact -- then tcgen05.commit
 //    to an mbarrier that the threads wait on (bounded);
-//  - the 4 warps read their 32 accumulator lanes (rows) with
-//    tcgen05.ld.32x32b and apply the epilogue.
+//  - the accumulator covers one K block: the 4 warps read their 32 lanes
+//    (rows) with tcgen05.ld.32x32b after every block and add them to FP32
+//    registers, so the tensor core's own accumulation rounding stays that
+//    of 32-term sums (the error of a long K would otherwise grow with K);
+//    the epilogue then works from those registers.
 #include "../dade_internal.h"
 
 namespace dade {
@@ -191,12 +194,21 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
 
     uint32_t phase = 0;
     const int nkb = (Kd + TKB - 1) / TKB;
+    // the accumulator restarts at every K block and the block results are
+    // summed here in FP32 (round to nearest): the tensor core's FP32
+    // accumulation then spans 32 products, not all of K
+    float acc[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[j] = 0.f;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     for (int kb = 0; kb < nkb; ++kb) {
         const int k0 = kb * TKB;
         load_split<VA>(A, lda, sub, m0, M, k0, Kd, a_hi, a_md, a_lo, tid);
         load_split<VB>(Bm, ldb, nullptr, n0, N, k0, Kd, b_hi, b_md, nullptr, tid);
-        // make the generic-proxy stores visible to the tensor core
+        // make the generic-proxy stores visible to the tensor core (and
+        // order the previous block's tensor-memory reads before its MMAs)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -205,7 +217,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
 #pragma unroll
             for (int s = 0; s < TKB / 8; ++s) {
                 const uint32_t step = (uint32_t)s * 2 * LBO;  // K = 8 = two core matrices
-                const uint32_t first = (kb == 0 && s == 0) ? 0u : 1u;
+                const uint32_t first = s == 0 ? 0u : 1u;
                 mma_tf32(tmem, smem_desc(ah + step), smem_desc(bh + step), first);
                 mma_tf32(tmem, smem_desc(ah + step), smem_desc(bm + step), 1u);
                 mma_tf32(tmem, smem_desc(am + step), smem_desc(bh + step), 1u);
@@ -221,6 +233,21 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         __syncthreads();
         if (!s_ok) break;
+        // this block's products: warp w reads its 32 accumulator lanes (rows)
+#pragma unroll
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                "%12, %13, %14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                  "=r"(v[14]), "=r"(v[15])
+                : "r"(trow + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
+        }
     }
 
     if (s_ok) {
@@ -231,21 +258,11 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
         const int r = warp * 32 + lane;
         const int64_t gm = m0 + r;
         const float arow = (EPI == EPI_L2 && gm < M) ? an[gm] : 0.f;
-#pragma unroll 1
+#pragma unroll
         for (int c0 = 0; c0 < TN; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                "%12, %13, %14, %15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float dot = __uint_as_float(v[j]);
+                const float dot = acc[c0 + j];
                 float out;
                 if (EPI == EPI_L2) out = fmaxf(0.f, arow + (n0 + c0 + j < N ? bn[n0 + c0 + j] : 0.f) - 2.f * dot);
                 else out = dot;

@@ -61,6 +61,35 @@ int64_t wave_bound(const dade_index* idx, int P, int f, int g, int w) {
 // The RES test is in use (PRUNE mode with estimator RES).
 bool uses_res(const dade_search_opts& o) { return o.mode == DADE_SCAN_PRUNE && o.estimator == DADE_EST_RES; }
 
+// Steps of the estimate: ceil(Dpad / delta_d); OPQ-L has one test (S = 2).
+int n_steps(const dade_index* idx, int32_t delta_d, const dade_search_opts& o) {
+    if (o.estimator == DADE_EST_PQ) return 2;
+    return (int)ceil_div(idx->Dpad, delta_d > 0 ? delta_d : idx->Dpad);
+}
+
+// The tensor-core kernel can run the learned test's waves of this search.
+bool tc_eligible(const dade_index* idx, int32_t delta_d, const dade_search_opts& o) {
+    return o.mode == DADE_SCAN_PRUNE && o.estimator == DADE_EST_LEARNED && !o.final_test && idx->tcslab_dev.p &&
+           tc_scan_supported(delta_d);
+}
+
+enum WaveKernel { WK_EXACT = 0, WK_CUDA = 1, WK_TENSOR = 2, WK_PQ = 3 };
+
+// Which kernel scans wave w: every candidate's exact distance (a full scan,
+// a wave whose tau is +inf for every query, or no test to run), the OPQ-L
+// scan, or the learned / RES test on the CUDA cores or the tensor cores.
+int wave_kernel(const dade_index* idx, int32_t delta_d, const dade_search_opts& o, int w) {
+    const int S = n_steps(idx, delta_d, o);
+    if (o.mode == DADE_SCAN_FULL || S <= 1 || (w == 0 && o.tau_dev == nullptr)) return WK_EXACT;
+    if (o.estimator == DADE_EST_PQ) return WK_PQ;
+    if (tc_eligible(idx, delta_d, o) && o.scan_kernel != DADE_KERNEL_CUDA) return WK_TENSOR;
+    return WK_CUDA;
+}
+
+// Queries per work unit of a wave: the tensor-core kernel takes up to 128
+// (its MMA N), the CUDA-core kernels kG.
+int wave_qgroup(int kernel) { return kernel == WK_TENSOR ? 128 : kG; }
+
 size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o, char* base, Plan* pl) {
     const int P = o.max_nprobe, Kmax = o.max_K;
     const bool frozen = o.tau_dev != nullptr;
@@ -99,8 +128,10 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     int64_t ucap = 0;
     for (int w = 0; w < nw; ++w) {
         const int64_t width = std::max(0, std::min(P, wave_begin(w + 1, f, g)) - wave_begin(w, f, g));
+        const int qg = wave_qgroup(wave_kernel(idx, delta_d, o, w));
         v.ubase[w] = ucap;
-        ucap += (ceil_div(B * width, kG) + std::min<int64_t>(nl, B * width)) * ntile_max;
+        v.qgroup[w] = qg;
+        ucap += (ceil_div(B * width, qg) + std::min<int64_t>(nl, B * width)) * ntile_max;
     }
     v.units = c.take<int4>((size_t)std::max<int64_t>(1, ucap));
     pl->cand_cap = B * cap_per_q;
@@ -146,6 +177,9 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
         if (o.mode == DADE_SCAN_PRUNE && (o.final_test || o.test_steps))
             return fail(DADE_ENOTIMPL, "OPQ-L has one test: no final_test or test_steps");
     }
+    if (o.scan_kernel < DADE_KERNEL_AUTO || o.scan_kernel > DADE_KERNEL_TENSOR) return fail(DADE_EINVAL, "bad scan_kernel");
+    if (o.scan_kernel == DADE_KERNEL_TENSOR && o.mode == DADE_SCAN_PRUNE && !tc_eligible(idx, delta_d, o))
+        return fail(DADE_ENOTIMPL, "the tensor-core scan runs the learned test without final_test only");
     if (o.test_steps < 0) return fail(DADE_EINVAL, "test_steps < 0");
     if (o.test_steps > 0 && o.final_test && o.mode == DADE_SCAN_PRUNE)
         return fail(DADE_ENOTIMPL, "test_steps with final_test");
@@ -220,17 +254,20 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     ix.scale = idx->scale_dev.as<float>();
     ix.eps = idx->dtype == DADE_SLAB_F32 ? nullptr : idx->eps_dev.as<float>();
     ix.sfx = idx->sfx_dev.as<float>();
+    ix.tcslab = idx->tcslab_dev.as<float>();
+    ix.tile_base = idx->tile_base_dev.as<int64_t>();
     ix.total_slots = idx->total_slots;
     ix.D = idx->D;
     ix.Dpad = idx->Dpad;
     ix.nb = idx->nb;
     ix.nlist = idx->nlist;
     ix.dtype = idx->dtype;
+    ix.tc_parts = idx->tc_parts;
 
     const bool full = o.mode == DADE_SCAN_FULL;
     const bool pq = o.estimator == DADE_EST_PQ;
     // OPQ-L has one test whatever delta_d is (S = 2: one test, then the exact distance)
-    const int S = pq ? 2 : (int)ceil_div(idx->Dpad, delta_d > 0 ? delta_d : idx->Dpad);
+    const int S = n_steps(idx, delta_d, o);
     const float *m1 = nullptr, *beta = nullptr;
     if (!full && S > 1 && !v.est && !pq) {
         const CorrectionTable& tb = idx->tables.at(delta_d);
@@ -296,13 +333,15 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
         }
         // wave 0 has tau = +inf for every query (no frozen tau): every
         // candidate's exact distance, through the full-scan kernel
-        const bool exact_wave = full || S <= 1 || (w == 0 && o.tau_dev == nullptr);
-        if (pq && !exact_wave) {
+        const int wk = wave_kernel(idx, delta_d, o, w);
+        if (wk == WK_PQ) {
             PQView pv{idx->pq_codes_dev.as<uint8_t>(), idx->pq_err_dev.as<float>(), pl.pq_lut, idx->total_slots,
                       idx->pq_m, idx->pq_m1, idx->pq_m3, idx->pq_beta};
             DADE_CUDA_TRY(launch_pq_scan(ix, v, w, pv, st));
+        } else if (wk == WK_TENSOR) {
+            DADE_CUDA_TRY(launch_wave_scan_tc(ix, v, w, delta_d, m1, beta, v.test_steps, idx->tc_parts, st));
         } else {
-            DADE_CUDA_TRY(launch_wave_scan(ix, v, w, exact_wave, delta_d, m1, beta, S, st));
+            DADE_CUDA_TRY(launch_wave_scan(ix, v, w, wk == WK_EXACT, delta_d, m1, beta, S, st));
         }
         if (timed) {
             DADE_CUDA_TRY(cudaEventRecord(e1, st));

@@ -168,6 +168,7 @@ extern "C" dade_status dade_index_shard(const dade_index* idx, int32_t n_shards,
     DADE_TRY(dup(sh->scale_dev, idx->scale_dev));
     DADE_TRY(dup(sh->var_dev, idx->var_dev));
     DADE_TRY(build_residual_norms(sh.get()));
+    DADE_TRY(build_tc_operands(sh.get()));
     for (const auto& kv : idx->tables)
         DADE_TRY(install_table_public(sh.get(), kv.first, kv.second.S, kv.second.m1.data(), kv.second.beta.data()));
     *out = sh.release();

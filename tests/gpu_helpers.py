@@ -20,6 +20,11 @@ AMB = {"f32": 3e-5, "bf16": 3e-5, "fp8": 3e-5, "exact": 5e-6}
 # stored at the neighbouring value, and an FP8 scale (amax / 448) moves with
 # the column maximum: the oracle's Xdev bounds both.
 FLIP_EPS = 4e-6
+# The tensor-core scan computes dis' = ||q||^2 + ||x~||^2 - 2 <q, x~> over the
+# d dims so far (split TF32, FP32 accumulation); the oracle's slack for it is
+# NORM_EPS * max(d, 16) * (||q||^2 + ||x~||^2): the dropped split terms
+# (~2^-22 relative) and the accumulation rounding that grows with d.
+NORM_EPS = 2e-8
 
 
 def oracle_inputs(X, T, nlist, iters=8, seed=7, K=10, nprobe=8, delta_d=16, dtype="f32", r=0.995,
@@ -67,7 +72,7 @@ def build_gpu(G, X, inp, nlist, dtype="f32", delta_d=16):
 
 def gpu_search(G, idx, Q, K, nprobe, delta_d, mode="prune", probe_in=None, tau=None, max_K=None,
                max_nprobe=None, first_wave=0, growth=0, final_test=False, estimator="learned", res_m=8.0,
-               test_steps=0, want=()):
+               test_steps=0, want=(), scan_kernel="auto"):
     import torch
     B = Q.shape[0]
     Kv = np.broadcast_to(np.asarray(K, np.int32), (B,)).copy()
@@ -93,6 +98,7 @@ def gpu_search(G, idx, Q, K, nprobe, delta_d, mode="prune", probe_in=None, tau=N
     G.dade_search(idx, q, k, n, delta_d, ids, dists, max_K=max_K, max_nprobe=max_nprobe, mode=mode,
                   first_wave=first_wave, tau=tin, probe_in=pin, status=status, wave_growth_log2=growth,
                   final_test=final_test, estimator=estimator, res_m=res_m, test_steps=test_steps,
+                  scan_kernel=scan_kernel,
                   **{kw: t for kw, t in extra.values()})
     torch.cuda.synchronize()
     st = int(status.item())

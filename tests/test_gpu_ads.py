@@ -49,7 +49,7 @@ def test_ads_matches_oracle(G, haar, delta_d, eps0):
     G.dade_set_correction(s["idx"], delta_d, m1, beta)
     pr = s["oidx"].probe(s["oidx"].rotate_queries(s["Q"]), 8)
     ids, d, st, ad = search.search(s["oidx"], s["Q"], pr, 8, 10, delta_d, None, None, estimator="ads",
-                                   ads_eps0=eps0, amb=H.AMB["exact"], with_amb=True)
+                                   ads_eps0=eps0, amb=H.AMB["exact"], with_amb=True, norm_eps=H.NORM_EPS)
     out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, delta_d, probe_in=pr, want=("stats",))
     assert out["status"] == 0
     parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb_d=ad)

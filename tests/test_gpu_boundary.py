@@ -113,7 +113,7 @@ def test_ragged_packed_output_matches_the_oracle(G, pre):
     Kq = np.maximum(K, 1)
     oi, od, ost, ad = search.search(oidx, Q[live], pr[live], npb[live], Kq[live], 16,
                                     pre["inp"]["m1"].astype(np.float64), pre["inp"]["beta"].astype(np.float64),
-                                    amb=H.AMB["exact"], with_amb=True)
+                                    amb=H.AMB["exact"], with_amb=True, norm_eps=H.NORM_EPS)
     parity.check(gi[live], gd[live], oi, od, X, Q[live], K[live], amb_d=ad)
     # the padded layout of the same search holds the same entries
     pad = H.gpu_search(G, idx, Q, K, npb, 16, probe_in=pr, max_K=30, max_nprobe=16)

@@ -45,7 +45,7 @@ def _oracle_search(inp, Q, K, nprobe, delta_d, amb="exact", final_rel=np.inf):
     P = int(np.max(nprobe))
     pr = oidx.probe(oidx.rotate_queries(Q), P)
     ids, d, st, ad = search.search(oidx, Q, pr, nprobe, K, delta_d, inp["m1"].astype(np.float64),
-                                   inp["beta"].astype(np.float64), amb=H.AMB[amb], final_rel=final_rel, with_amb=True)
+                                   inp["beta"].astype(np.float64), amb=H.AMB[amb], final_rel=final_rel, with_amb=True, norm_eps=H.NORM_EPS)
     return ids, d, st, pr, ad
 
 
@@ -152,7 +152,7 @@ def test_sift_full_size_matches_the_oracle(G, sift_full):
     m1, beta = G.dade_get_correction(idx, 16)
     ids, d, st, ad = search.search(oidx, Q[:nq], out["probes"][:nq], 64, 100, 16, m1.astype(np.float64),
                                    beta.astype(np.float64), first_wave=8, growth=30, amb=H.AMB["f32"],
-                                   with_amb=True, qdev_eps=H.FLIP_EPS)
+                                   with_amb=True, norm_eps=H.NORM_EPS, qdev_eps=H.FLIP_EPS)
     checked, total = parity.check(out["ids"][:nq], out["dists"][:nq], ids, d, X, Q[:nq], 100, amb_d=ad,
                                   exact_ties=True)
     un = st[:, 4] == 0
@@ -249,7 +249,7 @@ def test_gist_full_size_in_the_benchmark_configuration(G):
         m1, beta = G.dade_get_correction(idx, 16)
         ids, d, ost, ad = search.search(oidx, Q, pr["probes"], 128, 100, 16, m1.astype(np.float64),
                                         beta.astype(np.float64), first_wave=16, growth=30, amb=H.AMB["f32"],
-                                        with_amb=True, qdev_eps=H.FLIP_EPS)
+                                        with_amb=True, norm_eps=H.NORM_EPS, qdev_eps=H.FLIP_EPS)
         del oidx
         checked, total = parity.check(pr["ids"], pr["dists"], ids, d, X, Q, 100, amb_d=ad)
         un = ost[:, 4] == 0

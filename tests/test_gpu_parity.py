@@ -51,7 +51,7 @@ def _oracle(s, Q, K, nprobe, delta_d=16, m1=None, beta=None, mode="waves", tau=N
     m1 = s["inp"]["m1"] if m1 is None else m1
     beta = s["inp"]["beta"] if beta is None else beta
     ids, d, st, ad = search.search(oidx, Q, pr, nprobe, K, delta_d, m1.astype(np.float64),
-                                   beta.astype(np.float64), mode=mode, tau=tau, amb=H.AMB[dtype_amb], with_amb=True,
+                                   beta.astype(np.float64), mode=mode, tau=tau, amb=H.AMB[dtype_amb], with_amb=True, norm_eps=H.NORM_EPS,
                                    qdev_eps=s["inp"]["qdev"])
     return ids, d, st, pr, ad
 
@@ -87,21 +87,22 @@ def test_probes_match_oracle_up_to_near_ties(G, tiny_setup):
     assert n_exact >= 0.95 * len(s["Q"])
 
 
+@pytest.mark.parametrize("kernel", ["tensor", "cuda"])
 @pytest.mark.parametrize("setup", ["tiny_setup", "tiny_pre"])
 @pytest.mark.parametrize("mode", ["waves", "tables_off"])
-def test_prune_path_matches_oracle(G, request, setup, mode):
+def test_prune_path_matches_oracle(G, request, setup, mode, kernel):
     s = request.getfixturevalue(setup)
     Q = s["Q"]
     if mode == "waves":
         ids, d, st, pr, ad = _oracle(s, Q, 10, 8)
-        out = H.gpu_search(G, s["idx"], Q, 10, 8, 16, probe_in=pr, want=("stats",))
+        out = H.gpu_search(G, s["idx"], Q, 10, 8, 16, probe_in=pr, want=("stats",), scan_kernel=kernel)
     else:
         S = search.n_steps(128, 16)
         m1, beta = search.disabled_tables(S)
         ids, d, st, pr, ad = _oracle(s, Q, 10, 8, m1=m1, beta=beta)
         G.dade_set_correction(s["idx"], 16, m1.astype(np.float32), beta.astype(np.float32))
         try:
-            out = H.gpu_search(G, s["idx"], Q, 10, 8, 16, probe_in=pr, want=("stats",))
+            out = H.gpu_search(G, s["idx"], Q, 10, 8, 16, probe_in=pr, want=("stats",), scan_kernel=kernel)
         finally:
             G.dade_set_correction(s["idx"], 16, s["inp"]["m1"], s["inp"]["beta"])
     assert out["status"] == 0
@@ -158,7 +159,7 @@ def test_wave_growth_schedules(G, tiny_pre, fw, g):
     pr = oidx.probe(oidx.rotate_queries(s["Q"]), 8)
     ids, d, st, ad = search.search(oidx, s["Q"], pr, 8, 10, 16, s["inp"]["m1"].astype(np.float64),
                                    s["inp"]["beta"].astype(np.float64), first_wave=fw, growth=g,
-                                   amb=H.AMB["exact"], with_amb=True)
+                                   amb=H.AMB["exact"], with_amb=True, norm_eps=H.NORM_EPS)
     out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, first_wave=fw, growth=g, want=("stats",))
     assert out["status"] == 0
     parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb_d=ad)
@@ -174,7 +175,7 @@ def test_final_test_on_completed_distance(G, tiny_pre):
     pr = oidx.probe(oidx.rotate_queries(s["Q"]), 8)
     args = (oidx, s["Q"], pr, 8, 10, 16, s["inp"]["m1"].astype(np.float64), s["inp"]["beta"].astype(np.float64))
     ids, d, st, ad = search.search(*args, first_wave=2, amb=H.AMB["exact"], final_rel=search.FINAL_REL,
-                                   with_amb=True)
+                                   with_amb=True, norm_eps=H.NORM_EPS)
     out = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, first_wave=2, final_test=True,
                        want=("stats",))
     off = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, first_wave=2, want=("stats",))
@@ -199,9 +200,10 @@ def test_ragged_K_and_nprobe(G, tiny_pre):
         assert np.all(out["ids"][b, K[b]:] == -1)
 
 
+@pytest.mark.parametrize("kernel", ["tensor", "cuda"])
 @pytest.mark.parametrize("dtype,delta_d", [("f32", 8), ("f32", 32), ("bf16", 8), ("bf16", 16),
                                            ("bf16", 32), ("fp8", 8), ("fp8", 16), ("fp8", 32)])
-def test_slab_precisions_and_step_widths_strict(G, dtype, delta_d):
+def test_slab_precisions_and_step_widths_strict(G, dtype, delta_d, kernel):
     # pre-rotated inputs: both sides quantise the same FP32 values
     X, Q, T, cfg = synth.workload("tiny", n_train=600)
     inp = H.oracle_inputs(X, T, cfg["nlist"], K=10, nprobe=8, delta_d=delta_d, dtype=dtype, n_train=600,
@@ -210,7 +212,7 @@ def test_slab_precisions_and_step_widths_strict(G, dtype, delta_d):
     s = dict(inp=inp)
     Qr = inp["rot"](Q)
     ids, d, st, pr, ad = _oracle(s, Qr, 10, 8, delta_d=delta_d, dtype_amb="exact")
-    out = H.gpu_search(G, idx, Qr, 10, 8, delta_d, probe_in=pr, want=("stats",))
+    out = H.gpu_search(G, idx, Qr, 10, 8, delta_d, probe_in=pr, want=("stats",), scan_kernel=kernel)
     parity.check(out["ids"], out["dists"], ids, d, inp["X"], Qr, 10, amb_d=ad)
     un = st[:, 4] == 0
     assert np.array_equal(out["stats"][un], st[un, :4])

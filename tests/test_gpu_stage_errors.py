@@ -69,7 +69,7 @@ def test_stage_errors_against_fp64(G):
     assert rel.max() < 2e-6
     # result: ids equal to the oracle's at every rank below amb_d (device rotation)
     oi, od, st, ad = search.search(oidx, Q, pr, 8, 10, 16, inp["m1"].astype(np.float64),
-                                   inp["beta"].astype(np.float64), amb=H.AMB["f32"], with_amb=True,
+                                   inp["beta"].astype(np.float64), amb=H.AMB["f32"], with_amb=True, norm_eps=H.NORM_EPS,
                                    qdev_eps=inp["qdev"])
     checked, total = parity.check(ids, d, oi, od, X, Q, 10, amb_d=ad)
     report["ids_identical_queries"] = float(np.mean(np.all(ids == oi, axis=1)))
