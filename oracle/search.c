@@ -219,7 +219,12 @@ static int estimate_and_test(const double* qr, const double* qdev, const double*
             double e = (xdev ? xdev[j] : 0.0) + (qdev ? qdev[j] : 0.0);
             f += 2.0 * fabs(t) * e + e * e;
         }
+        if (ne > 0.0) {
+            qn += qr[j] * qr[j];
+            xn += xs[j] * xs[j];
+        }
     }
+    f += ne * (double)(D > 16 ? D : 16) * (qn + xn);
     if (isfinite(final_rel)) {
         double T[3];
         for (int i = 0; i < 3; i++) {

@@ -176,6 +176,255 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(IndexView ix, W
     }
 }
 
+// ------------------------------------------------------------ merge, K <= 128
+// The top-K of a query (K <= 128) kept in registers: 128 entries per warp,
+// entry e = 32 r + lane in slot r of lane `lane`, ordered by (distance, id).
+// New candidates are streamed in chunks of up to 128 -- only those that can
+// still enter, i.e. not above the current K-th entry -- each chunk sorted by
+// a bitonic network (shuffles across lanes, swaps across slots) and merged
+// with the top by taking the elementwise minimum with the reversed chunk
+// (a bitonic sequence holding the 128 smallest) and sorting that.
+constexpr int kM128Warps = 8;
+
+struct Ent {
+    float d;
+    long long id;
+};
+__device__ __forceinline__ bool ent_less(const Ent& a, const Ent& b) { return a.d < b.d || (a.d == b.d && a.id < b.id); }
+__device__ __forceinline__ Ent shfl_xor_ent(const Ent& x, int m) {
+    Ent y;
+    y.d = __shfl_xor_sync(0xffffffffu, x.d, m);
+    y.id = __shfl_xor_sync(0xffffffffu, x.id, m);
+    return y;
+}
+__device__ __forceinline__ Ent shfl_ent(const Ent& x, int src) {
+    Ent y;
+    y.d = __shfl_sync(0xffffffffu, x.d, src);
+    y.id = __shfl_sync(0xffffffffu, x.id, src);
+    return y;
+}
+
+// Entry e of the 128 (slot e / 32 of lane e % 32), to every lane; the slot
+// is chosen with selects, not an indexed register array.
+__device__ __forceinline__ Ent entry_at(const Ent (&v)[4], int e) {
+    const int r = e >> 5;
+    Ent x = v[0];
+    if (r == 1) x = v[1];
+    if (r == 2) x = v[2];
+    if (r == 3) x = v[3];
+    return shfl_ent(x, e & 31);
+}
+
+// One compare-exchange level (distance j) of a bitonic network over the 128
+// entries; `up(e)` tells whether the block containing entry e sorts upward.
+template <class Up>
+__device__ __forceinline__ void bitonic_level(Ent (&v)[4], int j, int lane, Up up) {
+    if (j >= 32) {
+        const int js = j >> 5;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int p = r ^ js;
+            if (p > r) {
+                const bool asc = up(r * 32 + lane);
+                const bool sw = asc ? ent_less(v[p], v[r]) : ent_less(v[r], v[p]);
+                if (sw) {
+                    const Ent t = v[r];
+                    v[r] = v[p];
+                    v[p] = t;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = r * 32 + lane;
+            const Ent o = shfl_xor_ent(v[r], j);
+            const bool lower = (lane & j) == 0;
+            const bool asc = up(e);
+            // the lower entry of an upward pair keeps the smaller one
+            const bool take_min = lower == asc;
+            const bool o_less = ent_less(o, v[r]);
+            if (take_min ? o_less : !o_less && (o.d != v[r].d || o.id != v[r].id)) v[r] = o;
+        }
+    }
+}
+
+__device__ __forceinline__ void bitonic_sort128(Ent (&v)[4], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 128; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) bitonic_level(v, j, lane, [k](int e) { return (e & k) == 0; });
+}
+
+constexpr int kM128Bins = 512;
+
+__global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix, WaveView wv, int w) {
+    __shared__ float s_d[kM128Warps][128];
+    __shared__ long long s_i[kM128Warps][128];
+    __shared__ int s_h[kM128Warps][kM128Bins];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * kM128Warps + warp;
+    if (q >= wv.B) return;
+    const int64_t* co = wv.cand_off + (int64_t)w * (wv.B + 1);
+    const int64_t off = co[q], cap = co[q + 1] - off;
+    const int cnt = (int)((int64_t)wv.cand_cnt[q] < cap ? (int64_t)wv.cand_cnt[q] : cap);
+    const int K = wv.K[q];
+    if (cnt == 0 || K < 1 || K > wv.Kmax) {
+        if (lane == 0) wv.cand_cnt[q] = 0;
+        return;
+    }
+    const float* cd = wv.cand_d + off;
+    const int32_t* cp = wv.cand_pos + off;
+    float* td = wv.top_d + q * wv.Kmax;
+    int64_t* ti = wv.top_id + q * wv.Kmax;
+    const int cur = wv.top_n[q];
+    Ent a[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = r * 32 + lane;
+        a[r].d = e < cur ? td[e] : INFINITY;
+        a[r].id = e < cur ? (long long)ti[e] : LLONG_MAX;
+    }
+    int total = cur;  // entries held (up to 128)
+    // Many new candidates: only the K smallest of them can enter.  Their
+    // distances are binned linearly between their minimum and maximum; the
+    // bins up to the one where the count reaches K hold them all, and only
+    // those candidates are streamed below (bin(d) is monotone in d).
+    float lo = 0.f, scale = 0.f;
+    int kbin = kM128Bins;  // no bin filter
+    if (cnt > K) {
+        float mn = INFINITY, mx = -INFINITY;
+        for (int i = lane; i < cnt; i += 32) {
+            const float d = cd[i];
+            mn = fminf(mn, d);
+            mx = fmaxf(mx, d);
+        }
+        for (int o = 16; o; o >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (mx > mn && isfinite(mx)) {
+            lo = mn;
+            scale = (float)kM128Bins / (mx - mn);
+            int* h = s_h[warp];
+            for (int b = lane; b < kM128Bins; b += 32) h[b] = 0;
+            __syncwarp();
+            for (int i = lane; i < cnt; i += 32)
+                atomicAdd(&h[min(kM128Bins - 1, (int)((cd[i] - lo) * scale))], 1);
+            __syncwarp();
+            constexpr int PER = kM128Bins / 32;  // bins per lane, contiguous
+            int hs[PER], sum = 0;
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                hs[u] = h[lane * PER + u];
+                sum += hs[u];
+            }
+            int incl = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int excl = incl - sum;
+            const unsigned hit = __ballot_sync(0xffffffffu, excl < K && incl >= K);
+            const int src = __ffs(hit) - 1;
+            int kb = 0;
+            if (lane == src) {
+                int c = excl;
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    c += hs[u];
+                    if (c >= K) { kb = lane * PER + u; break; }
+                }
+            }
+            kbin = __shfl_sync(0xffffffffu, kb, src);
+        }
+    }
+    int i0 = 0;
+    while (i0 < cnt) {
+        // the current K-th entry bounds what can still enter
+        Ent kth;
+        kth.d = INFINITY;
+        kth.id = LLONG_MAX;
+        if (total >= K) kth = entry_at(a, K - 1);
+        // gather up to 128 candidates that are not above the K-th entry
+        int m = 0;
+        for (; i0 < cnt && m < 128; i0 += 32) {
+            const int i = i0 + lane;
+            Ent x;
+            x.d = INFINITY;
+            x.id = LLONG_MAX;
+            bool keep = false;
+            if (i < cnt) {
+                x.d = cd[i];
+                keep = x.d <= kth.d && (kbin == kM128Bins || min(kM128Bins - 1, (int)((x.d - lo) * scale)) <= kbin);
+                if (keep) {
+                    x.id = (long long)ix.ids[cp[i]];
+                    keep = !ent_less(kth, x);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            const int pos = m + __popc(bal & lanemask_lt());
+            if (keep && pos < 128) {
+                s_d[warp][pos] = x.d;
+                s_i[warp][pos] = x.id;
+            }
+            const int got = __popc(bal);
+            if (m + got > 128) {
+                // the chunk is full: leave the rest of these 32 for the next round
+                const int take = 128 - m;
+                // rank of the (take+1)-th kept lane: resume there
+                int seen = 0, resume = 32;
+                for (int l2 = 0; l2 < 32; ++l2) {
+                    if ((bal >> l2) & 1u) {
+                        if (seen == take) { resume = l2; break; }
+                        ++seen;
+                    }
+                }
+                m = 128;
+                i0 += resume;
+                break;
+            }
+            m += got;
+        }
+        __syncwarp();
+        if (m == 0) break;
+        Ent b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = r * 32 + lane;
+            b[r].d = e < m ? s_d[warp][e] : INFINITY;
+            b[r].id = e < m ? s_i[warp][e] : LLONG_MAX;
+        }
+        __syncwarp();
+        bitonic_sort128(b, lane);
+        // a ascending, b reversed descending: the elementwise minimum is a
+        // bitonic sequence of the 128 smallest of both
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const Ent br = shfl_ent(b[3 - r], 31 - lane);
+            if (ent_less(br, a[r])) a[r] = br;
+        }
+#pragma unroll
+        for (int j = 64; j > 0; j >>= 1) bitonic_level(a, j, lane, [](int) { return true; });
+        total = min(128, total + m);
+    }
+    const int n_out = min(K, total);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = r * 32 + lane;
+        if (e < n_out) {
+            td[e] = a[r].d;
+            ti[e] = a[r].id;
+        }
+    }
+    if (lane == 0) {
+        wv.top_n[q] = n_out;
+        wv.cand_cnt[q] = 0;
+    }
+    const Ent kth = entry_at(a, K - 1);
+    if (lane == 0) wv.tau[q] = n_out == K ? kth.d : INFINITY;
+}
+
 __global__ void output_kernel(WaveView wv, int64_t* ids, float* dists, const int64_t* offsets) {
     const int64_t q = blockIdx.x;
     const int K = wv.K[q];
@@ -495,6 +744,10 @@ cudaError_t launch_wave_scan(const IndexView& ix, const WaveView& wv, int w, boo
 
 cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStream_t st) {
     if (wv.B == 0) return cudaSuccess;
+    if (wv.Kmax <= 128) {
+        merge128_kernel<<<(unsigned)ceil_div(wv.B, kM128Warps), kM128Warps * 32, 0, st>>>(ix, wv, w);
+        return cudaGetLastError();
+    }
     const int smem = kMergeWarps * (2 * wv.Kmax + kMergeChunk) * (int)(sizeof(float) + sizeof(long long));
     static int configured = 0;
     if (smem > configured) {

@@ -90,10 +90,12 @@ cudaError_t launch_wave_scan_res(const IndexView& ix, const WaveView& wv, int w,
 cudaError_t launch_res_terms(const float* qrot, int64_t B, int32_t D, int32_t Dpad, const float* var,
                              int delta_d, int S, float m, float* res_q, cudaStream_t st);
 // The tensor-core estimate-and-prune scan of the learned test (scan_tc.cu):
-// units of up to kTcRows candidates x 128 queries, nsteps tested steps.
+// units of up to kTcRows candidates x 128 queries, nsteps steps (the last
+// one the final test on the completed distance when final_test).
 bool tc_scan_supported(int delta_d);
+int tc_scan_qmax(int delta_d);  // queries per unit of the tensor-core scan
 cudaError_t launch_wave_scan_tc(const IndexView& ix, const WaveView& wv, int w, int delta_d, const float* m1,
-                                const float* beta, int nsteps, int parts, cudaStream_t st);
+                                const float* beta, int nsteps, int parts, bool final_test, cudaStream_t st);
 cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStream_t st);
 cudaError_t launch_output(const WaveView& wv, int64_t* ids, float* dists,
                           const int64_t* offsets, cudaStream_t st);

@@ -8,8 +8,8 @@
 // result queue whose largest entry is tau (Section I).
 //
 // Here a work unit is (bucket l, tile of up to 128 candidates, group of up
-// to 128 queries probing l in the wave), and the partial distances of the
-// whole tile x group are one dense contraction per step:
+// to QW = 128 queries probing l in the wave), and the partial distances of
+// the whole tile x group are one dense contraction per step:
 //   dis'_s(q, x) = ||q_{<d}||^2 + ||x_{<d}||^2 - 2 <q_{<d}, x_{<d}>,  d = s Delta_d,
 // with the cumulative dot product accumulated step by step in tensor memory
 // (M = 128 candidates, N = the group's queries rounded up to 16, K = 8 per
@@ -21,25 +21,28 @@
 //  - The query operand is gathered by the threads (thread i loads query i's
 //    step values, splits them, stores them in the canonical layout) while
 //    they also sum the squares of their query's values.
-//  - One thread issues the MMAs and commits to an mbarrier; every thread
-//    then reads its candidate's row of the accumulator (tcgen05.ld) and
-//    tests every (candidate, query) pair of the group:
+//  - One thread issues the MMAs and commits to an mbarrier.  A CTA has QW
+//    threads: warp w reads accumulator lanes (candidates) 32 (w % 4) ..
+//    32 (w % 4) + 31 and columns (queries) 128 (w / 4) .. 128 (w / 4) + 127
+//    (tcgen05.ld), and each thread tests its candidate against those
+//    queries:
 //      m1 dis' + beta - tau = m1 ||x||^2 + (m1 ||q||^2 + beta - tau) - 2 m1 <q, x>  > 0,
 //    keeping one alive bit per pair in registers.
-//  - After the last tested step the surviving pairs are listed per warp in
-//    shared memory and get the exact FP32 distance, one lane each.
+//  - With the final test, one more step completes the rotated distance and
+//    a pair is kept iff dis'_S <= (sqrt(tau) + e_x)^2 (1 + kFinalRel).
+//  - After the last step the surviving pairs are listed per warp in shared
+//    memory and get the exact FP32 distance, one lane each.
 // Every device wait is bounded (about 2 s, then DADE_ETIMEOUT).
 #include "scan_steps.cuh"
 
 namespace dade {
 namespace {
 
-constexpr int kTcQ = 128;            // queries per unit at most (MMA N)
-constexpr int kChunkF = 1024;        // floats per 4 KB operand chunk (128 rows x 8 dims)
+constexpr int kChunkF = 1024;        // floats per 4 KB candidate-operand chunk (128 rows x 8 dims)
 constexpr uint32_t kTcLBO = 128;     // bytes between the two K halves of a chunk
 constexpr uint32_t kTcSBO = 256;     // bytes between 8-row groups
 
-// offset (floats) of element (row r, dim j) in a chunk
+// offset (floats) of element (row r, dim j) in a chunk (of any row count)
 __device__ __forceinline__ int chunk_off(int r, int j) { return (r >> 3) * 64 + (j >> 2) * 32 + (r & 7) * 4 + (j & 3); }
 
 // tcgen05 shared memory descriptor of a chunk: no swizzle, version 1.
@@ -96,37 +99,77 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int32_
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-template <int NBLK, int PARTS>
-constexpr int tc_smem_bytes() {
-    // two candidate-operand buffers, one query-operand buffer, alignment slack
-    return (2 * NBLK * PARTS + 2 * NBLK) * 4096 + 1024;
+// exact_distance with eight blocks' loads in flight at a time (the same
+// arithmetic: block sums added in block order).
+__device__ __forceinline__ float exact_distance8(const float* xo, int64_t npad, const float* qp, int nb) {
+    float d = 0.f;
+    const int64_t stride = npad * kBlock;
+    int b = 0;
+    for (; b + 8 <= nb; b += 8) {
+        float x[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) load8_ro(xo + (int64_t)(b + i) * stride, x[i]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float q[8];
+            load_q8(qp + (b + i) * kBlock, q);
+            d += block_sq(q, x[i]);
+        }
+    }
+    for (; b < nb; ++b) {
+        float x0[8], q0[8];
+        load8_ro(xo + (int64_t)b * stride, x0);
+        load_q8(qp + b * kBlock, q0);
+        d += block_sq(q0, x0);
+    }
+    return d;
 }
 
-template <int NBLK, int PARTS>
-__global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, WaveView wv, int w,
-                                                                  const float* __restrict__ m1,
-                                                                  const float* __restrict__ beta, int nsteps) {
-    static_assert(kScanThreads == kTcRows && kTcRows == kTcQ, "one thread per candidate row and per query row");
-    constexpr int ACH = NBLK * PARTS;  // chunks per candidate-operand buffer
-    constexpr int NW = kTcQ / 32;      // alive words per thread
+// Queries per unit: 128 (four CTAs of four warps per SM, so that one CTA's
+// tests overlap the others' MMAs and copies; 256-query units with eight
+// warps and two CTAs per SM measured slower on the SIFT-shaped workload).
+template <int NBLK> constexpr int tc_qw() { return 128; }
+
+template <int NBLK, int PARTS, int QW>
+constexpr int tc_smem_bytes() {
+    // two candidate-operand buffers, one query-operand buffer (QW rows per
+    // chunk), alignment slack
+    return (2 * NBLK * PARTS) * 4096 + 2 * NBLK * QW * 32 + 1024;
+}
+
+// With FIN the last step (k = nsteps - 1) completes the rotated distance
+// and its test is the one on the whole distance: a candidate is kept iff
+// dis'_S <= (sqrt(tau) + e_x)^2 (1 + kFinalRel), e_x its stored vector's
+// quantisation error (0 for FP32 slabs).
+template <int NBLK, int PARTS, int QW, bool FIN>
+__global__ void __launch_bounds__(QW, 512 / QW) tc_scan_kernel(IndexView ix, WaveView wv, int w,
+                                                               const float* __restrict__ m1,
+                                                               const float* __restrict__ beta, int nsteps) {
+    static_assert(QW == 128 || QW == 256, "one or two warps per accumulator lane quarter");
+    constexpr int ACH = NBLK * PARTS;       // chunks per candidate-operand buffer
+    constexpr int BCH = QW * kBlock;        // floats per query-operand chunk (QW rows x 8 dims)
+    constexpr int NW = 4;                   // alive words per thread: 128 columns
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) uint64_t bar_a[2];
     __shared__ __align__(8) uint64_t bar_m;
     __shared__ uint32_t s_taddr;
     __shared__ int s_unit, s_fail;
     __shared__ int4 s_desc;
-    __shared__ int s_q[kTcQ];
-    __shared__ float s_tau[kTcQ];
-    __shared__ __align__(16) float s_a[2][kTcQ];
-    __shared__ unsigned s_st[kTcQ * 4];
+    __shared__ int s_q[QW];
+    __shared__ float s_tau[QW];
+    __shared__ __align__(16) float s_a[2][QW];
+    __shared__ __align__(16) float s_rt[FIN ? QW : 1];  // sqrt(tau) per query (the final test)
+    __shared__ unsigned s_st[QW * 4];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tsm) + 1023) & ~uintptr_t(1023));
     float* abuf = reinterpret_cast<float*>(base);
     float* bbuf = abuf + 2 * ACH * kChunkF;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row = (warp & 3) * 32 + lane;   // this thread's candidate (accumulator lane)
+    const int cb0 = (warp >> 2) * 128;        // its first column (query)
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
-                     "r"(kTcQ)
+                     "r"(QW)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -141,7 +184,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_taddr;
-    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb0;
 
     uint32_t ph_a = 0u, ph_m = 0u;  // parity to wait for: bit b for bar_a[b]; bar_m
     const int total = wv.unit_off[(int64_t)w * (ix.nlist + 1) + ix.nlist];
@@ -169,6 +212,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
         const Unit un = unpack_unit(s_desc);
         const int l = un.l, t = un.t, nq = un.nq, nt = un.nt;
         const int ncols = (nq + 15) & ~15;
+        const int mycols = min(128, max(0, ncols - cb0));   // this warp's columns
+        const int myq = min(128, max(0, nq - cb0));
         const int64_t slot_l = ix.list_slot[l];
         const int64_t npad = ix.list_slot[l + 1] - slot_l;
         const int32_t slot0 = (int32_t)(slot_l + (int64_t)t * kTcRows);
@@ -190,16 +235,18 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
             tq = wv.tau[q];
             s_q[tid] = q;
             s_tau[tid] = tq;
+            if (FIN) s_rt[tid] = sqrtf(tq);
             qsrc = wv.qrot + (int64_t)q * ix.Dpad;
         }
+        const float ex = (FIN && ix.eps && row < nt) ? ix.eps[slot0 + row] : 0.f;
         if (want_stats)
-            for (int i = tid; i < nq * 4; i += kScanThreads) s_st[i] = (i & 3) == 0 ? (unsigned)nt : 0u;
-        // alive bit j of word c4: the pair (this thread's candidate, query 32 c4 + j)
+            for (int i = tid; i < nq * 4; i += QW) s_st[i] = (i & 3) == 0 ? (unsigned)nt : 0u;
+        // alive bit j of word c4: the pair (this thread's candidate, query cb0 + 32 c4 + j)
         uint32_t alive[NW];
 #pragma unroll
         for (int c4 = 0; c4 < NW; ++c4) {
-            const int lo = c4 * 32, n = min(32, max(0, nq - lo));
-            alive[c4] = (tid < nt && n > 0) ? (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) : 0u;
+            const int n = min(32, max(0, myq - c4 * 32));
+            alive[c4] = (row < nt && n > 0) ? (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) : 0u;
         }
         float qv[NBLK * kBlock];
         auto load_q = [&](int k) {
@@ -220,7 +267,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
         bool mma_failed = false;
         for (; k < nsteps; ++k) {
             const int b0 = k * NBLK, nbk = min(NBLK, nb - b0);
-            const float mk = m1[k], bk = beta[k];
+            const bool fin_k = FIN && k == nsteps - 1;
+            const float mk = fin_k ? 1.f : m1[k], bk = fin_k ? 0.f : beta[k];
             // 1. the step's query operand, the query norms and the test constants
             if (tid < nq) {
 #pragma unroll
@@ -234,15 +282,15 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
                             m[j] = tf32_rna(x - h[j]);
                             qn = fmaf(x, x, qn);
                         }
-                        float* ch = bbuf + (bb * 2) * kChunkF + chunk_off(tid, 0);
-                        float* cm = ch + kChunkF;
+                        float* ch = bbuf + (bb * 2) * BCH + chunk_off(tid, 0);
+                        float* cm = ch + BCH;
                         *reinterpret_cast<float4*>(ch) = make_float4(h[0], h[1], h[2], h[3]);
                         *reinterpret_cast<float4*>(ch + 32) = make_float4(h[4], h[5], h[6], h[7]);
                         *reinterpret_cast<float4*>(cm) = make_float4(m[0], m[1], m[2], m[3]);
                         *reinterpret_cast<float4*>(cm + 32) = make_float4(m[4], m[5], m[6], m[7]);
                     }
                 }
-                s_a[k & 1][tid] = fmaf(mk, qn, bk) - tq;
+                s_a[k & 1][tid] = fin_k ? qn : fmaf(mk, qn, bk) - tq;
             }
             fence_proxy_async();
             // 2. the candidate operand of the step has landed
@@ -267,7 +315,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
                 for (int bb = 0; bb < NBLK; ++bb) {
                     if (bb < nbk) {
                         const uint32_t ah = a0 + (uint32_t)(bb * PARTS) * 4096u, am = ah + 4096u;
-                        const uint32_t bh = bq + (uint32_t)(bb * 2) * 4096u, bm = bh + 4096u;
+                        const uint32_t bh = bq + (uint32_t)(bb * 2) * (BCH * 4u), bm = bh + BCH * 4u;
                         tc_mma(tmem, tc_desc(ah), tc_desc(bh), idesc, (k > 0 || bb > 0) ? 1u : 0u);
                         tc_mma(tmem, tc_desc(ah), tc_desc(bm), idesc, 1u);
                         if (PARTS > 1) tc_mma(tmem, tc_desc(am), tc_desc(bh), idesc, 1u);
@@ -279,8 +327,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
             }
             // 4. meanwhile: the next step's query values, this step's candidate norms
             if (k + 1 < nsteps) load_q(k + 1);
-            if (tid < nt) {
-                const float* ar = abuf + (k & 1) * ACH * kChunkF + chunk_off(tid, 0);
+            if (row < nt && mycols > 0) {
+                const float* ar = abuf + (k & 1) * ACH * kChunkF + chunk_off(row, 0);
 #pragma unroll
                 for (int bb = 0; bb < NBLK; ++bb) {
                     if (bb < nbk) {
@@ -310,20 +358,22 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
                 if (lane == 0) s_fail = 1;
             }
             tc_fence_after();
-            // 6. the tests of every (candidate, query) pair
+            // 6. the tests of every (candidate, query) pair of this warp's columns
 #pragma unroll
             for (int c4 = 0; c4 < NW; ++c4) {
-                if (okm && c4 * 32 < ncols) {
+                if (okm && c4 * 32 < mycols) {
                     uint32_t v[32];
-                    if (ncols - c4 * 32 >= 32) tmem_ld32(tmem_row + (uint32_t)(c4 * 32), v);
+                    if (mycols - c4 * 32 >= 32) tmem_ld32(tmem_row + (uint32_t)(c4 * 32), v);
                     else tmem_ld16(tmem_row + (uint32_t)(c4 * 32), v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     uint32_t newly = 0u;
-                    if (alive[c4]) {
-                        const float4* ap = reinterpret_cast<const float4*>(&s_a[k & 1][c4 * 32]);
+                    if (alive[c4] && !fin_k) {
+                        // the learned test: m1 dis' + beta - tau > 0
+                        const float4* ap = reinterpret_cast<const float4*>(&s_a[k & 1][cb0 + c4 * 32]);
                         uint32_t prune = 0u;
 #pragma unroll
                         for (int j4 = 0; j4 < 8; ++j4) {
+                            if (c4 * 32 + j4 * 4 >= myq) break;  // the group's columns only
                             const float4 a4 = ap[j4];
                             const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
@@ -335,13 +385,33 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
                         }
                         newly = alive[c4] & prune;
                         alive[c4] &= ~prune;
+                    } else if (FIN && alive[c4]) {
+                        // the test on the completed rotated distance
+                        const float4* ap = reinterpret_cast<const float4*>(&s_a[k & 1][cb0 + c4 * 32]);
+                        const float4* rp = reinterpret_cast<const float4*>(&s_rt[cb0 + c4 * 32]);
+                        uint32_t prune = 0u;
+#pragma unroll
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            if (c4 * 32 + j4 * 4 >= myq) break;
+                            const float4 a4 = ap[j4], r4 = rp[j4];
+                            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int j = j4 * 4 + i;
+                                const float r = rv[i] + ex;
+                                const float dis = fmaf(-2.f, __uint_as_float(v[j]), xn + av[i]);
+                                prune |= (dis > r * r * (1.f + kFinalRel) ? 1u : 0u) << j;
+                            }
+                        }
+                        newly = alive[c4] & prune;
+                        alive[c4] &= ~prune;
                     }
                     if (want_stats) {
                         for (int j = 0; j < 32; ++j) {
                             const int np = __popc(__ballot_sync(0xffffffffu, (newly >> j) & 1u));
                             if (lane == 0 && np) {
-                                atomicAdd(&s_st[(c4 * 32 + j) * 4 + 1], (unsigned)np);
-                                atomicAdd(&s_st[(c4 * 32 + j) * 4 + 3], (unsigned)np * dims_k);
+                                atomicAdd(&s_st[(cb0 + c4 * 32 + j) * 4 + 1], (unsigned)np);
+                                atomicAdd(&s_st[(cb0 + c4 * 32 + j) * 4 + 3], (unsigned)np * dims_k);
                             }
                         }
                     }
@@ -361,7 +431,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
         unsigned long long ex_bytes = 0;
 #pragma unroll
         for (int c4 = 0; c4 < NW; ++c4) {
-            if (c4 * 32 >= ncols) continue;
+            if (c4 * 32 >= mycols) continue;
             uint32_t bits = alive[c4];
             const int cnt = __popc(bits);
             int incl = cnt;
@@ -376,19 +446,19 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
             while (bits) {
                 const int j = __ffs(bits) - 1;
                 bits &= bits - 1u;
-                list[pos++] = (uint16_t)(((c4 * 32 + j) << 8) | tid);
+                list[pos++] = (uint16_t)(((cb0 + c4 * 32 + j) << 7) | row);
             }
             __syncwarp();
             for (int b = 0; b < tot; b += 32) {
                 const int i = b + lane;
                 const bool valid = i < tot;
                 const int key = valid ? list[i] : 0;
-                const int g = key >> 8, c = key & 255;
+                const int g = key >> 7, c = key & 127;
                 const int q = s_q[g];
                 float d = 0.f;
                 if (valid)
-                    d = exact_distance(ix.orig + slot_l * ix.Dpad + ((int64_t)t * kTcRows + c) * kBlock, npad,
-                                       wv.qpad + (int64_t)q * ix.Dpad, nb);
+                    d = exact_distance8(ix.orig + slot_l * ix.Dpad + ((int64_t)t * kTcRows + c) * kBlock, npad,
+                                        wv.qpad + (int64_t)q * ix.Dpad, nb);
                 append_any(wv, w, q, valid && d <= s_tau[g], d, slot0 + c, lane);
                 if (want_stats && valid) {
                     atomicAdd(&s_st[g * 4 + 2], 1u);
@@ -401,7 +471,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
         if (wv.staged_bytes && lane == 0 && ex_bytes) atomicAdd(wv.staged_bytes, ex_bytes);
         __syncthreads();
         if (want_stats)
-            for (int i = tid; i < nq * 4; i += kScanThreads)
+            for (int i = tid; i < nq * 4; i += QW)
                 if (s_st[i])
                     atomicAdd((unsigned long long*)&wv.stats[(int64_t)s_q[i >> 2] * 4 + (i & 3)],
                               (unsigned long long)s_st[i]);
@@ -411,42 +481,43 @@ __global__ void __launch_bounds__(kScanThreads, 4) tc_scan_kernel(IndexView ix, 
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcQ) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(QW) : "memory");
     }
 }
 
-template <int NBLK, int PARTS>
+template <int NBLK, int PARTS, bool FIN>
 cudaError_t launch_tc_t(const IndexView& ix, const WaveView& wv, int w, const float* m1, const float* beta,
                         int nsteps, cudaStream_t st) {
+    constexpr int QW = tc_qw<NBLK>();
     static int grid = 0, smem = 0;
-    auto kern = tc_scan_kernel<NBLK, PARTS>;
+    auto kern = tc_scan_kernel<NBLK, PARTS, QW, FIN>;
     if (grid == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        // each CTA holds kTcQ of the SM's 512 tensor-memory columns for its
-        // whole life: request enough shared memory that at most
-        // 512 / kTcQ CTAs are resident on an SM, so that no allocation waits
-        int bytes = tc_smem_bytes<NBLK, PARTS>();
+        // each CTA holds QW of the SM's 512 tensor-memory columns for its
+        // whole life: request enough shared memory that at most 512 / QW
+        // CTAs are resident on an SM, so that no allocation waits
+        int bytes = tc_smem_bytes<NBLK, PARTS, QW>();
         for (;;) {
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
             if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kScanThreads, bytes);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, QW, bytes);
             if (e != cudaSuccess) return e;
-            if (per <= 512 / kTcQ) break;
+            if (per <= 512 / QW) break;
             bytes += 8192;
         }
         smem = bytes;
         // the occupancy query can report fewer resident CTAs than registers and
         // shared memory allow (it does not know how much tensor memory a CTA
-        // takes); the scan is persistent, so a launch of 512 / kTcQ CTAs per
-        // SM is safe either way: CTAs that are not resident start later and
-        // find the work taken
-        grid = sms * (512 / kTcQ);
+        // takes); the scan is persistent, so a launch of 512 / QW CTAs per SM
+        // is safe either way: CTAs that are not resident start later and find
+        // the work taken
+        grid = sms * (512 / QW);
     }
-    kern<<<grid, kScanThreads, smem, st>>>(ix, wv, w, m1, beta, nsteps);
+    kern<<<grid, QW, smem, st>>>(ix, wv, w, m1, beta, nsteps);
     return cudaGetLastError();
 }
 
@@ -454,17 +525,21 @@ cudaError_t launch_tc_t(const IndexView& ix, const WaveView& wv, int w, const fl
 
 bool tc_scan_supported(int delta_d) { return delta_d == 8 || delta_d == 16 || delta_d == 32; }
 
+int tc_scan_qmax(int delta_d) { return delta_d == 8 ? tc_qw<1>() : delta_d == 16 ? tc_qw<2>() : tc_qw<4>(); }
+
 cudaError_t launch_wave_scan_tc(const IndexView& ix, const WaveView& wv, int w, int delta_d, const float* m1,
-                                const float* beta, int nsteps, int parts, cudaStream_t st) {
-    if (parts == 1) {
-        if (delta_d == 8) return launch_tc_t<1, 1>(ix, wv, w, m1, beta, nsteps, st);
-        if (delta_d == 16) return launch_tc_t<2, 1>(ix, wv, w, m1, beta, nsteps, st);
-        if (delta_d == 32) return launch_tc_t<4, 1>(ix, wv, w, m1, beta, nsteps, st);
-    } else {
-        if (delta_d == 8) return launch_tc_t<1, 2>(ix, wv, w, m1, beta, nsteps, st);
-        if (delta_d == 16) return launch_tc_t<2, 2>(ix, wv, w, m1, beta, nsteps, st);
-        if (delta_d == 32) return launch_tc_t<4, 2>(ix, wv, w, m1, beta, nsteps, st);
-    }
+                                const float* beta, int nsteps, int parts, bool final_test, cudaStream_t st) {
+#define DADE_TC_CASE(NB, PT)                                                                        \
+    if (delta_d == NB * kBlock && parts == PT)                                                      \
+        return final_test ? launch_tc_t<NB, PT, true>(ix, wv, w, m1, beta, nsteps, st)             \
+                          : launch_tc_t<NB, PT, false>(ix, wv, w, m1, beta, nsteps, st);
+    DADE_TC_CASE(1, 1)
+    DADE_TC_CASE(2, 1)
+    DADE_TC_CASE(4, 1)
+    DADE_TC_CASE(1, 2)
+    DADE_TC_CASE(2, 2)
+    DADE_TC_CASE(4, 2)
+#undef DADE_TC_CASE
     return cudaErrorInvalidValue;
 }
 

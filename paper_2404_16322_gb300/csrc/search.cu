@@ -69,7 +69,7 @@ int n_steps(const dade_index* idx, int32_t delta_d, const dade_search_opts& o) {
 
 // The tensor-core kernel can run the learned test's waves of this search.
 bool tc_eligible(const dade_index* idx, int32_t delta_d, const dade_search_opts& o) {
-    return o.mode == DADE_SCAN_PRUNE && o.estimator == DADE_EST_LEARNED && !o.final_test && idx->tcslab_dev.p &&
+    return o.mode == DADE_SCAN_PRUNE && o.estimator == DADE_EST_LEARNED && idx->tcslab_dev.p &&
            tc_scan_supported(delta_d);
 }
 
@@ -87,8 +87,8 @@ int wave_kernel(const dade_index* idx, int32_t delta_d, const dade_search_opts& 
 }
 
 // Queries per work unit of a wave: the tensor-core kernel takes up to 128
-// (its MMA N), the CUDA-core kernels kG.
-int wave_qgroup(int kernel) { return kernel == WK_TENSOR ? 128 : kG; }
+// or 256 (its MMA N), the CUDA-core kernels kG.
+int wave_qgroup(int kernel, int32_t delta_d) { return kernel == WK_TENSOR ? tc_scan_qmax(delta_d) : kG; }
 
 size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o, char* base, Plan* pl) {
     const int P = o.max_nprobe, Kmax = o.max_K;
@@ -128,7 +128,7 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     int64_t ucap = 0;
     for (int w = 0; w < nw; ++w) {
         const int64_t width = std::max(0, std::min(P, wave_begin(w + 1, f, g)) - wave_begin(w, f, g));
-        const int qg = wave_qgroup(wave_kernel(idx, delta_d, o, w));
+        const int qg = wave_qgroup(wave_kernel(idx, delta_d, o, w), delta_d);
         v.ubase[w] = ucap;
         v.qgroup[w] = qg;
         ucap += (ceil_div(B * width, qg) + std::min<int64_t>(nl, B * width)) * ntile_max;
@@ -179,7 +179,7 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
     }
     if (o.scan_kernel < DADE_KERNEL_AUTO || o.scan_kernel > DADE_KERNEL_TENSOR) return fail(DADE_EINVAL, "bad scan_kernel");
     if (o.scan_kernel == DADE_KERNEL_TENSOR && o.mode == DADE_SCAN_PRUNE && !tc_eligible(idx, delta_d, o))
-        return fail(DADE_ENOTIMPL, "the tensor-core scan runs the learned test without final_test only");
+        return fail(DADE_ENOTIMPL, "the tensor-core scan runs the learned test (tables or ADS) only");
     if (o.test_steps < 0) return fail(DADE_EINVAL, "test_steps < 0");
     if (o.test_steps > 0 && o.final_test && o.mode == DADE_SCAN_PRUNE)
         return fail(DADE_ENOTIMPL, "test_steps with final_test");
@@ -339,7 +339,8 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
                       idx->pq_m, idx->pq_m1, idx->pq_m3, idx->pq_beta};
             DADE_CUDA_TRY(launch_pq_scan(ix, v, w, pv, st));
         } else if (wk == WK_TENSOR) {
-            DADE_CUDA_TRY(launch_wave_scan_tc(ix, v, w, delta_d, m1, beta, v.test_steps, idx->tc_parts, st));
+            DADE_CUDA_TRY(launch_wave_scan_tc(ix, v, w, delta_d, m1, beta, v.final_test ? S : v.test_steps,
+                                              idx->tc_parts, v.final_test != 0, st));
         } else {
             DADE_CUDA_TRY(launch_wave_scan(ix, v, w, wk == WK_EXACT, delta_d, m1, beta, S, st));
         }
