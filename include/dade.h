@@ -287,6 +287,14 @@ typedef struct {
     int32_t scan_kernel;     /* PRUNE mode with the learned test (tables, ADS):  */
                              /* dade_scan_kernel: which kernel runs the waves   */
                              /* whose tau is finite.  0 (auto) = tensor cores.  */
+    int64_t candidate_budget_bytes; /* bound of the candidate buffer (8 bytes  */
+                             /* per candidate a pass can append for a query in */
+                             /* the worst case: the sum of its largest buckets);*/
+                             /* a wave over the bound is scanned in passes of  */
+                             /* fewer probe ranks, all tested against the      */
+                             /* wave's tau (results do not change).  0: 8 GiB. */
+                             /* The bound grows if it would take more than 128 */
+                             /* passes.                                        */
 } dade_search_opts;
 
 /* The estimate-and-prune kernels of the learned test.  DADE_KERNEL_TENSOR:

@@ -266,20 +266,22 @@ def dade_get_correction(idx: Index, delta_d: int):
 
 def _opts(mode, max_K, max_nprobe, first_wave=0, tau=None, probe_in=None, probe_out=None, qrot_out=None,
           stats=None, status=None, workspace=None, wave_growth_log2=0, final_test=False, estimator="learned",
-          res_m=8.0, test_steps=0, scan_kernel="auto"):
+          res_m=8.0, test_steps=0, scan_kernel="auto", candidate_budget_bytes=0):
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     return L.SearchOpts(L.MODE[mode], int(max_K), int(max_nprobe), int(first_wave), _ptr(tau),
                         _ptr(probe_in), _ptr(probe_out), _ptr(qrot_out), _ptr(stats), _ptr(status),
                         _ptr(workspace), ws_bytes, int(wave_growth_log2), int(bool(final_test)),
-                        L.ESTIMATOR[estimator], float(res_m), int(test_steps), L.SCAN_KERNEL[scan_kernel])
+                        L.ESTIMATOR[estimator], float(res_m), int(test_steps), L.SCAN_KERNEL[scan_kernel],
+                        int(candidate_budget_bytes))
 
 
 def dade_search_workspace_size(idx: Index, B: int, delta_d: int, max_K: int, max_nprobe: int,
                                mode: str = "prune", first_wave: int = 0, frozen: bool = False,
                                probe_in: bool = False, wave_growth_log2: int = 0, final_test: bool = False,
-                               estimator: str = "learned", scan_kernel: str = "auto") -> int:
+                               estimator: str = "learned", scan_kernel: str = "auto",
+                               candidate_budget_bytes: int = 0) -> int:
     o = _opts(mode, max_K, max_nprobe, first_wave, wave_growth_log2=wave_growth_log2, final_test=final_test,
-              estimator=estimator, scan_kernel=scan_kernel)
+              estimator=estimator, scan_kernel=scan_kernel, candidate_budget_bytes=candidate_budget_bytes)
     if frozen:
         o.tau_dev = 1  # only its presence matters for sizing
     if probe_in:
@@ -291,7 +293,8 @@ def dade_search(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: in
                 mode: str = "prune", first_wave: int = 0, tau=None, probe_in=None, probe_out=None,
                 qrot_out=None, stats=None, status=None, workspace=None, offsets=None, stream=None,
                 wave_growth_log2: int = 0, final_test: bool = False, estimator: str = "learned",
-                res_m: float = 8.0, test_steps: int = 0, scan_kernel: str = "auto") -> None:
+                res_m: float = 8.0, test_steps: int = 0, scan_kernel: str = "auto",
+                candidate_budget_bytes: int = 0) -> None:
     """Enqueue a search on ``stream`` (a torch.cuda.Stream; default: current).
 
     Q: (B, D) float32 CUDA tensor; K, nprobe: (B,) int32 CUDA tensors; ids
@@ -304,7 +307,8 @@ def dade_search(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: in
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     o = _opts(mode, max_K, max_nprobe, first_wave, tau, probe_in, probe_out, qrot_out, stats, status,
-              workspace, wave_growth_log2, final_test, estimator, res_m, test_steps, scan_kernel)
+              workspace, wave_growth_log2, final_test, estimator, res_m, test_steps, scan_kernel,
+              candidate_budget_bytes)
     _check(library().dade_search(idx.ptr, _ptr(Q), int(Q.shape[0]), _ptr(K), _ptr(nprobe), int(delta_d),
                                  ctypes.byref(o), _ptr(ids), _ptr(dists), _ptr(offsets),
                                  ctypes.c_void_p(s.cuda_stream)))
@@ -315,14 +319,14 @@ def dade_search_noalloc(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, m
                         probe_in=None, probe_out=None, qrot_out=None, stats=None, status=None,
                         offsets=None, stream=None, wave_growth_log2: int = 0, final_test: bool = False,
                         estimator: str = "learned", res_m: float = 8.0, test_steps: int = 0,
-                        scan_kernel: str = "auto") -> None:
+                        scan_kernel: str = "auto", candidate_budget_bytes: int = 0) -> None:
     """dade_search whose scratch is the library's fixed device array: for
     callers that cannot allocate device memory.  Same arguments and results
     as dade_search except that no workspace is passed."""
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     o = _opts(mode, max_K, max_nprobe, first_wave, tau, probe_in, probe_out, qrot_out, stats, status, None,
-              wave_growth_log2, final_test, estimator, res_m, test_steps, scan_kernel)
+              wave_growth_log2, final_test, estimator, res_m, test_steps, scan_kernel, candidate_budget_bytes)
     _check(library().dade_search_noalloc(idx.ptr, _ptr(Q), int(Q.shape[0]), _ptr(K), _ptr(nprobe),
                                          int(delta_d), ctypes.byref(o), _ptr(ids), _ptr(dists), _ptr(offsets),
                                          ctypes.c_void_p(s.cuda_stream)))

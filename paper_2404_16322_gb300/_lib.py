@@ -34,7 +34,7 @@ class SearchOpts(ctypes.Structure):
                 ("qrot_out_dev", c_vp), ("stats_dev", c_vp), ("status_dev", c_vp),
                 ("workspace", c_vp), ("workspace_bytes", c_sz), ("wave_growth_log2", c_i32),
                 ("final_test", c_i32), ("estimator", c_i32), ("res_m", ctypes.c_float),
-                ("test_steps", c_i32), ("scan_kernel", c_i32)]
+                ("test_steps", c_i32), ("scan_kernel", c_i32), ("candidate_budget_bytes", c_i64)]
 
 
 class IndexInfo(ctypes.Structure):

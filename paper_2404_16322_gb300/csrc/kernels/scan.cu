@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(IndexView ix, W
     }
     if (lane == 0) {
         wv.top_n[q] = cur;
-        wv.tau[q] = cur == K ? ad[K - 1] : INFINITY;
+        wv.tau_run[q] = cur == K ? ad[K - 1] : INFINITY;
         wv.cand_cnt[q] = 0;
     }
 }
@@ -185,76 +185,6 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(IndexView ix, W
 // with the top by taking the elementwise minimum with the reversed chunk
 // (a bitonic sequence holding the 128 smallest) and sorting that.
 constexpr int kM128Warps = 8;
-
-struct Ent {
-    float d;
-    long long id;
-};
-__device__ __forceinline__ bool ent_less(const Ent& a, const Ent& b) { return a.d < b.d || (a.d == b.d && a.id < b.id); }
-__device__ __forceinline__ Ent shfl_xor_ent(const Ent& x, int m) {
-    Ent y;
-    y.d = __shfl_xor_sync(0xffffffffu, x.d, m);
-    y.id = __shfl_xor_sync(0xffffffffu, x.id, m);
-    return y;
-}
-__device__ __forceinline__ Ent shfl_ent(const Ent& x, int src) {
-    Ent y;
-    y.d = __shfl_sync(0xffffffffu, x.d, src);
-    y.id = __shfl_sync(0xffffffffu, x.id, src);
-    return y;
-}
-
-// Entry e of the 128 (slot e / 32 of lane e % 32), to every lane; the slot
-// is chosen with selects, not an indexed register array.
-__device__ __forceinline__ Ent entry_at(const Ent (&v)[4], int e) {
-    const int r = e >> 5;
-    Ent x = v[0];
-    if (r == 1) x = v[1];
-    if (r == 2) x = v[2];
-    if (r == 3) x = v[3];
-    return shfl_ent(x, e & 31);
-}
-
-// One compare-exchange level (distance j) of a bitonic network over the 128
-// entries; `up(e)` tells whether the block containing entry e sorts upward.
-template <class Up>
-__device__ __forceinline__ void bitonic_level(Ent (&v)[4], int j, int lane, Up up) {
-    if (j >= 32) {
-        const int js = j >> 5;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int p = r ^ js;
-            if (p > r) {
-                const bool asc = up(r * 32 + lane);
-                const bool sw = asc ? ent_less(v[p], v[r]) : ent_less(v[r], v[p]);
-                if (sw) {
-                    const Ent t = v[r];
-                    v[r] = v[p];
-                    v[p] = t;
-                }
-            }
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int e = r * 32 + lane;
-            const Ent o = shfl_xor_ent(v[r], j);
-            const bool lower = (lane & j) == 0;
-            const bool asc = up(e);
-            // the lower entry of an upward pair keeps the smaller one
-            const bool take_min = lower == asc;
-            const bool o_less = ent_less(o, v[r]);
-            if (take_min ? o_less : !o_less && (o.d != v[r].d || o.id != v[r].id)) v[r] = o;
-        }
-    }
-}
-
-__device__ __forceinline__ void bitonic_sort128(Ent (&v)[4], int lane) {
-#pragma unroll
-    for (int k = 2; k <= 128; k <<= 1)
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) bitonic_level(v, j, lane, [k](int e) { return (e & k) == 0; });
-}
 
 constexpr int kM128Bins = 512;
 
@@ -422,7 +352,7 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
         wv.cand_cnt[q] = 0;
     }
     const Ent kth = entry_at(a, K - 1);
-    if (lane == 0) wv.tau[q] = n_out == K ? kth.d : INFINITY;
+    if (lane == 0) wv.tau_run[q] = n_out == K ? kth.d : INFINITY;
 }
 
 __global__ void output_kernel(WaveView wv, int64_t* ids, float* dists, const int64_t* offsets) {
@@ -457,7 +387,7 @@ __global__ void count_kernel(IndexView ix, WaveView wv) {
             atomicCAS(wv.status, 0, (int)DADE_EINVAL);
             continue;
         }
-        const int wr = r < wv.first_wave ? 0 : 1 + (31 - __clz(r / wv.first_wave)) / wv.wave_shift;
+        const int wr = pass_of_rank(wv, r);
         atomicAdd(&wv.cnt_wl[wr * ix.nlist + l], 1);
         wv.cand_off[(int64_t)wr * (wv.B + 1) + b] += ix.list_size[l];
     }
@@ -472,7 +402,7 @@ __global__ void scatter_kernel(IndexView ix, WaveView wv) {
     for (int r = 0; r < np; ++r) {
         const int l = wv.probes[b * wv.P + r];
         if (l < 0 || l >= ix.nlist) continue;
-        const int wr = r < wv.first_wave ? 0 : 1 + (31 - __clz(r / wv.first_wave)) / wv.wave_shift;
+        const int wr = pass_of_rank(wv, r);
         const int key = wr * ix.nlist + l;
         const int pos = atomicAdd(&wv.fill_wl[key], 1);
         wv.items[wv.off_wl[key] + pos] = (int32_t)b;
@@ -538,7 +468,7 @@ struct LoadUnits {
     const int32_t* cnt;
     const int32_t* size;
     int nlist;
-    int32_t qgroup[16];
+    int32_t qgroup[kMaxPasses];
     __device__ int32_t operator()(int seg, int64_t l) const {
         int c = cnt[(int64_t)seg * nlist + l];
         int s = size[l];
@@ -711,7 +641,7 @@ cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStre
     const int64_t nwl = (int64_t)wv.n_waves * ix.nlist;
     seg_scan_kernel<<<1, 1024, 0, st>>>(LoadI32{wv.cnt_wl}, wv.off_wl, nwl, 0);
     LoadUnits lu{wv.cnt_wl, ix.list_size, ix.nlist, {}};
-    for (int w = 0; w < 16; ++w) lu.qgroup[w] = wv.qgroup[w];
+    for (int w = 0; w < kMaxPasses; ++w) lu.qgroup[w] = wv.qgroup[w];
     seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(lu, wv.unit_off, (int64_t)ix.nlist, (int64_t)ix.nlist + 1);
     seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(LoadCap{wv.cand_off, wv.B + 1}, wv.cand_off, wv.B,
                                                  wv.B + 1);

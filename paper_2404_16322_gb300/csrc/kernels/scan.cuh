@@ -25,9 +25,13 @@ struct IndexView {
     int32_t D, Dpad, nb, nlist, dtype, tc_parts;
 };
 
+// A wave of probe ranks (tested against one tau) is scanned in one or more
+// passes of consecutive ranks; the candidate buffer holds one pass.
+constexpr int kMaxPasses = 128;
+
 struct WaveView {
     int64_t B;
-    int32_t P, Kmax, first_wave, n_waves, wave_shift;
+    int32_t P, Kmax, n_waves;  // n_waves: passes (below)
     int32_t final_test;       // PRUNE: test the completed rotated distance before the exact one
     int32_t est;              // PRUNE: 0 learned tables, 1 the Gaussian-bound (RES) test
     int32_t res_stride;       // S - 1: entries of res_q per query
@@ -38,28 +42,41 @@ struct WaveView {
     const int32_t* probes;    // B x P
     const int32_t* nprobe;    // B
     const int32_t* K;         // B
-    int32_t* cnt_wl;          // n_waves x nlist: queries probing (wave, bucket)
-    int32_t* off_wl;          // n_waves x nlist + 1: exclusive prefix of cnt_wl
-    int32_t* fill_wl;         // n_waves x nlist: scatter cursors
+    int32_t* cnt_wl;          // passes x nlist: queries probing (pass, bucket)
+    int32_t* off_wl;          // passes x nlist + 1: exclusive prefix of cnt_wl
+    int32_t* fill_wl;         // passes x nlist: scatter cursors
     int32_t* items;           // B x P query ids grouped by (wave, bucket)
-    int32_t* unit_off;        // n_waves x (nlist + 1): work units per wave, prefix
+    int32_t* unit_off;        // passes x (nlist + 1): work units per pass, prefix
     int4* units;              // unit descriptors {bucket, tile, first item, nq << 16 | nt}
-    int64_t ubase[16];        // first descriptor of each wave in `units`
-    int32_t qgroup[16];       // queries per unit at most, per wave (the queries probing a
-                              // bucket in a wave are split into balanced groups)
-    int64_t* cand_off;        // n_waves x (B + 1): candidate capacity per query, prefix
-    int32_t* cand_cnt;        // B: candidates appended in the current wave
-    float* cand_d;            // candidate buffer (capacity of the largest wave)
+    int64_t ubase[kMaxPasses];    // first descriptor of each pass in `units`
+    int32_t qgroup[kMaxPasses];   // queries per unit at most, per pass (the queries probing a
+                                  // bucket in a pass are split into balanced groups)
+    int32_t pass_begin[kMaxPasses + 1];  // probe ranks [pass_begin[p], pass_begin[p + 1]) of pass p
+    int64_t* cand_off;        // passes x (B + 1): candidate capacity per query, prefix
+    int32_t* cand_cnt;        // B: candidates appended in the current pass
+    float* cand_d;            // candidate buffer (capacity of the largest pass)
     int32_t* cand_pos;
     float* top_d;             // B x Kmax current top-K distances (sorted)
     int64_t* top_id;          // B x Kmax
     int32_t* top_n;           // B
-    float* tau;               // B: the K-th distance (+inf while fewer than K)
-    int32_t* work;            // 2 x n_waves work counters (scan, collect), then an 8-byte counter
+    float* tau;               // B: the tau the current wave tests against (the top-K's K-th
+                              // distance when the wave began; +inf while fewer than K)
+    float* tau_run;           // B: the top-K's current K-th distance (written by the merges)
+    int32_t* work;            // 2 x passes work counters (scan, collect), then an 8-byte counter
     int32_t* status;          // device status word
     int64_t* stats;           // B x 4 or null
     unsigned long long* staged_bytes;  // bytes staged by the scan, or null
 };
+
+// The pass that scans probe rank r (0 <= r < P).
+__device__ __forceinline__ int pass_of_rank(const WaveView& wv, int r) {
+    int lo = 0, hi = wv.n_waves;  // pass_begin[lo] <= r < pass_begin[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (wv.pass_begin[mid] <= r) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 cudaError_t launch_prepare_queries(const float* Q, int64_t B, int32_t D, int32_t Dpad,
                                    float* qpad, cudaStream_t st);

@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(kPqThreads) pq_scan_kernel(IndexView ix, WaveV
     __shared__ int64_t s_item;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nlut = pv.m * 256;
-    const int r0 = w == 0 ? 0 : (int)min((int64_t)wv.first_wave << min(wv.wave_shift * (w - 1), 30), (int64_t)1 << 30);
-    const int r1 = (int)min((int64_t)wv.first_wave << min(wv.wave_shift * w, 30), (int64_t)1 << 30);
+    const int r0 = wv.pass_begin[w];
+    const int r1 = wv.pass_begin[w + 1];
     const int nch = (min(r1, wv.P) - r0 + rpi - 1) / rpi;  // items per query in this wave
     const int64_t n_items = nch > 0 ? wv.B * nch : 0;
     const bool want_stats = wv.stats != nullptr;
@@ -199,8 +199,8 @@ cudaError_t launch_pq_scan(const IndexView& ix, const WaveView& wv, int w, const
     e = cudaMemsetAsync(wv.work + 2 * wv.n_waves, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     const int64_t grid = (int64_t)sms * std::max(per, 1);
-    const int r0 = wave_begin(w, wv.first_wave, wv.wave_shift);
-    const int nranks = std::max(0, std::min(wave_begin(w + 1, wv.first_wave, wv.wave_shift), (int)wv.P) - r0);
+    const int r0 = wv.pass_begin[w];
+    const int nranks = std::max(0, std::min(wv.pass_begin[w + 1], (int)wv.P) - r0);
     const int rpi = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(nranks, 1),
                                                                 ceil_div(wv.B * nranks, 4 * grid)));
     pq_scan_kernel<<<(unsigned)grid, kPqThreads, smem, st>>>(ix, wv, w, pv, rpi);

@@ -1,5 +1,6 @@
 // Top-nprobe bucket selection (Section II-A: a query probes its nprobe
-// nearest centroids).  One CTA per query: an MSD radix select over the
+// nearest centroids).  nprobe <= 128: select128_kernel (registers, below).
+// Larger nprobe: one warp per query, an MSD radix select over the
 // 32-bit patterns of the non-negative FP32 distances (monotone as unsigned
 // integers) finds the nprobe-th smallest key; the keys below it and the
 // lowest-id keys equal to it are gathered in column order and sorted by
@@ -108,12 +109,162 @@ __global__ void __launch_bounds__(kSelWarps * 32) select_kernel(const float* __r
     for (int r = lane; r < P; r += 32) out[r] = r < np ? sel_id[r] : -1;
 }
 
+// nprobe <= 128: one warp per query, the selection in registers.  The
+// scores are binned linearly between their minimum and maximum (512 bins);
+// only the bins up to the one where the count reaches nprobe can hold the
+// nprobe smallest.  Those scores stream in chunks of up to 128 (also not
+// above the current nprobe-th entry), each chunk sorted by (score, column)
+// with a bitonic network over shuffles and merged with the sorted best.
+constexpr int kSelBins = 512;
+
+__global__ void __launch_bounds__(kSelWarps * 32) select128_kernel(const float* __restrict__ scores, int64_t B, int n,
+                                                                  const int32_t* __restrict__ nprobe, int P,
+                                                                  int32_t* __restrict__ probes,
+                                                                  int32_t* __restrict__ status) {
+    __shared__ int s_h[kSelWarps][kSelBins];
+    __shared__ float s_d[kSelWarps][128];
+    __shared__ long long s_i[kSelWarps][128];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * kSelWarps + warp;
+    if (b >= B) return;
+    const float* row = scores + b * (int64_t)n;
+    int32_t* out = probes + b * (int64_t)P;
+    const int np = nprobe[b];
+    if (np < 1 || np > P || np > n) {
+        if (lane == 0 && status && np != 0) atomicCAS(status, 0, (int)DADE_EINVAL);
+        for (int r = lane; r < P; r += 32) out[r] = -1;
+        return;
+    }
+    float mn = INFINITY, mx = -INFINITY;
+    for (int i = lane; i < n; i += 32) {
+        const float d = row[i];
+        mn = fminf(mn, d);
+        mx = fmaxf(mx, d);
+    }
+    for (int o = 16; o; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    float scale = 0.f;
+    int kbin = kSelBins;  // no bin filter (all scores equal, or not finite)
+    if (mx > mn && isfinite(mx) && isfinite(mn)) {
+        scale = (float)kSelBins / (mx - mn);
+        int* h = s_h[warp];
+        for (int u = lane; u < kSelBins; u += 32) h[u] = 0;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) atomicAdd(&h[min(kSelBins - 1, (int)((row[i] - mn) * scale))], 1);
+        __syncwarp();
+        constexpr int PER = kSelBins / 32;
+        int hs[PER], sum = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            hs[u] = h[lane * PER + u];
+            sum += hs[u];
+        }
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - sum;
+        const unsigned hit = __ballot_sync(0xffffffffu, excl < np && incl >= np);
+        const int src = __ffs(hit) - 1;
+        int kb = 0;
+        if (lane == src) {
+            int c = excl;
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                c += hs[u];
+                if (c >= np) { kb = lane * PER + u; break; }
+            }
+        }
+        kbin = __shfl_sync(0xffffffffu, kb, src);
+    }
+    Ent a[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        a[r].d = INFINITY;
+        a[r].id = LLONG_MAX;
+    }
+    int total = 0, i0 = 0;
+    while (i0 < n) {
+        Ent kth;
+        kth.d = INFINITY;
+        kth.id = LLONG_MAX;
+        if (total >= np) kth = entry_at(a, np - 1);
+        int m = 0;
+        for (; i0 < n && m < 128; i0 += 32) {
+            const int i = i0 + lane;
+            Ent x;
+            x.d = INFINITY;
+            x.id = LLONG_MAX;
+            bool keep = false;
+            if (i < n) {
+                x.d = row[i];
+                x.id = i;
+                keep = (kbin == kSelBins || min(kSelBins - 1, (int)((x.d - mn) * scale)) <= kbin) && !ent_less(kth, x);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            const int pos = m + __popc(bal & ((1u << lane) - 1u));
+            if (keep && pos < 128) {
+                s_d[warp][pos] = x.d;
+                s_i[warp][pos] = x.id;
+            }
+            const int got = __popc(bal);
+            if (m + got > 128) {
+                // the chunk is full: resume at the first kept lane not taken
+                const int take = 128 - m;
+                int seen = 0, resume = 32;
+                for (int l2 = 0; l2 < 32; ++l2) {
+                    if ((bal >> l2) & 1u) {
+                        if (seen == take) { resume = l2; break; }
+                        ++seen;
+                    }
+                }
+                m = 128;
+                i0 += resume;
+                break;
+            }
+            m += got;
+        }
+        __syncwarp();
+        if (m == 0) break;
+        Ent c[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = r * 32 + lane;
+            c[r].d = e < m ? s_d[warp][e] : INFINITY;
+            c[r].id = e < m ? s_i[warp][e] : LLONG_MAX;
+        }
+        __syncwarp();
+        bitonic_sort128(c, lane);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const Ent cr = shfl_ent(c[3 - r], 31 - lane);
+            if (ent_less(cr, a[r])) a[r] = cr;
+        }
+#pragma unroll
+        for (int j = 64; j > 0; j >>= 1) bitonic_level(a, j, lane, [](int) { return true; });
+        total = min(128, total + m);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = r * 32 + lane;
+        if (e < P) out[e] = e < np ? (int32_t)a[r].id : -1;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_select_probes(const float* scores, int64_t B, int n, const int32_t* nprobe,
                                  int P, int32_t* probes, int32_t* status, cudaStream_t st) {
     if (B <= 0) return cudaSuccess;
     if (P > PMAX || P < 1) return cudaErrorInvalidValue;
+    if (P <= 128) {
+        select128_kernel<<<(unsigned)ceil_div(B, kSelWarps), kSelWarps * 32, 0, st>>>(scores, B, n, nprobe, P, probes,
+                                                                                     status);
+        return cudaGetLastError();
+    }
     int Pp = 2;
     while (Pp < P) Pp <<= 1;
     const int smem = kSelWarps * 2 * Pp * (int)sizeof(uint32_t);

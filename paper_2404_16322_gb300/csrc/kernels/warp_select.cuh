@@ -2,6 +2,8 @@
 // merge.
 #pragma once
 
+#include <climits>
+#include <math.h>
 #include <stdint.h>
 
 namespace dade {
@@ -59,5 +61,80 @@ __device__ uint32_t warp_kth_key(Key keys, int n, int k, int* hist, int lane) {
     }
     return prefix;
 }
+
+// ------------------------------------------------------------ 128 in registers
+// A warp holds 128 (key, id) entries, entry e = 32 r + lane in slot r of
+// lane `lane`, ordered by (key, id).  Bitonic networks over them exchange
+// across lanes with shuffles and across slots with swaps.
+struct Ent {
+    float d;
+    long long id;
+};
+__device__ __forceinline__ bool ent_less(const Ent& a, const Ent& b) { return a.d < b.d || (a.d == b.d && a.id < b.id); }
+__device__ __forceinline__ Ent shfl_xor_ent(const Ent& x, int m) {
+    Ent y;
+    y.d = __shfl_xor_sync(0xffffffffu, x.d, m);
+    y.id = __shfl_xor_sync(0xffffffffu, x.id, m);
+    return y;
+}
+__device__ __forceinline__ Ent shfl_ent(const Ent& x, int src) {
+    Ent y;
+    y.d = __shfl_sync(0xffffffffu, x.d, src);
+    y.id = __shfl_sync(0xffffffffu, x.id, src);
+    return y;
+}
+
+// Entry e of the 128 (slot e / 32 of lane e % 32), to every lane; the slot
+// is chosen with selects, not an indexed register array.
+__device__ __forceinline__ Ent entry_at(const Ent (&v)[4], int e) {
+    const int r = e >> 5;
+    Ent x = v[0];
+    if (r == 1) x = v[1];
+    if (r == 2) x = v[2];
+    if (r == 3) x = v[3];
+    return shfl_ent(x, e & 31);
+}
+
+// One compare-exchange level (distance j) of a bitonic network over the 128
+// entries; `up(e)` tells whether the block containing entry e sorts upward.
+template <class Up>
+__device__ __forceinline__ void bitonic_level(Ent (&v)[4], int j, int lane, Up up) {
+    if (j >= 32) {
+        const int js = j >> 5;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int p = r ^ js;
+            if (p > r) {
+                const bool asc = up(r * 32 + lane);
+                const bool sw = asc ? ent_less(v[p], v[r]) : ent_less(v[r], v[p]);
+                if (sw) {
+                    const Ent t = v[r];
+                    v[r] = v[p];
+                    v[p] = t;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = r * 32 + lane;
+            const Ent o = shfl_xor_ent(v[r], j);
+            const bool lower = (lane & j) == 0;
+            const bool asc = up(e);
+            // the lower entry of an upward pair keeps the smaller one
+            const bool take_min = lower == asc;
+            const bool o_less = ent_less(o, v[r]);
+            if (take_min ? o_less : !o_less && (o.d != v[r].d || o.id != v[r].id)) v[r] = o;
+        }
+    }
+}
+
+__device__ __forceinline__ void bitonic_sort128(Ent (&v)[4], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 128; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) bitonic_level(v, j, lane, [k](int e) { return (e & k) == 0; });
+}
+
 
 }  // namespace dade

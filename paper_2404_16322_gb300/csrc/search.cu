@@ -40,6 +40,8 @@ struct Carve {
 
 struct Plan {
     WaveView wv{};
+    int pass_wave[kMaxPasses] = {};   // the wave of each pass
+    bool pass_new[kMaxPasses] = {};   // the pass starts its wave (tau is taken then)
     float* pq_lut = nullptr;   // B x m x 256 (OPQ-L)
     float* scores = nullptr;
     float* qnorm = nullptr;
@@ -49,13 +51,52 @@ struct Plan {
     int64_t cand_cap = 0;
 };
 
-// Upper bound of one wave's candidates for a query: the sum of the largest
-// (end - begin) bucket sizes.
-int64_t wave_bound(const dade_index* idx, int P, int f, int g, int w) {
-    int b0 = wave_begin(w, f, g), b1 = std::min(P, wave_begin(w + 1, f, g));
-    int n = std::max(0, b1 - b0);
-    n = std::min<int>(n, idx->nlist);
-    return idx->sizes_desc_prefix[n];
+// Upper bound of a query's candidates in a pass of n probe ranks: the sum
+// of the n largest bucket sizes.
+int64_t pass_bound(const dade_index* idx, int n) { return idx->sizes_desc_prefix[std::max(0, std::min(n, idx->nlist))]; }
+
+// Default bound of the candidate buffer (distance and slot, 8 bytes per
+// entry): a wave whose worst case exceeds it is scanned in several passes.
+constexpr int64_t kDefaultCandidateBudget = int64_t(8) << 30;
+
+// The passes of the wave schedule: every wave [b, e) of probe ranks is cut
+// into the fewest passes of equal width (up to one rank) whose worst-case
+// candidates for B queries fit the budget (at least one rank per pass); if
+// that makes more than kMaxPasses passes the budget is doubled.
+void make_passes(const dade_index* idx, int64_t B, int P, int f, int g, int64_t budget, WaveView& v, Plan* pl) {
+    const int nw = num_waves(P, f, g);
+    for (;;) {
+        int np = 0;
+        bool fits = true;
+        for (int w = 0; w < nw && fits; ++w) {
+            const int b0 = wave_begin(w, f, g), b1 = std::min(P, wave_begin(w + 1, f, g));
+            const int width = std::max(0, b1 - b0);
+            auto fits_in = [&](int h) { return (double)B * (double)pass_bound(idx, h) * 8.0 <= (double)budget; };
+            int lo = 1, hi = std::max(1, width);  // largest width that fits (1 if none)
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (fits_in(mid)) lo = mid; else hi = mid - 1;
+            }
+            const int npass = (width + lo - 1) / std::max(1, lo);
+            const int h = npass > 0 ? (width + npass - 1) / npass : 1;
+            for (int r = b0; r < b1; r += h) {
+                if (np == kMaxPasses) {
+                    fits = false;
+                    break;
+                }
+                v.pass_begin[np] = r;
+                pl->pass_wave[np] = w;
+                pl->pass_new[np] = r == b0;
+                ++np;
+            }
+        }
+        if (fits) {
+            v.pass_begin[np] = P;
+            v.n_waves = np;
+            return;
+        }
+        budget *= 2;
+    }
 }
 
 // The RES test is in use (PRUNE mode with estimator RES).
@@ -78,9 +119,9 @@ enum WaveKernel { WK_EXACT = 0, WK_CUDA = 1, WK_TENSOR = 2, WK_PQ = 3 };
 // Which kernel scans wave w: every candidate's exact distance (a full scan,
 // a wave whose tau is +inf for every query, or no test to run), the OPQ-L
 // scan, or the learned / RES test on the CUDA cores or the tensor cores.
-int wave_kernel(const dade_index* idx, int32_t delta_d, const dade_search_opts& o, int w) {
+int wave_kernel(const dade_index* idx, int32_t delta_d, const dade_search_opts& o, int wave) {
     const int S = n_steps(idx, delta_d, o);
-    if (o.mode == DADE_SCAN_FULL || S <= 1 || (w == 0 && o.tau_dev == nullptr)) return WK_EXACT;
+    if (o.mode == DADE_SCAN_FULL || S <= 1 || (wave == 0 && o.tau_dev == nullptr)) return WK_EXACT;
     if (o.estimator == DADE_EST_PQ) return WK_PQ;
     if (tc_eligible(idx, delta_d, o) && o.scan_kernel != DADE_KERNEL_CUDA) return WK_TENSOR;
     return WK_CUDA;
@@ -95,21 +136,20 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     const bool frozen = o.tau_dev != nullptr;
     const int f = frozen ? P : std::max(1, o.first_wave);
     const int g = std::max(1, o.wave_growth_log2);
-    const int nw = num_waves(P, f, g);
     const int64_t nl = idx->nlist;
-    int64_t cap_per_q = 0;
-    for (int w = 0; w < nw; ++w) cap_per_q = std::max(cap_per_q, wave_bound(idx, P, f, g, w));
     Carve c{base};
     WaveView& v = pl->wv;
+    make_passes(idx, B, P, f, g, o.candidate_budget_bytes > 0 ? o.candidate_budget_bytes : kDefaultCandidateBudget, v,
+                pl);
+    const int nw = v.n_waves;  // passes
+    int64_t cap_per_q = 0;
+    for (int w = 0; w < nw; ++w) cap_per_q = std::max(cap_per_q, pass_bound(idx, v.pass_begin[w + 1] - v.pass_begin[w]));
     v.B = B;
     v.P = P;
     v.Kmax = Kmax;
-    v.first_wave = f;
-    v.wave_shift = g;
     v.final_test = o.final_test != 0;
     v.est = uses_res(o) ? 1 : 0;
     v.res_stride = v.est ? (int)ceil_div(idx->Dpad, delta_d) - 1 : 0;
-    v.n_waves = nw;
     {
         const int all = delta_d > 0 ? (int)ceil_div(idx->Dpad, delta_d) - 1 : 0;
         v.test_steps = o.test_steps > 0 ? std::min(all, (int)o.test_steps) : all;
@@ -127,8 +167,8 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     const int64_t ntile_max = std::max<int64_t>(1, ceil_div(idx->max_list, kT));
     int64_t ucap = 0;
     for (int w = 0; w < nw; ++w) {
-        const int64_t width = std::max(0, std::min(P, wave_begin(w + 1, f, g)) - wave_begin(w, f, g));
-        const int qg = wave_qgroup(wave_kernel(idx, delta_d, o, w), delta_d);
+        const int64_t width = v.pass_begin[w + 1] - v.pass_begin[w];
+        const int qg = wave_qgroup(wave_kernel(idx, delta_d, o, pl->pass_wave[w]), delta_d);
         v.ubase[w] = ucap;
         v.qgroup[w] = qg;
         ucap += (ceil_div(B * width, qg) + std::min<int64_t>(nl, B * width)) * ntile_max;
@@ -140,6 +180,7 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     v.top_d = c.take<float>((size_t)B * Kmax);
     v.top_id = c.take<int64_t>((size_t)B * Kmax);
     v.tau = c.take<float>((size_t)B);
+    v.tau_run = c.take<float>((size_t)B);
     v.res_q = v.res_stride > 0 ? c.take<float>((size_t)B * v.res_stride) : nullptr;
     pl->pq_lut = o.estimator == DADE_EST_PQ ? c.take<float>((size_t)B * idx->pq_m * 256) : nullptr;
     // zero-initialised block
@@ -167,6 +208,7 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
         return fail(DADE_EINVAL, "max_nprobe must be in [1, min(nlist, 1024)]");
     if (o.mode != DADE_SCAN_PRUNE && o.mode != DADE_SCAN_FULL) return fail(DADE_EINVAL, "bad mode");
     if (o.first_wave < 0) return fail(DADE_EINVAL, "first_wave < 0");
+    if (o.candidate_budget_bytes < 0) return fail(DADE_EINVAL, "candidate_budget_bytes < 0");
     if (o.wave_growth_log2 < 0 || o.wave_growth_log2 > 30) return fail(DADE_EINVAL, "wave_growth_log2 must be in [0, 30]");
     if (o.estimator != DADE_EST_LEARNED && o.estimator != DADE_EST_RES && o.estimator != DADE_EST_PQ)
         return fail(DADE_EINVAL, "bad estimator");
@@ -280,6 +322,7 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
         DADE_CUDA_TRY(cudaMemcpyAsync(v.tau, o.tau_dev, sizeof(float) * B, cudaMemcpyDeviceToDevice, st));
     else
         DADE_CUDA_TRY(launch_fill(v.tau, B, INFINITY, st));
+    DADE_CUDA_TRY(launch_fill(v.tau_run, B, INFINITY, st));
 
     // 1. q' = R (q - mean); the original query zero-padded to Dpad
     DADE_CUDA_TRY(launch_tc_dot(Q, idx->D, idx->mean_dev.as<float>(), idx->R_dev.as<float>(), idx->Dpad,
@@ -315,6 +358,10 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     DADE_CUDA_TRY(launch_build_units(ix, v, st));
     // 4-5. waves
     for (int w = 0; w < v.n_waves; ++w) {
+        // a new wave tests against the top-K's K-th distance as the previous
+        // waves left it; the passes of one wave share that tau
+        if (w > 0 && pl.pass_new[w] && !o.tau_dev)
+            DADE_CUDA_TRY(cudaMemcpyAsync(v.tau, v.tau_run, sizeof(float) * B, cudaMemcpyDeviceToDevice, st));
         if (collect) {
             CollectArgs ca = *collect;
             if (pq) {
@@ -333,7 +380,7 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
         }
         // wave 0 has tau = +inf for every query (no frozen tau): every
         // candidate's exact distance, through the full-scan kernel
-        const int wk = wave_kernel(idx, delta_d, o, w);
+        const int wk = wave_kernel(idx, delta_d, o, pl.pass_wave[w]);
         if (wk == WK_PQ) {
             PQView pv{idx->pq_codes_dev.as<uint8_t>(), idx->pq_err_dev.as<float>(), pl.pq_lut, idx->total_slots,
                       idx->pq_m, idx->pq_m1, idx->pq_m3, idx->pq_beta};

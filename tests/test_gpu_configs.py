@@ -17,9 +17,9 @@
 * GIST-shaped 1M x 960 with BF16 slabs, 1,000 queries, nprobe 128, first
   wave 16 (the GIST-shaped bench configuration) against the oracle in the
   same way, and the 10M x 96 vMF-like
-  set with BF16 slabs and a batch of 512 requests with K in [1, 100] and
-  nprobe in [8, 256], checked the same way (distances within 1e-5 of
-  FP64)."""
+  set with BF16 and FP8 slabs and all 20,000 requests (K in [1, 100],
+  nprobe in [8, 256]) in one call, also replayed from a CUDA graph, checked
+  the same way (distances within 1e-5 of FP64)."""
 import numpy as np
 import pytest
 
@@ -261,26 +261,60 @@ def test_gist_full_size_in_the_benchmark_configuration(G):
         idx.close()
 
 
-def test_vmf_10m_full_size_uneven_requests(G):
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_vmf_10m_full_size_uneven_requests(G, dtype):
+    """Config 4 at its stated size: 10M x 96 L2-normalised vMF-like vectors,
+    all 20,000 requests in one call with K uniform in [1, 100] and nprobe
+    uniform in [8, 256], BF16 or FP8-E4M3 slabs.  The candidate buffer is
+    bounded (the waves run in passes), and the search replays bit for bit
+    from a CUDA graph.  Checked on sampled queries: exact distances of the
+    returned ids, sorted unique results, containment in the full scan's
+    result, brute-force recall@10."""
+    import torch
     X, Q, T, cfg = synth.workload("vmf10m")
     mean, R, _ = G.dade_train_rotation(X, sample_n=1_000_000, seed=1)
-    idx = G.ivf_build(X, mean, R, cfg["nlist"], kmeans_iters=10, seed=1, dtype="bf16")
+    idx = G.ivf_build(X, mean, R, cfg["nlist"], kmeans_iters=10, seed=1, dtype=dtype)
     try:
         G.dade_fit_correction(idx, T, 100, 64, 16, target_recall=0.995, seed=1)
-        # one batch of 512 uneven requests (the candidate buffer of a batch
-        # grows with the batch times the largest buckets' sizes)
-        Qb = Q[:512]
+        B = len(Q)
+        assert B == 20_000
         rng = np.random.default_rng(10)
-        K = rng.integers(1, 101, len(Qb)).astype(np.int32)
-        npb = rng.integers(8, 257, len(Qb)).astype(np.int32)
-        pr = H.gpu_search(G, idx, Qb, K, npb, 16, max_K=100, max_nprobe=256, first_wave=8, growth=30,
-                          want=("stats",))
-        fu = H.gpu_search(G, idx, Qb, K, npb, 0, mode="full", max_K=100, max_nprobe=256, first_wave=8, growth=30)
+        K = rng.integers(1, 101, B).astype(np.int32)
+        npb = rng.integers(8, 257, B).astype(np.int32)
+        kw = dict(max_K=100, max_nprobe=256, first_wave=8, growth=30)
+        pr = H.gpu_search(G, idx, Q, K, npb, 16, want=("stats",), **kw)
+        fu = H.gpu_search(G, idx, Q, K, npb, 0, mode="full", **kw)
         assert pr["status"] == 0 and fu["status"] == 0
-        sample = np.random.default_rng(7).choice(len(Qb), 8, replace=False)
-        rec = _check_sampled(X, Qb, pr, fu, K, sample)
+        sample = np.random.default_rng(7).choice(B, 8, replace=False)
+        rec = _check_sampled(X, Q, pr, fu, K, sample)
         assert rec >= 0.8
         st = pr["stats"]
         assert st[:, 1].sum() > 0.3 * st[:, 0].sum()
+        # the same search captured in a CUDA graph and replayed
+        dev = torch.device("cuda")
+        q = torch.from_numpy(Q).to(dev)
+        kt = torch.from_numpy(K).to(dev)
+        nt = torch.from_numpy(npb).to(dev)
+        ids = torch.full((B * 100,), -7, dtype=torch.int64, device=dev)
+        d = torch.full((B * 100,), -7.0, dtype=torch.float32, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        ws = torch.empty(G.dade_search_workspace_size(idx, B, 16, 100, 256, first_wave=8, wave_growth_log2=30),
+                         dtype=torch.uint8, device=dev)
+        assert ws.numel() < 12 << 30  # the candidate buffer is bounded, not B x the worst wave
+        call = dict(max_K=100, max_nprobe=256, first_wave=8, wave_growth_log2=30, workspace=ws, status=status)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            G.dade_search(idx, q, kt, nt, 16, ids, d, **call)  # first call: kernel attributes set outside capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            G.dade_search(idx, q, kt, nt, 16, ids, d, **call)
+        ids.fill_(-7)
+        d.fill_(-7.0)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert np.array_equal(ids.view(B, 100).cpu().numpy(), pr["ids"])
+        assert np.array_equal(d.view(B, 100).cpu().numpy(), pr["dists"])
     finally:
         idx.close()

@@ -378,3 +378,30 @@ def test_tested_steps_limit_matches_disabled_later_steps(G, tiny_pre, L):
     parity.check(out["ids"], out["dists"], ids, d, s["X"], s["Q"], 10, amb_d=ad)
     un = st[:, 4] == 0
     assert np.array_equal(out["stats"][un], st[un, :4])
+
+
+@pytest.mark.parametrize("kernel", ["tensor", "cuda"])
+@pytest.mark.parametrize("fw,g", [(1, 1), (2, 30)])
+def test_passes_within_a_wave_change_nothing(G, tiny_pre, kernel, fw, g):
+    """A candidate budget below one bucket's worth makes every wave run one
+    probe rank per pass, each pass tested against the wave's tau: ids,
+    distances and work counters are those of one pass per wave, and agree
+    with the oracle's waves."""
+    s = tiny_pre
+    oidx = s["inp"]["oidx"]
+    pr = oidx.probe(oidx.rotate_queries(s["Q"]), 8)
+    one = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, first_wave=fw, growth=g, scan_kernel=kernel,
+                       want=("stats",))
+    many = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, probe_in=pr, first_wave=fw, growth=g, scan_kernel=kernel,
+                        want=("stats",), candidate_budget_bytes=1)
+    assert one["status"] == 0 and many["status"] == 0
+    for k in ("ids", "dists", "stats"):
+        assert np.array_equal(one[k], many[k]), k
+    oi, od, ost, oad = search.search(oidx, s["Q"], pr, 8, 10, 16, s["inp"]["m1"].astype(np.float64),
+                                     s["inp"]["beta"].astype(np.float64), first_wave=fw, growth=g,
+                                     amb=H.AMB["exact"], with_amb=True, norm_eps=H.NORM_EPS)
+    parity.check(many["ids"], many["dists"], oi, od, s["X"], s["Q"], 10, amb_d=oad)
+    small = G.dade_search_workspace_size(s["idx"], 100, 16, 10, 8, first_wave=fw, wave_growth_log2=g,
+                                         candidate_budget_bytes=1)
+    big = G.dade_search_workspace_size(s["idx"], 100, 16, 10, 8, first_wave=fw, wave_growth_log2=g)
+    assert small <= big
