@@ -61,8 +61,8 @@ def parse():
     ap.add_argument("--no-estimators", action="store_true",
                     help="skip the RES and ADS comparison lines")
     ap.add_argument("--cpu-sample-queries", type=int, default=1000)
-    ap.add_argument("--workload", default="sift1m", choices=sorted(WORKLOAD_INFO),
-                    help="sift1m (the benchmark line) or gist1m")
+    ap.add_argument("--workload", default="sift1m", choices=sorted(WORKLOAD_INFO) + ["vmf10m"],
+                    help="sift1m (the benchmark line), gist1m, or vmf10m (20,000 uneven requests on 10M x 96)")
     ap.add_argument("--slabs", default=None, choices=["f32", "bf16", "fp8"],
                     help="slab precision (default: f32 for sift1m, bf16 for gist1m)")
     ap.add_argument("--profile", default=None,
@@ -161,18 +161,15 @@ def ground_truth(X, Q, k=10, chunk=1024):
     return out
 
 
-def n_waves(nprobe, first_wave=1, growth=1):
-    b, w = 0, 0
-    while b < nprobe:
-        b = first_wave if b == 0 else b << min(max(growth, 1), 40)
-        w += 1
-    return w
+SCAN_SOURCES = {"tc_scan_kernel": ["scan_tc.cu", "scan.cuh", "scan_steps.cuh"],
+                "wave_scan_kernel": ["scan.cu", "scan.cuh", "scan_steps.cuh"]}
+PROFILE_OF = {"tc_scan_kernel": "tc_scan_sift1m.md", "wave_scan_kernel": "wave_scan_sift1m.md"}
 
 
-def traffic_from_profiles(kernel_src_hash):
+def traffic_from_profiles(kernel, kernel_src_hash):
     """Per-launch DRAM bytes of the scan kernel from the committed ncu summary,
     if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "wave_scan_sift1m.md")
+    p = os.path.join(ROOT, "profiles", PROFILE_OF[kernel])
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -183,11 +180,11 @@ def traffic_from_profiles(kernel_src_hash):
     return float(t.group(1))
 
 
-def kernel_hash(root=ROOT):
+def kernel_hash(kernel="tc_scan_kernel", root=ROOT):
     """sha256 of the scan kernel's sources with comments and blank lines
     removed (a comment edit does not make the recorded counters stale)."""
     h = hashlib.sha256()
-    for f in ["scan.cu", "scan.cuh", "scan_steps.cuh"]:
+    for f in SCAN_SOURCES[kernel]:
         src = open(os.path.join(root, "paper_2404_16322_gb300", "csrc", "kernels", f)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
@@ -321,6 +318,199 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- uneven requests
+UNEVEN_METRIC = ("QPS of 20,000 uneven requests in one call (estimate-and-prune IVF search, vMF-like 10M x 96, "
+                 "nlist 4096, K in [1,100], nprobe in [8,256])")
+UNEVEN_SCHEDULES = ((8, 30), (4, 30), (16, 30), (8, 2))
+
+
+def uneven_requests(args, G, torch, world, rank, local):
+    """The large-N uneven-request line: one dade_search over all 20,000
+    requests (per-request K uniform in [1, 100] and nprobe in [8, 256]) on
+    the 10M x 96 vMF-like set, BF16 (or FP8) slabs, graph-captured; the wave
+    schedule is the fastest of a few; the full-dimension scan of the same
+    requests beside it; recall against brute force on a sample."""
+    t_setup = time.perf_counter()
+    slabs = args.slabs or "bf16"
+    X, Q, T, cfg = make_workload(args.n, args.queries, "vmf10m")
+    nlist = cfg["nlist"] if args.n is None else max(16, int(round(args.n / 2441)))
+    mean, R, _ = G.dade_train_rotation(X, sample_n=min(len(X), 1_000_000), seed=1)
+    idx = G.ivf_build(X, mean, R, nlist, kmeans_iters=10, seed=1, dtype=slabs)
+    dd, maxK, maxP = 16, 100, min(256, nlist)
+    G.dade_fit_correction(idx, T, maxK, min(64, nlist), dd, target_recall=0.995, seed=1)
+    B = len(Q)
+    rng = np.random.default_rng(10)
+    Kv = rng.integers(1, maxK + 1, B).astype(np.int32)
+    Nv = np.minimum(rng.integers(8, 257, B), maxP).astype(np.int32)
+    n_gt = min(B, 1000)
+    gt = ground_truth(X, Q[:n_gt], 10)
+    dev = torch.device("cuda")
+    q = torch.from_numpy(Q).to(dev)
+    k = torch.from_numpy(Kv).to(dev)
+    npb = torch.from_numpy(Nv).to(dev)
+    ids = torch.empty(B * maxK, dtype=torch.int64, device=dev)
+    dists = torch.empty(B * maxK, dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stats = torch.zeros((B, 4), dtype=torch.int64, device=dev)
+    ws = torch.empty(max(G.dade_search_workspace_size(idx, B, dd, maxK, maxP, mode=m, first_wave=fw,
+                                                      wave_growth_log2=g)
+                         for m in ("prune", "full") for fw, g in UNEVEN_SCHEDULES + ((1, 1),)),
+                     dtype=torch.uint8, device=dev)
+
+    def search(mode, fw, g, with_stats=False):
+        G.dade_search(idx, q, k, npb, dd if mode == "prune" else 0, ids, dists, max_K=maxK, max_nprobe=maxP,
+                      mode=mode, first_wave=fw, wave_growth_log2=g, status=status, workspace=ws,
+                      stats=stats if with_stats else None)
+
+    def timed(mode, fw, g, steps, warmup):
+        search(mode, fw, g)  # outside the capture: kernel attributes, module loads
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(graph, stream=s):
+            search(mode, fw, g)
+        for _ in range(warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            e0.record()
+            graph.replay()
+            e1.record()
+        torch.cuda.synchronize()
+        if int(status.item()):
+            raise RuntimeError(f"device status {int(status.item())}")
+        return [a.elapsed_time(b) for a, b in evs]
+
+    def recall():
+        got = ids.view(B, maxK)[:n_gt].cpu().numpy()
+        m10 = Kv[:n_gt] >= 10
+        r10 = float(np.mean([len(set(got[b, :10].tolist()) & set(gt[b].tolist())) / 10
+                             for b in np.flatnonzero(m10)])) if m10.any() else None
+        r1 = float(np.mean(got[:, 0] == gt[:, 0]))
+        return r10, r1
+
+    tried = []
+    for fw, g in UNEVEN_SCHEDULES:
+        per = timed("prune", fw, g, 5, 2)
+        tried.append(dict(first_wave=fw, growth=g, ms=float(np.median(per))))
+    best = min(tried, key=lambda t: t["ms"])
+    fw, g = best["first_wave"], best["growth"]
+    setup_s = time.perf_counter() - t_setup
+
+    sampler = ClockSampler(local)
+    sampler.wait_ready()
+    per = timed("prune", fw, g, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms_step = float(np.mean(per))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * B / (ms_step / 1000.0)
+    r10, r1 = recall()
+    fper = timed("full", 1, 1, args.steps, args.warmup)
+    full_qps = B / (float(np.mean(fper)) / 1000.0)
+    fr10, fr1 = recall()
+
+    G.dade_stage_timing(True, tensor_only=True)
+    G.dade_stage_timing_read()
+    for _ in range(args.steps):
+        search("prune", fw, g)
+    scan_ms, scan_launches, scan_bytes = G.dade_stage_timing_read()
+    G.dade_stage_timing(False)
+    per_launch_ms = scan_ms / max(1, scan_launches)
+    per_launch_bytes = scan_bytes / max(1, scan_launches)
+    peak, peak_kind = peaks()
+    achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
+
+    stats.zero_()
+    search("prune", fw, g, with_stats=True)
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy()
+
+    # end to end: requests (vectors, K, nprobe) from pinned host memory in,
+    # results out, every step
+    q_h, k_h, n_h = (torch.from_numpy(Q).pin_memory(), torch.from_numpy(Kv).pin_memory(),
+                     torch.from_numpy(Nv).pin_memory())
+    ids_h = torch.empty(B * maxK, dtype=torch.int64).pin_memory()
+    d_h = torch.empty(B * maxK, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        q.copy_(q_h, non_blocking=True)
+        k.copy_(k_h, non_blocking=True)
+        npb.copy_(n_h, non_blocking=True)
+        search("prune", fw, g)
+        ids_h.copy_(ids, non_blocking=True)
+        d_h.copy_(dists, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_qps = world * B / (e0.elapsed_time(e1) / args.steps / 1000.0)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import search as osearch
+        oidx = osearch.OracleIndex(X, mean, R, G.dade_index_centroids(idx).astype(np.float64),
+                                   G.dade_index_assignment(idx), dtype=slabs)
+        m1, beta = G.dade_get_correction(idx, dd)
+        nq = min(B, max(20, args.cpu_sample_queries // 5))
+        threads = osearch.max_threads()
+        osearch.set_threads(threads)
+        t0 = time.perf_counter()
+        pr = oidx.probe(oidx.rotate_queries(Q[:nq]), maxP)
+        osearch.search(oidx, Q[:nq], pr, Nv[:nq], Kv[:nq], dd, m1.astype(np.float64), beta.astype(np.float64),
+                       first_wave=fw, growth=g)
+        cpu_s = time.perf_counter() - t0
+        del oidx
+        cpu = dict(value=nq / cpu_s, unit="queries/s", cores=threads, kind="oracle",
+                   sample=f"oracle FP64 C loop on the first {nq} of the {B} requests (their own K and nprobe) "
+                          f"against the same {len(X)}-vector index as the GPU line (the library's rotation, "
+                          f"centroids, assignment and fitted table; {slabs} slabs emulated), delta_d {dd}, "
+                          f"first wave {fw}, growth 2^{g}; probing included")
+
+    line = {
+        "metric": UNEVEN_METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"vmf10m-shaped: N={len(X)}, D=96, L2-normalised vMF mixture of 2048 components; "
+                               f"B={B} requests, K~U[1,100], nprobe~U[8,256]; nlist={nlist}",
+                   "delta_d": dd, "first_wave": fw, "wave_growth_log2": g, "slabs": slabs,
+                   "recall@10(K>=10)": r10, "recall@1": r1, "graph": True, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 (index {G.dade_index_info_get(idx)['device_bytes'] / 1e9:.1f} GB "
+                         "> 129 MB L2)",
+                   "workspace_bytes": int(ws.numel())},
+        "full_scan": {"value": full_qps, "unit": "queries/s", "recall@10(K>=10)": fr10, "recall@1": fr1},
+        "speedup_vs_full_scan": value / world / full_qps,
+        "scanned_dims_ratio": float(st[:, 3].sum() / max(1, st[:, 0].sum() * 96)),
+        "latency_ms": {"batch_p50": float(np.percentile(per, 50)), "batch_p99": float(np.percentile(per, 99))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind, "kernel": "tc_scan_kernel",
+                     "per_launch_ms": per_launch_ms, "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "launches": scan_launches},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes + Kv.nbytes + Nv.nbytes),
+                "d2h_bytes_per_step": int(B * maxK * 12)},
+        "gpu_launches": args.steps * G.dade_search_kernel_count(
+            idx, q, k, npb, dd, ids, dists, max_K=maxK, max_nprobe=maxP, workspace=ws, status=status,
+            first_wave=fw, wave_growth_log2=g),
+        "clocks": clocks,
+        "schedules": tried,
+        "setup_s": setup_s,
+    }
+    idx.close()
+    return line
+
+
 # ---------------------------------------------------------------- main arm
 def compare_estimators(G, X, Q, T, gt, idx, mean, R, nlist, K, slabs, maxp, nps, steps, warmup):
     """The other estimators of the paper on the same data and buckets, each
@@ -402,6 +592,14 @@ def main():
     from paper_2404_16322_gb300 import build as gbuild
     gbuild.build()
 
+    if args.workload == "vmf10m":
+        line = uneven_requests(args, G, torch, world, rank, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     t_setup = time.perf_counter()
     wl = WORKLOAD_INFO[args.workload]
     slabs = args.slabs or wl["slabs"]
@@ -437,7 +635,9 @@ def main():
         torch.cuda.nvtx.range_pop()
         ids = run.result()
         print(json.dumps({"profile": args.profile, "recall@10": autotune.recall_at(ids, gt, 10), "steps": args.steps,
-                          "launches_per_step": 12 + 2 * n_waves(npb, fw, gw), "setup_s": time.perf_counter() - t_setup}))
+                          "launches_per_step": G.dade_search_kernel_count(
+                              idx, run.q, run.k, run.np, dd, run.ids, run.d, max_K=K, max_nprobe=npb,
+                              workspace=run.ws, first_wave=fw, wave_growth_log2=gw), "setup_s": time.perf_counter() - t_setup}))
         return
     nps = [p for p in NPROBES + ([384, 512] if args.workload == "gist1m" else []) if p <= maxp]
     bd, tried_p = autotune.autotune(run, gt, TARGET_RECALL, 10, DELTAS, nprobes=nps, mode="prune")
@@ -450,15 +650,27 @@ def main():
         dist.barrier()
     sampler = ClockSampler(local)
     sampler.wait_ready()
+    kn = dict(first_wave=bd["first_wave"], growth=bd["growth"], final_test=bd["final_test"],
+              scan_kernel=bd.get("scan_kernel", "auto"), queries_per_unit=bd.get("queries_per_unit", 0))
+    graph = run.capture(bd["nprobe"], bd["delta_d"], "prune", **kn)  # the timed step: one graph replay
     for _ in range(args.warmup):
-        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"],
-                final_test=bd["final_test"])
+        graph.replay()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms, per = run.time(bd["nprobe"], bd["delta_d"], "prune", args.steps, 0, first_wave=bd["first_wave"],
-                             growth=bd["growth"], final_test=bd["final_test"])
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record()
+    for e0, e1 in evs:
+        e0.record()
+        graph.replay()
+        e1.record()
+    t1e.record()
+    torch.cuda.synchronize()
+    total_ms, per = t0e.elapsed_time(t1e), [a.elapsed_time(b) for a, b in evs]
+    run.result()  # raises on a device status
+    del graph
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:
@@ -470,27 +682,29 @@ def main():
 
     # --- full-scan reference point on the same GPU, same timing
     f_total, f_per = run.time(bf["nprobe"], 0, "full", args.steps, args.warmup, first_wave=bf["first_wave"],
-                              growth=bf["growth"])
+                              growth=bf["growth"], graph=True)
     full_qps = run.B / (f_total / args.steps / 1000.0)
 
-    # --- stage timing of the dominant kernel (the refinement scan)
-    G.dade_stage_timing(True)
+    # --- stage timing of the dominant kernel (the estimate-and-prune scan of
+    # the waves after the first: the tensor-core kernel unless the tuner
+    # chose the CUDA-core one)
+    tensor_scan = kn["scan_kernel"] != "cuda"
+    G.dade_stage_timing(True, tensor_only=tensor_scan)
     G.dade_stage_timing_read()
     for _ in range(args.steps):
-        run.run(bd["nprobe"], bd["delta_d"], "prune", first_wave=bd["first_wave"], growth=bd["growth"],
-                final_test=bd["final_test"])
+        run.run(bd["nprobe"], bd["delta_d"], "prune", **kn)
     scan_ms, scan_launches, scan_bytes = G.dade_stage_timing_read()
     G.dade_stage_timing(False)
     per_launch_ms = scan_ms / max(1, scan_launches)
     per_launch_bytes = scan_bytes / max(1, scan_launches)
     peak, peak_kind = peaks()
     achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
-    khash = kernel_hash()
-    traffic = traffic_from_profiles(khash) if args.workload == "sift1m" else None
+    kname = "tc_scan_kernel" if tensor_scan else "wave_scan_kernel"
+    khash = kernel_hash(kname)
+    traffic = traffic_from_profiles(kname, khash) if args.workload == "sift1m" else None
 
     # --- work accounting (bytes per query) for both modes
-    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True, first_wave=bd["first_wave"], growth=bd["growth"],
-                final_test=bd["final_test"])
+    run.run(bd["nprobe"], bd["delta_d"], "prune", stats=True, **kn)
     run.result()
     st = run.stats.cpu().numpy()
     esz = {"f32": 4, "bf16": 2, "fp8": 1}[slabs]
@@ -515,7 +729,8 @@ def main():
         run.np.copy_(n_h, non_blocking=True)
         G.dade_search(idx, run.q, run.k, run.np, bd["delta_d"], run.ids, run.d, max_K=K,
                       max_nprobe=bd["nprobe"], status=run.status, workspace=run.ws,
-                      first_wave=bd["first_wave"], wave_growth_log2=bd["growth"], final_test=bd["final_test"])
+                      first_wave=bd["first_wave"], wave_growth_log2=bd["growth"], final_test=bd["final_test"],
+                      scan_kernel=kn["scan_kernel"], queries_per_unit=kn["queries_per_unit"])
         ids_h.copy_(run.ids, non_blocking=True)
         d_h.copy_(run.d, non_blocking=True)
 
@@ -568,7 +783,12 @@ def main():
                                       args.cpu_sample_queries if D <= 256 else max(20, args.cpu_sample_queries // 5),
                                       bd["first_wave"], bd["growth"], bd["final_test"], args.workload)
 
-    launches = 12 + 2 * n_waves(bd["nprobe"], bd["first_wave"], bd["growth"])
+    run.np.fill_(bd["nprobe"])
+    launches = G.dade_search_kernel_count(idx, run.q, run.k, run.np, bd["delta_d"], run.ids, run.d, max_K=K,
+                                          max_nprobe=bd["nprobe"], workspace=run.ws, status=run.status,
+                                          first_wave=bd["first_wave"], wave_growth_log2=bd["growth"],
+                                          final_test=bd["final_test"], scan_kernel=kn["scan_kernel"],
+                                          queries_per_unit=kn["queries_per_unit"])
     line = {
         "metric": wl["metric"], "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -576,6 +796,7 @@ def main():
         "config": {"workload": wl["desc"].format(N=len(X)) + f"; B={run.B} queries; nlist={nlist}, K={K}",
                    "nprobe": bd["nprobe"], "delta_d": bd["delta_d"], "first_wave": bd["first_wave"],
                    "wave_growth_log2": bd["growth"], "final_test": bd["final_test"],
+                   "scan_kernel": kn["scan_kernel"], "queries_per_unit": kn["queries_per_unit"], "graph": True,
                    "slabs": slabs, "recall@10": bd["recall"],
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (index {G.dade_index_info_get(idx)['device_bytes'] / 1e9:.1f} GB > "
@@ -589,7 +810,11 @@ def main():
         "estimators": estimators,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "wave_scan_kernel", "per_launch_ms": per_launch_ms,
+                     "dram_achieved": (traffic / (per_launch_ms / 1000.0) / 1e9
+                                       if traffic and per_launch_ms > 0 else None),
+                     "dram_frac": (traffic / (per_launch_ms / 1000.0) / 1e9 / peak
+                                   if traffic and per_launch_ms > 0 else None),
+                     "kernel": kname, "kernel_src_sha256": khash, "per_launch_ms": per_launch_ms,
                      "algorithmic_bytes_per_launch": per_launch_bytes, "launches": scan_launches},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

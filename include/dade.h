@@ -295,6 +295,11 @@ typedef struct {
                              /* wave's tau (results do not change).  0: 8 GiB. */
                              /* The bound grows if it would take more than 128 */
                              /* passes.                                        */
+    int32_t queries_per_unit; /* at most this many queries share one staged   */
+                             /* tile of a bucket (a work unit); 0: the scan    */
+                             /* kernel's maximum (128 on tensor cores, 16 on   */
+                             /* CUDA cores), larger values are clamped to it.  */
+                             /* Results do not change, only the time.  >= 0.   */
 } dade_search_opts;
 
 /* The estimate-and-prune kernels of the learned test.  DADE_KERNEL_TENSOR:
@@ -306,8 +311,8 @@ typedef struct {
  * (16 queries per unit, survivors compacted in shared memory after every
  * step).  Both test every pair after every step and give the same results
  * up to the rounding of the partial distances (a decision within that
- * rounding of its threshold may differ).  The final test, RES and OPQ-L
- * always use the CUDA-core kernels. */
+ * rounding of its threshold may differ).  RES and OPQ-L always use the
+ * CUDA-core kernels. */
 typedef enum { DADE_KERNEL_AUTO = 0, DADE_KERNEL_CUDA = 1, DADE_KERNEL_TENSOR = 2 } dade_scan_kernel;
 
 /* ------------------------------------------------------------------------
@@ -402,6 +407,16 @@ dade_status dade_search_noalloc(const dade_index* idx, const float* Q_dev, int64
 size_t dade_search_workspace_size(const dade_index* idx, int64_t B, int32_t delta_d,
                                   const dade_search_opts* opts);
 
+/* The number of kernels one dade_search with these arguments launches
+ * (*count), found by capturing the call into a CUDA graph on a private
+ * stream and counting its kernel nodes; nothing runs.  The arguments are
+ * those of dade_search; opts->workspace is required (the per-stream scratch
+ * is not taken inside a capture): DADE_EINVAL without it. */
+dade_status dade_search_kernel_count(const dade_index* idx, const float* Q_dev, int64_t B,
+                                     const int32_t* K_dev, const int32_t* nprobe_dev, int32_t delta_d,
+                                     const dade_search_opts* opts, int64_t* ids_dev, float* dists_dev,
+                                     const int64_t* out_offsets_dev, int64_t* count);
+
 /* ------------------------------------------------------------------------
  * Bucket-sharded search (the layout for spreading one index over several
  * GPUs).  The paper has no counterpart: it searches one index on one CPU.
@@ -478,7 +493,8 @@ void dade_index_free(dade_index* idx);
  * dade_search record a CUDA event pair around each refinement-scan launch
  * (on the search's stream) and count the bytes that launch stages from
  * device memory (slab blocks copied to shared memory plus original vectors
- * read for exact distances); dade_stage_timing(0) stops.
+ * read for exact distances); dade_stage_timing(2) does the same for the
+ * tensor-core scan launches alone; dade_stage_timing(0) stops.
  * dade_stage_timing_read synchronises the recorded events and returns the
  * summed milliseconds, the number of launches and the staged bytes since the
  * last read, then resets them.  Process-wide; not for concurrent searches.

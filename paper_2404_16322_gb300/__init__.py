@@ -266,22 +266,23 @@ def dade_get_correction(idx: Index, delta_d: int):
 
 def _opts(mode, max_K, max_nprobe, first_wave=0, tau=None, probe_in=None, probe_out=None, qrot_out=None,
           stats=None, status=None, workspace=None, wave_growth_log2=0, final_test=False, estimator="learned",
-          res_m=8.0, test_steps=0, scan_kernel="auto", candidate_budget_bytes=0):
+          res_m=8.0, test_steps=0, scan_kernel="auto", candidate_budget_bytes=0, queries_per_unit=0):
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     return L.SearchOpts(L.MODE[mode], int(max_K), int(max_nprobe), int(first_wave), _ptr(tau),
                         _ptr(probe_in), _ptr(probe_out), _ptr(qrot_out), _ptr(stats), _ptr(status),
                         _ptr(workspace), ws_bytes, int(wave_growth_log2), int(bool(final_test)),
                         L.ESTIMATOR[estimator], float(res_m), int(test_steps), L.SCAN_KERNEL[scan_kernel],
-                        int(candidate_budget_bytes))
+                        int(candidate_budget_bytes), int(queries_per_unit))
 
 
 def dade_search_workspace_size(idx: Index, B: int, delta_d: int, max_K: int, max_nprobe: int,
                                mode: str = "prune", first_wave: int = 0, frozen: bool = False,
                                probe_in: bool = False, wave_growth_log2: int = 0, final_test: bool = False,
                                estimator: str = "learned", scan_kernel: str = "auto",
-                               candidate_budget_bytes: int = 0) -> int:
+                               candidate_budget_bytes: int = 0, queries_per_unit: int = 0) -> int:
     o = _opts(mode, max_K, max_nprobe, first_wave, wave_growth_log2=wave_growth_log2, final_test=final_test,
-              estimator=estimator, scan_kernel=scan_kernel, candidate_budget_bytes=candidate_budget_bytes)
+              estimator=estimator, scan_kernel=scan_kernel, candidate_budget_bytes=candidate_budget_bytes,
+              queries_per_unit=queries_per_unit)
     if frozen:
         o.tau_dev = 1  # only its presence matters for sizing
     if probe_in:
@@ -294,7 +295,7 @@ def dade_search(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: in
                 qrot_out=None, stats=None, status=None, workspace=None, offsets=None, stream=None,
                 wave_growth_log2: int = 0, final_test: bool = False, estimator: str = "learned",
                 res_m: float = 8.0, test_steps: int = 0, scan_kernel: str = "auto",
-                candidate_budget_bytes: int = 0) -> None:
+                candidate_budget_bytes: int = 0, queries_per_unit: int = 0) -> None:
     """Enqueue a search on ``stream`` (a torch.cuda.Stream; default: current).
 
     Q: (B, D) float32 CUDA tensor; K, nprobe: (B,) int32 CUDA tensors; ids
@@ -303,15 +304,37 @@ def dade_search(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: in
     estimator "learned" (the installed tables) or "res" (the Gaussian-bound
     test with multiplier res_m); test_steps > 0 tests only the first
     test_steps steps; scan_kernel "auto" / "tensor" / "cuda" picks the
-    estimate-and-prune kernel of the learned test."""
+    estimate-and-prune kernel of the learned test; candidate_budget_bytes
+    bounds the candidate buffer (0: the library default) and
+    queries_per_unit the queries sharing one staged tile (0: the kernel's
+    maximum)."""
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     o = _opts(mode, max_K, max_nprobe, first_wave, tau, probe_in, probe_out, qrot_out, stats, status,
               workspace, wave_growth_log2, final_test, estimator, res_m, test_steps, scan_kernel,
-              candidate_budget_bytes)
+              candidate_budget_bytes, queries_per_unit)
     _check(library().dade_search(idx.ptr, _ptr(Q), int(Q.shape[0]), _ptr(K), _ptr(nprobe), int(delta_d),
                                  ctypes.byref(o), _ptr(ids), _ptr(dists), _ptr(offsets),
                                  ctypes.c_void_p(s.cuda_stream)))
+
+
+def dade_search_kernel_count(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: int, max_nprobe: int,
+                             workspace, offsets=None, **kw) -> int:
+    """How many kernels dade_search with these arguments launches (captured
+    into a CUDA graph, not run).  Keyword arguments as for dade_search; a
+    workspace is required."""
+    o = _opts(kw.pop("mode", "prune"), max_K, max_nprobe, kw.pop("first_wave", 0), kw.pop("tau", None),
+              kw.pop("probe_in", None), kw.pop("probe_out", None), kw.pop("qrot_out", None), kw.pop("stats", None),
+              kw.pop("status", None), workspace, kw.pop("wave_growth_log2", 0), kw.pop("final_test", False),
+              kw.pop("estimator", "learned"), kw.pop("res_m", 8.0), kw.pop("test_steps", 0),
+              kw.pop("scan_kernel", "auto"), kw.pop("candidate_budget_bytes", 0), kw.pop("queries_per_unit", 0))
+    if kw:
+        raise TypeError(f"unknown arguments {sorted(kw)}")
+    n = ctypes.c_int64()
+    _check(library().dade_search_kernel_count(idx.ptr, _ptr(Q), int(Q.shape[0]), _ptr(K), _ptr(nprobe),
+                                              int(delta_d), ctypes.byref(o), _ptr(ids), _ptr(dists), _ptr(offsets),
+                                              ctypes.byref(n)))
+    return int(n.value)
 
 
 def dade_search_noalloc(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, max_K: int,
@@ -319,14 +342,16 @@ def dade_search_noalloc(idx: Index, Q, K, nprobe, delta_d: int, ids, dists, *, m
                         probe_in=None, probe_out=None, qrot_out=None, stats=None, status=None,
                         offsets=None, stream=None, wave_growth_log2: int = 0, final_test: bool = False,
                         estimator: str = "learned", res_m: float = 8.0, test_steps: int = 0,
-                        scan_kernel: str = "auto", candidate_budget_bytes: int = 0) -> None:
+                        scan_kernel: str = "auto", candidate_budget_bytes: int = 0,
+                        queries_per_unit: int = 0) -> None:
     """dade_search whose scratch is the library's fixed device array: for
     callers that cannot allocate device memory.  Same arguments and results
     as dade_search except that no workspace is passed."""
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     o = _opts(mode, max_K, max_nprobe, first_wave, tau, probe_in, probe_out, qrot_out, stats, status, None,
-              wave_growth_log2, final_test, estimator, res_m, test_steps, scan_kernel, candidate_budget_bytes)
+              wave_growth_log2, final_test, estimator, res_m, test_steps, scan_kernel, candidate_budget_bytes,
+              queries_per_unit)
     _check(library().dade_search_noalloc(idx.ptr, _ptr(Q), int(Q.shape[0]), _ptr(K), _ptr(nprobe),
                                          int(delta_d), ctypes.byref(o), _ptr(ids), _ptr(dists), _ptr(offsets),
                                          ctypes.c_void_p(s.cuda_stream)))
@@ -408,8 +433,10 @@ def dade_merge_topk(ids, dists, K, ids_out, dists_out, *, max_K: int, stream=Non
                                      _ptr(dists_out), ctypes.c_void_p(s.cuda_stream)))
 
 
-def dade_stage_timing(enable: bool) -> None:
-    _check(library().dade_stage_timing(1 if enable else 0))
+def dade_stage_timing(enable: bool, tensor_only: bool = False) -> None:
+    """Event timing of the scan launches (all of them, or the tensor-core
+    scan's alone) and their staged bytes."""
+    _check(library().dade_stage_timing((2 if tensor_only else 1) if enable else 0))
 
 
 def dade_stage_timing_read():

@@ -34,7 +34,8 @@ class SearchOpts(ctypes.Structure):
                 ("qrot_out_dev", c_vp), ("stats_dev", c_vp), ("status_dev", c_vp),
                 ("workspace", c_vp), ("workspace_bytes", c_sz), ("wave_growth_log2", c_i32),
                 ("final_test", c_i32), ("estimator", c_i32), ("res_m", ctypes.c_float),
-                ("test_steps", c_i32), ("scan_kernel", c_i32), ("candidate_budget_bytes", c_i64)]
+                ("test_steps", c_i32), ("scan_kernel", c_i32), ("candidate_budget_bytes", c_i64),
+                ("queries_per_unit", c_i32)]
 
 
 class IndexInfo(ctypes.Structure):
@@ -67,6 +68,8 @@ SIGNATURES = {
     "dade_search_noalloc": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i32, ctypes.POINTER(SearchOpts),
                                            c_vp, c_vp, c_vp, c_vp]),
     "dade_search_workspace_size": (c_sz, [c_vp, c_i64, c_i32, ctypes.POINTER(SearchOpts)]),
+    "dade_search_kernel_count": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i32, ctypes.POINTER(SearchOpts),
+                                                c_vp, c_vp, c_vp, ctypes.POINTER(c_i64)]),
     "dade_index_info_get": (ctypes.c_int, [c_vp, ctypes.POINTER(IndexInfo)]),
     "dade_index_centroids": (ctypes.c_int, [c_vp, c_vp]),
     "dade_index_assignment": (ctypes.c_int, [c_vp, c_vp]),

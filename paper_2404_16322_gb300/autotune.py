@@ -48,14 +48,20 @@ class Bench:
                  for m in ("prune", "full") for dd in deltas for fw, g in sched)
         self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
 
-    def run(self, nprobe, delta_d, mode, first_wave=1, stats=False, growth=0, final_test=False):
+    def run(self, nprobe, delta_d, mode, first_wave=1, stats=False, growth=0, final_test=False,
+            scan_kernel="auto", queries_per_unit=0):
         self.np.fill_(nprobe)
         if stats:
             self.stats.zero_()
+        self._search(nprobe, delta_d, mode, first_wave, stats, growth, final_test, scan_kernel, queries_per_unit)
+
+    def _search(self, nprobe, delta_d, mode, first_wave, stats, growth, final_test, scan_kernel, queries_per_unit):
         self.G.dade_search(self.idx, self.q, self.k, self.np, delta_d, self.ids, self.d, max_K=self.K,
                            max_nprobe=nprobe, mode=mode, status=self.status, first_wave=first_wave,
                            stats=self.stats if stats else None, workspace=self.ws, wave_growth_log2=growth,
-                           final_test=final_test, estimator=self.estimator, res_m=self.res_m)
+                           final_test=final_test, estimator=self.estimator, res_m=self.res_m,
+                           scan_kernel=scan_kernel if mode == "prune" else "auto",
+                           queries_per_unit=queries_per_unit)
 
     def result(self) -> np.ndarray:
         self.torch.cuda.synchronize()
@@ -64,11 +70,38 @@ class Bench:
             raise RuntimeError(f"device status {st}")
         return self.ids.view(self.B, self.K).cpu().numpy()
 
-    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1, growth=0, final_test=False):
-        """Returns (total ms, per-step ms list), CUDA events on the stream."""
+    def capture(self, nprobe, delta_d, mode, first_wave=1, growth=0, final_test=False, scan_kernel="auto",
+                queries_per_unit=0):
+        """One search of this configuration captured in a CUDA graph (the
+        per-query nprobe is set outside the graph, once)."""
         torch = self.torch
+        self.run(nprobe, delta_d, mode, first_wave, growth=growth, final_test=final_test, scan_kernel=scan_kernel,
+                 queries_per_unit=queries_per_unit)  # kernel attributes and module loads outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=s):
+            self._search(nprobe, delta_d, mode, first_wave, False, growth, final_test, scan_kernel,
+                         queries_per_unit)
+        torch.cuda.synchronize()
+        return g
+
+    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1, growth=0, final_test=False,
+             scan_kernel="auto", queries_per_unit=0, graph=False):
+        """Returns (total ms, per-step ms list), CUDA events on the stream;
+        graph=True replays one captured search per step."""
+        torch = self.torch
+        kw = dict(growth=growth, final_test=final_test, scan_kernel=scan_kernel, queries_per_unit=queries_per_unit)
+        if graph:
+            g = self.capture(nprobe, delta_d, mode, first_wave, **kw)
+            step = g.replay
+        else:
+            self.np.fill_(nprobe)
+            step = (lambda: self._search(nprobe, delta_d, mode, first_wave, False, growth, final_test, scan_kernel,
+                                         queries_per_unit))
         for _ in range(warmup):
-            self.run(nprobe, delta_d, mode, first_wave, growth=growth, final_test=final_test)
+            step()
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         t0 = torch.cuda.Event(enable_timing=True)
@@ -76,7 +109,7 @@ class Bench:
         t0.record()
         for e0, e1 in evs:
             e0.record()
-            self.run(nprobe, delta_d, mode, first_wave, growth=growth, final_test=final_test)
+            step()
             e1.record()
         t1.record()
         torch.cuda.synchronize()
@@ -92,19 +125,24 @@ def cache_key(G, idx, K: int, target: float, mode: str) -> str:
             f"|{h}|K{K}|r{target}|{mode}")
 
 
-SCHEDULES = ((1, 1), (4, 1), (8, 1), (8, 2), (4, 30), (8, 30), (16, 30))
+SCHEDULES = ((1, 1), (4, 1), (8, 1), (8, 2), (4, 2), (2, 30), (4, 30), (8, 30), (16, 30))
+# (scan kernel, queries per unit, final test) tried at the chosen schedule
+KNOBS = (("auto", 0, False), ("auto", 0, True), ("tensor", 64, False), ("tensor", 32, False),
+         ("cuda", 0, False), ("cuda", 8, False))
 
 
 def autotune(bench: Bench, gt: np.ndarray, target: float = 0.95, k_recall: int = 10,
              deltas=(8, 16, 32), schedules=SCHEDULES,
              nprobes=(8, 16, 24, 32, 48, 64, 96, 128, 192, 256), reps: int = 5, warmup: int = 2,
-             mode: str = "prune"):
+             mode: str = "prune", knobs=KNOBS):
     """Returns (best configuration, every configuration tried).
 
     The smallest nprobe whose full-dimension scan reaches the target is found
     first (pruning can only lose recall); every (Delta_d, first wave, growth)
     schedule is then timed from that nprobe up to the first that reaches the
-    target.  Mode "full" tunes the full-dimension scan's schedule the same way."""
+    target, and the kernel knobs (scan kernel, queries per work unit, final
+    test) are timed at the fastest.  Mode "full" tunes the full-dimension
+    scan's schedule the same way."""
     tried = []
     start = 0
     for i, npb in enumerate(nprobes):
@@ -122,21 +160,34 @@ def autotune(bench: Bench, gt: np.ndarray, target: float = 0.95, k_recall: int =
                 rec = recall_at(bench.result(), gt, k_recall)
                 _, per = bench.time(npb, dd, mode, reps, warmup, fw, growth=g)
                 tried.append(dict(mode=mode, delta_d=dd, first_wave=fw, growth=g, nprobe=npb, recall=rec,
-                                  ms=float(np.median(per)), final_test=False))
+                                  ms=float(np.median(per)), final_test=False, scan_kernel="auto",
+                                  queries_per_unit=0))
                 if rec >= target:
                     break
     ok = [t for t in tried if t["recall"] >= target]
     best = min(ok, key=lambda t: t["ms"]) if ok else max(tried, key=lambda t: t["recall"])
     if mode == "prune" and bench.estimator != "pq":
-        # the test on the completed distance changes no result, only the time
-        # (OPQ-L has a single test and no such variant)
+        # kernel knobs at the chosen configuration: which estimate-and-prune
+        # kernel runs the later waves and how many queries share a staged
+        # tile; the test on the completed distance.  None changes the
+        # decisions (up to the kernels' rounding), so recall is re-measured
+        # but the nprobe search is not repeated.
         b = best
-        _, per = bench.time(b["nprobe"], b["delta_d"], mode, reps, warmup, b["first_wave"], growth=b["growth"],
-                            final_test=True)
-        t = dict(b, ms=float(np.median(per)), final_test=True)
-        tried.append(t)
-        if t["ms"] < b["ms"]:
-            best = t
+        for kern, qpu, fin in knobs:
+            if (kern, qpu, fin) == ("auto", 0, False):
+                continue
+            try:
+                bench.run(b["nprobe"], b["delta_d"], mode, b["first_wave"], growth=b["growth"], final_test=fin,
+                          scan_kernel=kern, queries_per_unit=qpu)
+                rec = recall_at(bench.result(), gt, k_recall)
+            except Exception:  # a knob the index or step width does not support
+                continue
+            _, per = bench.time(b["nprobe"], b["delta_d"], mode, reps, warmup, b["first_wave"], growth=b["growth"],
+                                final_test=fin, scan_kernel=kern, queries_per_unit=qpu)
+            t = dict(b, ms=float(np.median(per)), final_test=fin, scan_kernel=kern, queries_per_unit=qpu, recall=rec)
+            tried.append(t)
+            if rec >= min(target, b["recall"]) and t["ms"] < best["ms"]:
+                best = t
     return best, tried
 
 

@@ -19,6 +19,7 @@ namespace {
 struct StageTiming {
     std::mutex mu;
     bool on = false;
+    bool only_tensor = false;  // time the tensor-core scan launches alone
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     unsigned long long* bytes = nullptr;
 };
@@ -129,7 +130,10 @@ int wave_kernel(const dade_index* idx, int32_t delta_d, const dade_search_opts& 
 
 // Queries per work unit of a wave: the tensor-core kernel takes up to 128
 // or 256 (its MMA N), the CUDA-core kernels kG.
-int wave_qgroup(int kernel, int32_t delta_d) { return kernel == WK_TENSOR ? tc_scan_qmax(delta_d) : kG; }
+int wave_qgroup(int kernel, int32_t delta_d, int32_t requested) {
+    const int qmax = kernel == WK_TENSOR ? tc_scan_qmax(delta_d) : kG;
+    return requested > 0 ? std::min<int>(requested, qmax) : qmax;
+}
 
 size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_search_opts& o, char* base, Plan* pl) {
     const int P = o.max_nprobe, Kmax = o.max_K;
@@ -168,7 +172,7 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     int64_t ucap = 0;
     for (int w = 0; w < nw; ++w) {
         const int64_t width = v.pass_begin[w + 1] - v.pass_begin[w];
-        const int qg = wave_qgroup(wave_kernel(idx, delta_d, o, pl->pass_wave[w]), delta_d);
+        const int qg = wave_qgroup(wave_kernel(idx, delta_d, o, pl->pass_wave[w]), delta_d, o.queries_per_unit);
         v.ubase[w] = ucap;
         v.qgroup[w] = qg;
         ucap += (ceil_div(B * width, qg) + std::min<int64_t>(nl, B * width)) * ntile_max;
@@ -209,6 +213,7 @@ dade_status check_args(const dade_index* idx, int64_t B, int32_t delta_d, const 
     if (o.mode != DADE_SCAN_PRUNE && o.mode != DADE_SCAN_FULL) return fail(DADE_EINVAL, "bad mode");
     if (o.first_wave < 0) return fail(DADE_EINVAL, "first_wave < 0");
     if (o.candidate_budget_bytes < 0) return fail(DADE_EINVAL, "candidate_budget_bytes < 0");
+    if (o.queries_per_unit < 0) return fail(DADE_EINVAL, "queries_per_unit < 0");
     if (o.wave_growth_log2 < 0 || o.wave_growth_log2 > 30) return fail(DADE_EINVAL, "wave_growth_log2 must be in [0, 30]");
     if (o.estimator != DADE_EST_LEARNED && o.estimator != DADE_EST_RES && o.estimator != DADE_EST_PQ)
         return fail(DADE_EINVAL, "bad estimator");
@@ -372,15 +377,17 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
             }
             DADE_CUDA_TRY(launch_collect(ix, v, w, delta_d, S, ca, collect->query_offset, st));
         }
+        // wave 0 has tau = +inf for every query (no frozen tau): every
+        // candidate's exact distance, through the full-scan kernel
+        const int wk = wave_kernel(idx, delta_d, o, pl.pass_wave[w]);
+        const bool timed_here = timed && (tm.only_tensor == 0 || wk == WK_TENSOR);
+        v.staged_bytes = timed_here ? tm.bytes : nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (timed) {
+        if (timed_here) {
             DADE_CUDA_TRY(cudaEventCreate(&e0));
             DADE_CUDA_TRY(cudaEventCreate(&e1));
             DADE_CUDA_TRY(cudaEventRecord(e0, st));
         }
-        // wave 0 has tau = +inf for every query (no frozen tau): every
-        // candidate's exact distance, through the full-scan kernel
-        const int wk = wave_kernel(idx, delta_d, o, pl.pass_wave[w]);
         if (wk == WK_PQ) {
             PQView pv{idx->pq_codes_dev.as<uint8_t>(), idx->pq_err_dev.as<float>(), pl.pq_lut, idx->total_slots,
                       idx->pq_m, idx->pq_m1, idx->pq_m3, idx->pq_beta};
@@ -391,7 +398,7 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
         } else {
             DADE_CUDA_TRY(launch_wave_scan(ix, v, w, wk == WK_EXACT, delta_d, m1, beta, S, st));
         }
-        if (timed) {
+        if (timed_here) {
             DADE_CUDA_TRY(cudaEventRecord(e1, st));
             std::lock_guard<std::mutex> lk(tm.mu);
             tm.ev.emplace_back(e0, e1);
@@ -414,6 +421,46 @@ extern "C" dade_status dade_search(const dade_index* idx, const float* Q_dev, in
                              out_offsets_dev, static_cast<cudaStream_t>(cuda_stream), nullptr);
 }
 
+extern "C" dade_status dade_search_kernel_count(const dade_index* idx, const float* Q_dev, int64_t B,
+                                               const int32_t* K_dev, const int32_t* nprobe_dev, int32_t delta_d,
+                                               const dade_search_opts* opts, int64_t* ids_dev, float* dists_dev,
+                                               const int64_t* out_offsets_dev, int64_t* count) {
+    dade::clear_error();
+    if (!opts || !count) return dade::fail(DADE_EINVAL, "opts and count are required");
+    if (!opts->workspace) return dade::fail(DADE_EINVAL, "a workspace is required to count launches");
+    cudaStream_t st = nullptr;
+    DADE_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    dade_status s = DADE_OK;
+    if (e == cudaSuccess) {
+        s = dade::search_impl(idx, Q_dev, B, K_dev, nprobe_dev, delta_d, *opts, ids_dev, dists_dev,
+                              out_offsets_dev, st, nullptr);
+        e = cudaStreamEndCapture(st, &g);
+    }
+    int64_t n = 0;
+    if (e == cudaSuccess && s == DADE_OK && g) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+        for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+            cudaGraphNodeType t;
+            e = cudaGraphNodeGetType(nodes[i], &t);
+            if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ++n;
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(st);
+    if (s != DADE_OK) return s;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return dade::fail(DADE_ECUDA, "graph capture for the launch count: %s", cudaGetErrorString(e));
+    }
+    *count = n;
+    return DADE_OK;
+}
+
 extern "C" dade_status dade_stage_timing(int32_t enable) {
     dade::clear_error();
     dade::StageTiming& t = dade::timing();
@@ -423,6 +470,7 @@ extern "C" dade_status dade_stage_timing(int32_t enable) {
         DADE_CUDA_TRY(cudaMemset(t.bytes, 0, sizeof(unsigned long long)));
     }
     t.on = enable != 0;
+    t.only_tensor = enable == 2;
     return DADE_OK;
 }
 

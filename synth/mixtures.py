@@ -150,6 +150,9 @@ WORKLOADS = {
                    n_train=10_000, nlist=4096, nprobe=128, K=100, delta_d=32),
     "vmf10m": dict(spec=VmfSpec(D=96, n_comp=2048), N=10_000_000, n_queries=20_000,
                    n_train=10_000, nlist=4096, nprobe=256, K=100, delta_d=16),
+    # The first index of the two-index serving mix (the second is gist1m).
+    "serve2m": dict(spec=MixtureSpec(D=256, n_comp=256, alpha=1.0, mean_scale=0.65), N=2_000_000,
+                    n_queries=20_000, n_train=10_000, nlist=4096, nprobe=64, K=100, delta_d=32),
 }
 
 

@@ -72,7 +72,7 @@ def build_gpu(G, X, inp, nlist, dtype="f32", delta_d=16):
 
 def gpu_search(G, idx, Q, K, nprobe, delta_d, mode="prune", probe_in=None, tau=None, max_K=None,
                max_nprobe=None, first_wave=0, growth=0, final_test=False, estimator="learned", res_m=8.0,
-               test_steps=0, want=(), scan_kernel="auto", candidate_budget_bytes=0):
+               test_steps=0, want=(), scan_kernel="auto", candidate_budget_bytes=0, queries_per_unit=0):
     import torch
     B = Q.shape[0]
     Kv = np.broadcast_to(np.asarray(K, np.int32), (B,)).copy()
@@ -99,6 +99,7 @@ def gpu_search(G, idx, Q, K, nprobe, delta_d, mode="prune", probe_in=None, tau=N
                   first_wave=first_wave, tau=tin, probe_in=pin, status=status, wave_growth_log2=growth,
                   final_test=final_test, estimator=estimator, res_m=res_m, test_steps=test_steps,
                   scan_kernel=scan_kernel, candidate_budget_bytes=candidate_budget_bytes,
+                  queries_per_unit=queries_per_unit,
                   **{kw: t for kw, t in extra.values()})
     torch.cuda.synchronize()
     st = int(status.item())

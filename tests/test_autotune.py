@@ -2,8 +2,9 @@
 batch: it starts from the smallest nprobe whose full scan reaches the recall
 target, raises nprobe per (Delta_d, schedule) until the target is met, keeps
 the fastest configuration that meets it, tries the test on the completed
-distance for the learned estimator only, and falls back to the best recall
-when nothing meets the target."""
+distance and the kernel knobs (scan kernel, queries per work unit) at the
+chosen configuration for the learned estimator only, and falls back to the
+best recall when nothing meets the target."""
 import numpy as np
 
 from paper_2404_16322_gb300 import autotune
@@ -13,9 +14,11 @@ class FakeBench:
     """Recall grows with nprobe (0.9 at 8, +0.02 per doubling step of the
     grid); time grows with nprobe and depends on (Delta_d, schedule)."""
 
-    def __init__(self, estimator="learned", recall_shift=0.0):
+    def __init__(self, estimator="learned", recall_shift=0.0, knob_ms=None, knob_recall=None):
         self.estimator = estimator
         self.shift = recall_shift
+        self.knob_ms = knob_ms or {}  # (scan kernel, queries per unit) -> time offset
+        self.knob_recall = knob_recall or {}
         self.calls = []
         self._last = None
         self.K = 10
@@ -24,9 +27,10 @@ class FakeBench:
         grid = [8, 16, 24, 32, 48, 64, 96, 128]
         return min(1.0, 0.9 + 0.02 * grid.index(nprobe) + self.shift - (0.001 if mode == "prune" else 0.0))
 
-    def run(self, nprobe, delta_d, mode, first_wave=1, stats=False, growth=0, final_test=False):
-        self.calls.append((nprobe, delta_d, mode, first_wave, growth, final_test))
-        self._last = self._recall(nprobe, mode)
+    def run(self, nprobe, delta_d, mode, first_wave=1, stats=False, growth=0, final_test=False, scan_kernel="auto",
+            queries_per_unit=0):
+        self.calls.append((nprobe, delta_d, mode, first_wave, growth, final_test, scan_kernel, queries_per_unit))
+        self._last = self._recall(nprobe, mode) + self.knob_recall.get((scan_kernel, queries_per_unit), 0.0)
 
     def result(self):
         # ids whose recall@10 against gt = arange(10) per query is _last
@@ -34,10 +38,12 @@ class FakeBench:
         row = np.concatenate([np.arange(hit), 100 + np.arange(10 - hit)])
         return np.tile(row, (4, 1))
 
-    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1, growth=0, final_test=False):
-        self.calls.append((nprobe, delta_d, mode, first_wave, growth, final_test))
+    def time(self, nprobe, delta_d, mode, steps, warmup, first_wave=1, growth=0, final_test=False,
+             scan_kernel="auto", queries_per_unit=0, graph=False):
+        self.calls.append((nprobe, delta_d, mode, first_wave, growth, final_test, scan_kernel, queries_per_unit))
         ms = nprobe * (1.0 if mode == "full" else 0.5 + 0.01 * delta_d) + (0.3 if growth == 1 else 0.0)
         ms += 0.05 if final_test else 0.0
+        ms += self.knob_ms.get((scan_kernel, queries_per_unit), 0.1)
         ms -= 0.001 * first_wave
         return ms * steps, [ms] * max(steps, 1)
 
@@ -59,6 +65,20 @@ def test_picks_the_fastest_configuration_that_meets_the_target():
     # the completed-distance test was tried once, on the best configuration, and lost
     fin = [t for t in tried if t["final_test"]]
     assert len(fin) == 1 and not best["final_test"]
+    assert best["scan_kernel"] == "auto" and best["queries_per_unit"] == 0
+    # every kernel knob was timed once, at the chosen configuration
+    kn = [t for t in tried if (t["scan_kernel"], t["queries_per_unit"]) != ("auto", 0)]
+    assert len(kn) == len(autotune.KNOBS) - 2
+    assert all((t["nprobe"], t["delta_d"], t["growth"]) == (32, 8, 30) for t in kn)
+
+
+def test_a_faster_kernel_knob_is_kept_unless_it_loses_recall():
+    b = FakeBench(knob_ms={("auto", 0): 0.1, ("tensor", 64): -0.2, ("cuda", 8): -0.3},
+                  knob_recall={("cuda", 8): -0.2})
+    best, tried = autotune.autotune(b, GT, 0.95, 10, (8,), nprobes=NPROBES, mode="prune")
+    # cuda/8 is fastest but falls below the target; tensor/64 is next
+    assert (best["scan_kernel"], best["queries_per_unit"]) == ("tensor", 64)
+    assert best["recall"] >= 0.95
 
 
 def test_the_completed_distance_test_is_not_tried_for_opq():
@@ -66,6 +86,7 @@ def test_the_completed_distance_test_is_not_tried_for_opq():
     best, tried = autotune.autotune(b, GT, 0.95, 10, (16,), nprobes=NPROBES, mode="prune")
     assert not any(t["final_test"] for t in tried)
     assert not any(c[5] for c in b.calls)
+    assert all(c[6] == "auto" and c[7] == 0 for c in b.calls)
 
 
 def test_full_mode_tunes_only_the_schedule():

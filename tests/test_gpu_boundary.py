@@ -145,3 +145,29 @@ def test_ivf_build_from_device_rows(G):
     finally:
         a.close()
         b.close()
+
+
+def test_kernel_count_of_a_search(G, pre):
+    """dade_search_kernel_count captures the call without running it: the
+    outputs stay untouched, and more passes mean more launches (one scan and
+    one merge per pass)."""
+    import torch
+    idx, Q = pre["idx"], pre["Q"]
+    B = len(Q)
+    q = _dev(torch, Q, np.float32)
+    k = torch.full((B,), 10, dtype=torch.int32, device="cuda")
+    n = torch.full((B,), 8, dtype=torch.int32, device="cuda")
+    ids = torch.full((B * 10,), -7, dtype=torch.int64, device="cuda")
+    d = torch.full((B * 10,), -7.0, dtype=torch.float32, device="cuda")
+    counts = {}
+    for budget in (0, 1):
+        kw = dict(max_K=10, max_nprobe=8, first_wave=1, wave_growth_log2=1, candidate_budget_bytes=budget)
+        ws = torch.empty(G.dade_search_workspace_size(idx, B, 16, 10, 8, first_wave=1, wave_growth_log2=1,
+                                                      candidate_budget_bytes=budget), dtype=torch.uint8,
+                         device="cuda")
+        counts[budget] = G.dade_search_kernel_count(idx, q, k, n, 16, ids, d, workspace=ws, **kw)
+    torch.cuda.synchronize()
+    assert np.all(ids.cpu().numpy() == -7)
+    # waves of ranks [0,1) [1,2) [2,4) [4,8): 4 passes; one rank per pass: 8
+    assert counts[1] - counts[0] == 2 * (8 - 4)
+    assert counts[0] > 2 * 4

@@ -405,3 +405,18 @@ def test_passes_within_a_wave_change_nothing(G, tiny_pre, kernel, fw, g):
                                          candidate_budget_bytes=1)
     big = G.dade_search_workspace_size(s["idx"], 100, 16, 10, 8, first_wave=fw, wave_growth_log2=g)
     assert small <= big
+
+
+@pytest.mark.parametrize("kernel,qpu", [("tensor", 16), ("tensor", 48), ("cuda", 4)])
+def test_queries_per_unit_changes_nothing(G, tiny_pre, kernel, qpu):
+    """Fewer queries per work unit (more units, each staging its tile for
+    fewer queries): the same ids, distances and work counters."""
+    s = tiny_pre
+    oidx = s["inp"]["oidx"]
+    pr = oidx.probe(oidx.rotate_queries(s["Q"]), 8)
+    kw = dict(probe_in=pr, first_wave=2, growth=30, scan_kernel=kernel, want=("stats",))
+    a = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, **kw)
+    b = H.gpu_search(G, s["idx"], s["Q"], 10, 8, 16, queries_per_unit=qpu, **kw)
+    assert a["status"] == 0 and b["status"] == 0
+    for k in ("ids", "dists", "stats"):
+        assert np.array_equal(a[k], b[k]), k
