@@ -184,6 +184,20 @@ dade_status dade_fit_collect(dade_index* idx, const float* train_q_host, int64_t
                              float* partials_host, float* tau_host, int8_t* label_host, int64_t* query_host,
                              int64_t* id_host);
 
+/* dade_partials_collect: every candidate of each query's nprobe nearest
+ * buckets (Q_host: nq x D FP32 queries, original space), each with its
+ * partial distances dis'_1..dis'_{S-1} (S = ceil(Dpad / delta_d)) over the
+ * stored slabs, computed by the search's CUDA-core arithmetic (the partial
+ * squared distance of Section IV-B over the first s * delta_d rotated
+ * dims): the estimate-quality measurement of Section VII (Exp-7) on the
+ * device.  Rows are sorted by (query, id) into partials (n x (S-1)), query
+ * (n) and id (n), host, caller-owned; *n_rows receives the count, also when
+ * it exceeds max_rows, which returns DADE_EINVAL.  Errors: DADE_EINVAL
+ * (nprobe outside [1, nlist], delta_d not 8/16/32), DADE_ENOMEM, DADE_ECUDA. */
+dade_status dade_partials_collect(const dade_index* idx, const float* Q_host, int64_t nq, int32_t nprobe,
+                                  int32_t delta_d, int64_t max_rows, int64_t* n_rows, float* partials_host,
+                                  int64_t* query_host, int64_t* id_host);
+
 dade_status dade_fit_samples(const double* partials, const double* tau, const int8_t* label,
                              int64_t n, int32_t D, int32_t delta_d, double target_recall,
                              int32_t min_label0, double* m1_out, double* beta_out);

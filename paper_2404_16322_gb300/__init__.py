@@ -171,6 +171,24 @@ def dade_fit_collect(idx: Index, T, K: int, nprobe: int, delta_d: int, seed: int
     return dict(partials=P[:m, :S - 1], tau=tau[:m], label=lab[:m], query=qi[:m], id=ii[:m])
 
 
+def dade_partials_collect(idx: Index, Q, nprobe: int, delta_d: int, max_rows: int | None = None) -> dict:
+    """Every candidate of each query's nprobe nearest buckets with its
+    partial distances over the stored slabs, sorted by (query, id):
+    dict(partials[n, S-1], query[n], id[n])."""
+    Q = _host(Q, np.float32)
+    info = dade_index_info_get(idx)
+    S = n_steps(info["D"], delta_d)
+    cap = int(max_rows) if max_rows is not None else len(Q) * int(info["N"])
+    n = ctypes.c_int64(0)
+    P = np.empty((max(cap, 1), max(S - 1, 1)), np.float32)
+    qi = np.empty(max(cap, 1), np.int64)
+    ii = np.empty(max(cap, 1), np.int64)
+    _check(library().dade_partials_collect(idx.ptr, Q.ctypes.data, len(Q), int(nprobe), int(delta_d), cap,
+                                           ctypes.byref(n), P.ctypes.data, qi.ctypes.data, ii.ctypes.data))
+    m = n.value
+    return dict(partials=P[:m, :S - 1], query=qi[:m], id=ii[:m])
+
+
 def dade_fit_samples(partials, tau, label, D: int, delta_d: int, target_recall: float = 0.995,
                      min_label0: int = 100):
     P = _host(partials, np.float64)

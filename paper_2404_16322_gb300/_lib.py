@@ -60,6 +60,8 @@ SIGNATURES = {
                                            c_vp, c_vp]),
     "dade_fit_collect": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_u64, c_i64, c_i64,
                                         ctypes.POINTER(c_i64), c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "dade_partials_collect": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i64, ctypes.POINTER(c_i64),
+                                             c_vp, c_vp, c_vp]),
     "dade_fit_samples": (ctypes.c_int, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_f64, c_i32, c_vp, c_vp]),
     "dade_set_correction": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),
     "dade_get_correction": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),

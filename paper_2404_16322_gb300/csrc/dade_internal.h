@@ -287,6 +287,8 @@ struct CollectArgs {
     int8_t* label;            // row_cap
     int64_t* query;           // row_cap or null: training-query index of each row
     int64_t* id;              // row_cap or null: id of each row's candidate
+    int32_t keep_all;         // emit every candidate (also where tau is +inf);
+                              // label 2 = neither label 0 nor label 1
 };
 
 }  // namespace dade

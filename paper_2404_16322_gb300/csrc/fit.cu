@@ -244,6 +244,108 @@ extern "C" dade_status dade_fit_collect(dade_index* idx, const float* Tq, int64_
     return DADE_OK;
 }
 
+extern "C" dade_status dade_partials_collect(const dade_index* idx, const float* Q_host, int64_t nq, int32_t nprobe,
+                                             int32_t delta_d, int64_t max_rows, int64_t* n_rows, float* partials,
+                                             int64_t* query, int64_t* id) {
+    clear_error();
+    if (!idx || !n_rows) return fail(DADE_EINVAL, "null index or n_rows");
+    if (nq < 0 || max_rows < 0) return fail(DADE_EINVAL, "nq and max_rows must be >= 0");
+    if (nq > 0 && !Q_host) return fail(DADE_EINVAL, "null queries");
+    if (nprobe < 1 || nprobe > idx->nlist) return fail(DADE_EINVAL, "nprobe must be in [1, nlist]");
+    if (delta_d != 8 && delta_d != 16 && delta_d != 32) return fail(DADE_EINVAL, "delta_d must be 8, 16 or 32");
+    *n_rows = 0;
+    const int S = (int)ceil_div(idx->Dpad, delta_d);
+    if (nq == 0 || S <= 1) return DADE_OK;
+    if (max_rows > 0 && (!partials || !query || !id)) return fail(DADE_EINVAL, "null output");
+
+    cudaStream_t st;
+    DADE_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct G {
+        const dade_index* idx;
+        cudaStream_t s;
+        ~G() {
+            idx->ws.drop(s);
+            cudaStreamDestroy(s);
+        }
+    } guard{idx, st};
+    const int64_t Bc = std::min<int64_t>(nq, 1024);
+    const int D = idx->D;
+    const int64_t cap = std::max<int64_t>(1, max_rows);
+    DevBuf q, kk, np, ids, dists, cnt, status, rp, rq, ri;
+    DADE_TRY(q.alloc(sizeof(float) * Bc * D));
+    DADE_TRY(kk.alloc(sizeof(int32_t) * Bc));
+    DADE_TRY(np.alloc(sizeof(int32_t) * Bc));
+    DADE_TRY(ids.alloc(sizeof(int64_t) * Bc));
+    DADE_TRY(dists.alloc(sizeof(float) * Bc));
+    DADE_TRY(cnt.alloc(sizeof(unsigned long long) * 2));
+    DADE_TRY(status.alloc(sizeof(int32_t)));
+    DADE_TRY(rp.alloc(sizeof(float) * cap * (S - 1)));
+    DADE_TRY(rq.alloc(sizeof(int64_t) * cap));
+    DADE_TRY(ri.alloc(sizeof(int64_t) * cap));
+    {
+        std::vector<int32_t> kh((size_t)Bc, 1), nh((size_t)Bc, nprobe);
+        DADE_CUDA_TRY(cudaMemcpy(kk.p, kh.data(), sizeof(int32_t) * Bc, cudaMemcpyHostToDevice));
+        DADE_CUDA_TRY(cudaMemcpy(np.p, nh.data(), sizeof(int32_t) * Bc, cudaMemcpyHostToDevice));
+        DADE_CUDA_TRY(cudaMemset(cnt.p, 0, sizeof(unsigned long long) * 2));
+        DADE_CUDA_TRY(cudaMemset(status.p, 0, sizeof(int32_t)));
+    }
+    // one wave over all nprobe buckets, pruning off: every candidate is
+    // visited once and emitted with its partial distances
+    dade_search_opts o{};
+    o.mode = DADE_SCAN_FULL;
+    o.max_K = 1;
+    o.max_nprobe = nprobe;
+    o.first_wave = nprobe;
+    o.status_dev = status.as<int32_t>();
+    CollectArgs ca{};
+    ca.pass = 1;
+    ca.keep_all = 1;
+    ca.keep_rate = 1.0;
+    ca.n_label1 = cnt.as<unsigned long long>();
+    ca.n_rows = cnt.as<unsigned long long>() + 1;
+    ca.row_cap = max_rows;
+    ca.partials = rp.as<float>();
+    ca.query = rq.as<int64_t>();
+    ca.id = ri.as<int64_t>();
+    for (int64_t b0 = 0; b0 < nq; b0 += Bc) {
+        const int64_t B = std::min(Bc, nq - b0);
+        DADE_CUDA_TRY(cudaMemcpyAsync(q.p, Q_host + b0 * D, sizeof(float) * B * D, cudaMemcpyHostToDevice, st));
+        ca.query_offset = b0;
+        DADE_TRY(search_impl(idx, q.as<float>(), B, kk.as<int32_t>(), np.as<int32_t>(), delta_d, o,
+                             ids.as<int64_t>(), dists.as<float>(), nullptr, st, &ca));
+        DADE_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    unsigned long long counts[2] = {0, 0};
+    DADE_CUDA_TRY(cudaMemcpy(counts, cnt.p, sizeof counts, cudaMemcpyDeviceToHost));
+    int32_t dev_status = 0;
+    DADE_CUDA_TRY(cudaMemcpy(&dev_status, status.p, sizeof dev_status, cudaMemcpyDeviceToHost));
+    if (dev_status) return fail((dade_status)dev_status, "device status %d during the collection", dev_status);
+    const int64_t n = (int64_t)counts[1];
+    *n_rows = n;
+    if (n > max_rows) return fail(DADE_EINVAL, "%lld candidate rows; max_rows is %lld", (long long)n,
+                                  (long long)max_rows);
+    std::vector<float> pf((size_t)n * (S - 1));
+    std::vector<int64_t> qh((size_t)n), ih((size_t)n);
+    if (n > 0) {
+        DADE_CUDA_TRY(cudaMemcpy(pf.data(), rp.p, sizeof(float) * n * (S - 1), cudaMemcpyDeviceToHost));
+        DADE_CUDA_TRY(cudaMemcpy(qh.data(), rq.p, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+        DADE_CUDA_TRY(cudaMemcpy(ih.data(), ri.p, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+    }
+    std::vector<int64_t> ord((size_t)n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+        if (qh[(size_t)a] != qh[(size_t)b]) return qh[(size_t)a] < qh[(size_t)b];
+        return ih[(size_t)a] < ih[(size_t)b];
+    });
+    for (int64_t i = 0; i < n; ++i) {
+        const size_t o2 = (size_t)ord[(size_t)i];
+        std::copy(pf.begin() + o2 * (S - 1), pf.begin() + (o2 + 1) * (S - 1), partials + i * (S - 1));
+        query[i] = qh[o2];
+        id[i] = ih[o2];
+    }
+    return DADE_OK;
+}
+
 extern "C" dade_status dade_pq_fit_correction(dade_index* idx, const float* Tq, int64_t nt, int32_t K, int32_t nprobe,
                                               double target_recall, uint64_t seed, int64_t label1_cap, float* out3) {
     clear_error();

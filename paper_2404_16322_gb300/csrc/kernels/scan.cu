@@ -543,8 +543,8 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
         for (int g = warp; g < un.nq; g += kWarps) {
             const int q = wv.items[un.item + g];
             const float tau = wv.tau[q];
-            if (isinf(tau)) continue;
-            const int K = wv.K[q];
+            if (isinf(tau) && !ca.keep_all) continue;
+            const int K = ca.topk_ids ? wv.K[q] : 0;
             const float* qp = wv.qpad + (int64_t)q * ix.Dpad;
             const float* qr = wv.qrot + (int64_t)q * ix.Dpad;
             for (int base = 0; base < un.nt; base += 32) {
@@ -556,8 +556,7 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
                     const int64_t pos = (int64_t)un.t * kT + c;
                     const float d = exact_distance(ix.orig + ebase + pos * kBlock, npad, qp, ix.nb);
                     id = ix.ids[slot_l + pos];
-                    const int64_t* top = ca.topk_ids + (int64_t)q * ca.topk_stride;
-                    for (int k = 0; k < K; ++k) lab0 |= top[k] == id;
+                    for (int k = 0; k < K; ++k) lab0 |= ca.topk_ids[(int64_t)q * ca.topk_stride + k] == id;
                     lab1 = !lab0 && d > tau;
                 }
                 if (ca.pass == 0) {
@@ -565,8 +564,8 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
                     if (lane == 0 && bal) atomicAdd(ca.n_label1, (unsigned long long)__popc(bal));
                     continue;
                 }
-                bool emit = lab0;
-                if (lab1) {
+                bool emit = lab0 || (ca.keep_all && valid);
+                if (lab1 && !emit) {
                     // SplitMix64-derived uniform of (seed, query, id)
                     uint64_t key = ((uint64_t)(qoff + q) << 32) ^ (uint64_t)id;
                     auto mix = [](uint64_t z) {
@@ -594,7 +593,7 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
                     ca.partials[(int64_t)row * 2] = dis;
                     ca.partials[(int64_t)row * 2 + 1] = ca.pq_err[slot];
                     ca.tau[row] = tau;
-                    ca.label[row] = lab1 ? 1 : 0;
+                    ca.label[row] = lab0 ? 0 : lab1 ? 1 : 2;
                     continue;
                 }
                 const E* xs = reinterpret_cast<const E*>(ix.slab) + ebase + pos * kBlock;
@@ -610,8 +609,8 @@ __global__ void __launch_bounds__(kScanThreads) collect_kernel(IndexView ix, Wav
                     }
                     ca.partials[(int64_t)row * (S - 1) + k] = p;
                 }
-                ca.tau[row] = tau;
-                ca.label[row] = lab1 ? 1 : 0;
+                if (ca.tau) ca.tau[row] = tau;
+                if (ca.label) ca.label[row] = lab0 ? 0 : lab1 ? 1 : 2;
             }
         }
         __syncthreads();
