@@ -516,6 +516,27 @@ void dade_index_free(dade_index* idx);
 dade_status dade_stage_timing(int32_t enable);
 dade_status dade_stage_timing_read(double* scan_ms, int64_t* scan_launches, double* scan_bytes);
 
+/* ------------------------------------------------------------------------
+ * Workspace arena (host bookkeeping for admission control).  A serving loop
+ * holds one device allocation of `bytes` and hands each batch a byte range
+ * of it for its dade_search workspace; a batch is admitted when a range is
+ * free.  dade_arena_create: ranges are multiples of `align` (a power of
+ * two) within [0, bytes rounded down to align); DADE_EINVAL on bad sizes.
+ * dade_arena_alloc: the offset of the lowest free range of at least `bytes`
+ * (rounded up to align; 0 bytes take one unit), or -1 if none is free.
+ * dade_arena_free: releases the range that starts at `offset` (DADE_EINVAL
+ * if none does) and merges it with free neighbours.  dade_arena_used: bytes
+ * held by live ranges; dade_arena_largest_free: the longest free range.
+ * Thread-safe; no device calls (the arena never touches the memory).
+ * ---------------------------------------------------------------------- */
+typedef struct dade_arena dade_arena;
+dade_status dade_arena_create(int64_t bytes, int64_t align, dade_arena** out);
+int64_t dade_arena_alloc(dade_arena* arena, int64_t bytes);
+dade_status dade_arena_free(dade_arena* arena, int64_t offset);
+int64_t dade_arena_used(const dade_arena* arena);
+int64_t dade_arena_largest_free(const dade_arena* arena);
+void dade_arena_destroy(dade_arena* arena);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dade_last_error(void);
 

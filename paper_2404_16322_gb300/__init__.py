@@ -189,6 +189,42 @@ def dade_partials_collect(idx: Index, Q, nprobe: int, delta_d: int, max_rows: in
     return dict(partials=P[:m, :S - 1], query=qi[:m], id=ii[:m])
 
 
+class Arena:
+    """Offsets into one caller-held device allocation of `size` bytes: the
+    serving loop's admission control (first fit, aligned, coalescing)."""
+
+    def __init__(self, size: int, align: int = 256):
+        self.ptr = ctypes.c_void_p()
+        _check(library().dade_arena_create(int(size), int(align), ctypes.byref(self.ptr)))
+        self.size = int(size) // int(align) * int(align)
+
+    def alloc(self, nbytes: int) -> int:
+        """Offset of the range, or -1 when no free range holds nbytes."""
+        return int(library().dade_arena_alloc(self.ptr, int(nbytes)))
+
+    def free(self, offset: int) -> None:
+        _check(library().dade_arena_free(self.ptr, int(offset)))
+
+    @property
+    def used(self) -> int:
+        return int(library().dade_arena_used(self.ptr))
+
+    @property
+    def largest_free(self) -> int:
+        return int(library().dade_arena_largest_free(self.ptr))
+
+    def close(self):
+        if self.ptr:
+            library().dade_arena_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dade_fit_samples(partials, tau, label, D: int, delta_d: int, target_recall: float = 0.995,
                      min_label0: int = 100):
     P = _host(partials, np.float64)

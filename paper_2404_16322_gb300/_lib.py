@@ -62,6 +62,12 @@ SIGNATURES = {
                                         ctypes.POINTER(c_i64), c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dade_partials_collect": (ctypes.c_int, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i64, ctypes.POINTER(c_i64),
                                              c_vp, c_vp, c_vp]),
+    "dade_arena_create": (ctypes.c_int, [c_i64, c_i64, ctypes.POINTER(c_vp)]),
+    "dade_arena_alloc": (c_i64, [c_vp, c_i64]),
+    "dade_arena_free": (ctypes.c_int, [c_vp, c_i64]),
+    "dade_arena_used": (c_i64, [c_vp]),
+    "dade_arena_largest_free": (c_i64, [c_vp]),
+    "dade_arena_destroy": (None, [c_vp]),
     "dade_fit_samples": (ctypes.c_int, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_f64, c_i32, c_vp, c_vp]),
     "dade_set_correction": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),
     "dade_get_correction": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),

@@ -71,3 +71,47 @@ def test_memory_budget_limits_batch_size(served):
     assert out["status"] == 0 and out["requests"] == 200
     assert out["mean_batch"] <= 32
     assert all(r.ids is not None and len(r.ids) == 10 for r in reqs)
+
+
+def test_two_indices_share_the_arena(served):
+    """Two resident indices of different dimension behind one server: each
+    request's result equals its search alone on its own index, and the
+    arena is empty again afterwards."""
+    import torch
+    from paper_2404_16322_gb300 import serving
+    G, idx, Q = served
+    X2, Q2, T2, cfg2 = synth.workload("tiny", n_train=400, n_queries=200)
+    X2, Q2, T2 = X2[:, :64].copy(), Q2[:, :64].copy(), T2[:, :64].copy()
+    mean, R, _ = G.dade_train_rotation(X2)
+    idx2 = G.ivf_build(X2, mean, R, 32, kmeans_iters=4, seed=5, dtype="bf16")
+    try:
+        G.dade_fit_correction(idx2, T2, 10, 8, 16)
+        tenants = [serving.Tenant(idx, 16, 20, 16, first_wave=2, wave_growth_log2=30),
+                   serving.Tenant(idx2, 16, 20, 16, first_wave=2, wave_growth_log2=30)]
+        srv = serving.Server(G, tenants, buckets=(8, 32, 128), slots=3, use_graphs=False)
+        rng = np.random.default_rng(2)
+        n = 400
+        ten = rng.integers(0, 2, n)
+        qi = rng.integers(0, 200, n)
+        ks = rng.choice([1, 10, 20], n)
+        nps = rng.integers(1, 17, n)
+        arr = serving.poisson_arrivals(n, rate=30_000, seed=9)
+        ids, d, done, out = srv.serve_pool([Q[:200], Q2], ten, qi, ks, nps, arr, max_batch=128)
+        assert out["status"] == 0 and out["requests"] == n and set(out["tenants"]) == {0, 1}
+        assert srv.arena.used == 0
+        dev = torch.device("cuda")
+        for i in range(0, n, 9):
+            t = tenants[ten[i]]
+            q = (Q if ten[i] == 0 else Q2)[qi[i]]
+            oi = torch.empty(20, dtype=torch.int64, device=dev)
+            od = torch.empty(20, dtype=torch.float32, device=dev)
+            G.dade_search(t.idx, torch.from_numpy(q[None, :]).to(dev),
+                          torch.tensor([ks[i]], dtype=torch.int32, device=dev),
+                          torch.tensor([nps[i]], dtype=torch.int32, device=dev), 16, oi, od, max_K=20,
+                          max_nprobe=16, first_wave=2, wave_growth_log2=30)
+            torch.cuda.synchronize()
+            k = int(ks[i])
+            assert np.array_equal(ids[i, :k], oi.cpu().numpy()[:k])
+            assert np.array_equal(d[i, :k], od.cpu().numpy()[:k])
+    finally:
+        idx2.close()
