@@ -165,7 +165,7 @@ def ground_truth(X, Q, k=10, chunk=1024):
     return out
 
 
-SCAN_SOURCES = {"tc_scan_kernel": ["scan_tc.cu", "scan.cuh", "scan_steps.cuh"],
+SCAN_SOURCES = {"tc_scan_kernel": ["scan_tc.cu", "tc_common.cuh", "scan.cuh", "scan_steps.cuh"],
                 "wave_scan_kernel": ["scan.cu", "scan.cuh", "scan_steps.cuh"]}
 PROFILE_OF = {"tc_scan_kernel": "tc_scan_sift1m.md", "wave_scan_kernel": "wave_scan_sift1m.md"}
 

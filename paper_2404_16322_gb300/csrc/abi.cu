@@ -121,6 +121,11 @@ dade_status build_tc_operands(dade_index* idx) {
                                  idx->list_slot_dev.as<int64_t>(), idx->list_size_dev.as<int32_t>(),
                                  idx->tile_base_dev.as<int64_t>(), nl, idx->Dpad, idx->tc_parts, ntiles,
                                  idx->tcslab_dev.as<float>(), 0));
+    if (centroid_tc_supported(idx->Dpad)) {
+        DADE_TRY(idx->cent_tc_dev.alloc(sizeof(float) * 2 * 1024 * (size_t)ceil_div(nl, 128) * (idx->Dpad / 8)));
+        DADE_CUDA_TRY(launch_split_tc(idx->cent_dev.as<float>(), idx->Dpad, nl, idx->Dpad,
+                                      idx->cent_tc_dev.as<float>(), 0));
+    }
     DADE_CUDA_TRY(cudaDeviceSynchronize());
     return DADE_OK;
 }
@@ -203,7 +208,8 @@ extern "C" dade_status dade_index_info_get(const dade_index* idx, dade_index_inf
     out->device_bytes = (int64_t)(idx->slab_dev.bytes + idx->orig_dev.bytes + idx->ids_dev.bytes +
                                   idx->cent_dev.bytes + idx->R_dev.bytes + idx->eps_dev.bytes + idx->var_dev.bytes +
                                   idx->sfx_dev.bytes + idx->pq_codes_dev.bytes + idx->pq_err_dev.bytes +
-                                  idx->pq_cb_dev.bytes + idx->pq_perm_dev.bytes + idx->tcslab_dev.bytes);
+                                  idx->pq_cb_dev.bytes + idx->pq_perm_dev.bytes + idx->tcslab_dev.bytes +
+                                  idx->cent_tc_dev.bytes);
     return DADE_OK;
 }
 

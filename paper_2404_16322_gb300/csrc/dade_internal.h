@@ -154,6 +154,7 @@ struct dade_index {
     std::vector<int64_t> tile_base;    // nlist + 1: first tile of each bucket
     dade::DevBuf tile_base_dev;
     dade::DevBuf tcslab_dev;
+    dade::DevBuf cent_tc_dev;  // centroid TF32 parts in canonical chunks (probe step; Dpad <= 128)
     // OPQ-L: product quantisation of the stored rotated vectors
     int32_t pq_m = 0, pq_ds = 0;
     std::vector<int32_t> pq_perm;      // D: rotated dims of subspace j at [j*ds, (j+1)*ds)
@@ -205,6 +206,12 @@ cudaError_t launch_tc_l2(const float* A, int64_t lda, const float* an, const flo
                          int32_t* status, cudaStream_t st);
 cudaError_t launch_row_norms(const float* X, int64_t ld, int64_t M, int n, float* out, cudaStream_t st);
 // Per row b: the nprobe[b] smallest of scores[b, 0:n] ordered by (score, column).
+// The centroid distances of the probe step on the tensor cores (pre-split
+// operands, the query tile resident, pipelined): available for Dpad <= 128.
+bool centroid_tc_supported(int Dpad);
+cudaError_t launch_split_tc(const float* X, int64_t ld, int64_t nrows, int Dpad, float* out, cudaStream_t st);
+cudaError_t launch_centroid_dist_tc(const float* qtc, const float* ctc, const float* qn, const float* cn, int64_t B,
+                                    int nlist, int Dpad, float* scores, int32_t* status, cudaStream_t st);
 cudaError_t launch_select_probes(const float* scores, int64_t B, int n, const int32_t* nprobe,
                                  int P, int32_t* probes, int32_t* status, cudaStream_t st);
 

@@ -46,6 +46,8 @@ struct Plan {
     float* pq_lut = nullptr;   // B x m x 256 (OPQ-L)
     float* scores = nullptr;
     float* qnorm = nullptr;
+    bool cent_tc = false;        // centroid distances by the pipelined kernel on pre-split operands
+    float* qtc = nullptr;        // query TF32 parts in canonical chunks
     char* zero_begin = nullptr;
     size_t zero_bytes = 0;
     int32_t* status_internal = nullptr;
@@ -162,6 +164,8 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     v.qpad = c.take<float>((size_t)B * idx->Dpad);
     pl->scores = o.probe_in_dev ? nullptr : c.take<float>((size_t)B * nl);
     pl->qnorm = o.probe_in_dev ? nullptr : c.take<float>((size_t)B);
+    pl->cent_tc = !o.probe_in_dev && idx->cent_tc_dev.p && centroid_tc_supported(idx->Dpad);
+    if (pl->cent_tc) pl->qtc = c.take<float>((size_t)ceil_div(B, 128) * (idx->Dpad / 8) * 2 * 1024);
     v.probes = c.take<int32_t>((size_t)B * P);
     v.off_wl = c.take<int32_t>((size_t)nw * nl + 1);
     v.items = c.take<int32_t>((size_t)B * P);
@@ -350,9 +354,16 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
                                       sizeof(int32_t) * B * v.P, cudaMemcpyDeviceToDevice, st));
     } else {
         DADE_CUDA_TRY(launch_row_norms(v.qrot, idx->Dpad, B, idx->Dpad, pl.qnorm, st));
-        DADE_CUDA_TRY(launch_tc_l2(v.qrot, idx->Dpad, pl.qnorm, idx->cent_dev.as<float>(), idx->Dpad,
-                                   idx->cnorm_dev.as<float>(), pl.scores, idx->nlist, B, idx->nlist, idx->Dpad,
-                                   v.status, st));
+        if (pl.cent_tc) {
+            DADE_CUDA_TRY(launch_split_tc(v.qrot, idx->Dpad, B, idx->Dpad, pl.qtc, st));
+            DADE_CUDA_TRY(launch_centroid_dist_tc(pl.qtc, idx->cent_tc_dev.as<float>(), pl.qnorm,
+                                                  idx->cnorm_dev.as<float>(), B, idx->nlist, idx->Dpad, pl.scores,
+                                                  v.status, st));
+        } else {
+            DADE_CUDA_TRY(launch_tc_l2(v.qrot, idx->Dpad, pl.qnorm, idx->cent_dev.as<float>(), idx->Dpad,
+                                       idx->cnorm_dev.as<float>(), pl.scores, idx->nlist, B, idx->nlist, idx->Dpad,
+                                       v.status, st));
+        }
         DADE_CUDA_TRY(launch_select_probes(pl.scores, B, idx->nlist, nprobe_dev, v.P,
                                            const_cast<int32_t*>(v.probes), v.status, st));
     }

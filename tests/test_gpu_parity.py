@@ -420,3 +420,49 @@ def test_queries_per_unit_changes_nothing(G, tiny_pre, kernel, qpu):
     assert a["status"] == 0 and b["status"] == 0
     for k in ("ids", "dists", "stats"):
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("B", [5, 300, 3000])
+def test_probe_lists_at_several_batch_sizes(G, B):
+    """The probe step (pipelined tensor-core centroid distances on pre-split
+    operands, then the top-nprobe selection) on 400 buckets (three full
+    128-centroid tiles and a ragged one) for 5 / 300 / 3,000 queries (a
+    partial query tile): each list is the nprobe nearest by FP64 distance,
+    sorted, up to centroids within 1e-5 of the boundary; per-query nprobe
+    honoured, -1 beyond it and for inactive slots."""
+    import synth as S
+    X, Q, T, cfg = S.workload("sift1m", N=60_000, n_queries=B)
+    mean, R, _ = G.dade_train_rotation(X, sample_n=20_000, seed=1)
+    idx = G.ivf_build(X, mean, R, 400, kmeans_iters=3, seed=1)
+    try:
+        G.dade_set_correction(idx, 16, np.ones(7, np.float32), np.full(7, -np.inf, np.float32))
+        rng = np.random.default_rng(B)
+        npb = rng.integers(1, 65, B).astype(np.int32)
+        K = np.full(B, 10, np.int32)
+        if B > 5:
+            K[::11] = 0
+            npb[::11] = 0  # inactive slots
+        out = H.gpu_search(G, idx, Q, K, npb, 16, max_nprobe=64, want=("probes", "qrot"))
+        assert out["status"] == 0
+        C = G.dade_index_centroids(idx).astype(np.float64)
+        qr = out["qrot"].astype(np.float64)
+        d = (qr * qr).sum(1)[:, None] + (C * C).sum(1)[None, :] - 2.0 * qr @ C.T
+        same = 0
+        for b in range(B):
+            n = int(npb[b])
+            f = out["probes"][b]
+            assert np.all(f[n:] == -1)
+            if n == 0:
+                continue
+            assert len(set(f[:n].tolist())) == n and np.all(f[:n] >= 0)
+            assert np.all(np.diff(d[b, f[:n]]) >= -1e-5 * d[b, f[:n]].max())  # sorted by distance
+            ref = np.lexsort((np.arange(len(C)), d[b]))[:n]
+            if np.array_equal(f[:n], ref):
+                same += 1
+                continue
+            kth = d[b, ref[-1]]
+            for l in set(f[:n].tolist()) ^ set(ref.tolist()):
+                assert abs(d[b, l] - kth) <= 1e-5 * kth
+        assert same >= 0.95 * int((npb > 0).sum())
+    finally:
+        idx.close()
