@@ -211,9 +211,14 @@ cudaError_t launch_row_norms(const float* X, int64_t ld, int64_t M, int n, float
 bool centroid_tc_supported(int Dpad);
 cudaError_t launch_split_tc(const float* X, int64_t ld, int64_t nrows, int Dpad, float* out, cudaStream_t st);
 cudaError_t launch_centroid_dist_tc(const float* qtc, const float* ctc, const float* qn, const float* cn, int64_t B,
-                                    int nlist, int Dpad, float* scores, int32_t* status, cudaStream_t st);
+                                    int nlist, int Dpad, float* scores, float* tmin, int32_t* status,
+                                    cudaStream_t st);
+// tmin (optional): per query and 128-centroid tile the tile's 4 smallest
+// distances (from launch_centroid_dist_tc); with it, nprobe <= 128 and at most
+// 32 tiles, the selection takes one pass over each score row.
 cudaError_t launch_select_probes(const float* scores, int64_t B, int n, const int32_t* nprobe,
-                                 int P, int32_t* probes, int32_t* status, cudaStream_t st);
+                                 int P, int32_t* probes, int32_t* status, cudaStream_t st,
+                                 const float* tmin = nullptr);
 
 struct LayoutArgs {
     const float* xrot;       // N x Dpad rotated FP32 rows

@@ -22,7 +22,8 @@
 //    the loop: a 64-bit division per chunk cost more than the chunk's MMAs);
 //  - warps 0-3: the epilogue.  Thread t of warp w reads accumulator lane
 //    (query) 32 w + t (tcgen05.ld), forms its distances and stores them as
-//    float4 runs of its query's row; then the warp releases the accumulator
+//    float4 runs of its query's row, and the tile's 4 smallest of them (for
+//    the selection's threshold); then the warp releases the accumulator
 //    ("acc empty"), so the producer's next tile overlaps the stores.
 // Every wait is bounded (about 2 s, then DADE_ETIMEOUT, and the CTA's loops
 // stop; the MMAs issued are drained before the tensor memory is freed).
@@ -47,6 +48,7 @@ struct DistArgs {
     int64_t B;
     int nlist, nchunks, nqtile, nctile;
     float* scores;         // B x nlist
+    float* tmin;           // B x nctile x 4: each tile's 4 smallest distances per query (or null)
     int32_t* status;
 };
 
@@ -208,6 +210,20 @@ __global__ void __launch_bounds__(kPThreads, 1) centroid_dist_kernel(DistArgs a)
             tc_fence_after();
             __syncwarp();
             float* row = a.scores + q * (int64_t)a.nlist;
+            // the tile's 4 smallest distances of this query, ascending
+            float r0 = INFINITY, r1 = INFINITY, r2 = INFINITY, r3 = INFINITY;
+            auto keep4 = [&](float x) {
+                float t = fminf(r0, x);
+                x = fmaxf(r0, x);
+                r0 = t;
+                t = fminf(r1, x);
+                x = fmaxf(r1, x);
+                r1 = t;
+                t = fminf(r2, x);
+                x = fmaxf(r2, x);
+                r2 = t;
+                r3 = fminf(r3, x);
+            };
 #pragma unroll 1
             for (int j0 = 0; j0 < 128; j0 += 32) {
                 uint32_t v[32];
@@ -225,13 +241,23 @@ __global__ void __launch_bounds__(kPThreads, 1) centroid_dist_kernel(DistArgs a)
                         o.z = fmaxf(0.f, qnq + cv.z - 2.f * __uint_as_float(v[j + 2]));
                         o.w = fmaxf(0.f, qnq + cv.w - 2.f * __uint_as_float(v[j + 3]));
                         *reinterpret_cast<float4*>(row + cb + j) = o;
+                        keep4(o.x);
+                        keep4(o.y);
+                        keep4(o.z);
+                        keep4(o.w);
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (cb + j < a.nlist) row[cb + j] = fmaxf(0.f, qnq + cnw[j0 + j] - 2.f * __uint_as_float(v[j]));
+                        if (cb + j < a.nlist) {
+                            const float o = fmaxf(0.f, qnq + cnw[j0 + j] - 2.f * __uint_as_float(v[j]));
+                            row[cb + j] = o;
+                            keep4(o);
+                        }
                 }
             }
+            if (a.tmin && q < a.B)
+                *reinterpret_cast<float4*>(a.tmin + (q * a.nctile + ct) * 4) = make_float4(r0, r1, r2, r3);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[ab]);
@@ -282,7 +308,8 @@ cudaError_t launch_split_tc(const float* X, int64_t ld, int64_t nrows, int Dpad,
 }
 
 cudaError_t launch_centroid_dist_tc(const float* qtc, const float* ctc, const float* qn, const float* cn, int64_t B,
-                                    int nlist, int Dpad, float* scores, int32_t* status, cudaStream_t st) {
+                                    int nlist, int Dpad, float* scores, float* tmin, int32_t* status,
+                                    cudaStream_t st) {
     if (B == 0 || nlist == 0) return cudaSuccess;
     static int sms = 0;
     if (sms == 0) {
@@ -305,6 +332,7 @@ cudaError_t launch_centroid_dist_tc(const float* qtc, const float* ctc, const fl
     a.nqtile = (int)ceil_div(B, 128);
     a.nctile = (int)ceil_div(nlist, 128);
     a.scores = scores;
+    a.tmin = tmin;
     a.status = status;
     const int64_t tiles = (int64_t)a.nqtile * a.nctile;
     const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms);

@@ -117,24 +117,11 @@ __global__ void __launch_bounds__(kSelWarps * 32) select_kernel(const float* __r
 // with a bitonic network over shuffles and merged with the sorted best.
 constexpr int kSelBins = 512;
 
-__global__ void __launch_bounds__(kSelWarps * 32) select128_kernel(const float* __restrict__ scores, int64_t B, int n,
-                                                                  const int32_t* __restrict__ nprobe, int P,
-                                                                  int32_t* __restrict__ probes,
-                                                                  int32_t* __restrict__ status) {
-    __shared__ int s_h[kSelWarps][kSelBins];
-    __shared__ float s_d[kSelWarps][128];
-    __shared__ long long s_i[kSelWarps][128];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t b = (int64_t)blockIdx.x * kSelWarps + warp;
-    if (b >= B) return;
-    const float* row = scores + b * (int64_t)n;
-    int32_t* out = probes + b * (int64_t)P;
-    const int np = nprobe[b];
-    if (np < 1 || np > P || np > n) {
-        if (lane == 0 && status && np != 0) atomicCAS(status, 0, (int)DADE_EINVAL);
-        for (int r = lane; r < P; r += 32) out[r] = -1;
-        return;
-    }
+// One row (a warp): the np smallest of row[0, n) by (score, column) into
+// out[0, np), -1 up to P.  h: kSelBins ints, sd / si: 128 entries, all of
+// this warp.
+__device__ void select128_row(const float* __restrict__ row, int n, int np, int P, int32_t* __restrict__ out,
+                              int* h, float* sd, long long* si, int lane) {
     float mn = INFINITY, mx = -INFINITY;
     for (int i = lane; i < n; i += 32) {
         const float d = row[i];
@@ -149,7 +136,7 @@ __global__ void __launch_bounds__(kSelWarps * 32) select128_kernel(const float* 
     int kbin = kSelBins;  // no bin filter (all scores equal, or not finite)
     if (mx > mn && isfinite(mx) && isfinite(mn)) {
         scale = (float)kSelBins / (mx - mn);
-        int* h = s_h[warp];
+        
         for (int u = lane; u < kSelBins; u += 32) h[u] = 0;
         __syncwarp();
         for (int i = lane; i < n; i += 32) atomicAdd(&h[min(kSelBins - 1, (int)((row[i] - mn) * scale))], 1);
@@ -207,8 +194,8 @@ __global__ void __launch_bounds__(kSelWarps * 32) select128_kernel(const float* 
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             const int pos = m + __popc(bal & ((1u << lane) - 1u));
             if (keep && pos < 128) {
-                s_d[warp][pos] = x.d;
-                s_i[warp][pos] = x.id;
+                sd[pos] = x.d;
+                si[pos] = x.id;
             }
             const int got = __popc(bal);
             if (m + got > 128) {
@@ -233,8 +220,8 @@ __global__ void __launch_bounds__(kSelWarps * 32) select128_kernel(const float* 
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = r * 32 + lane;
-            c[r].d = e < m ? s_d[warp][e] : INFINITY;
-            c[r].id = e < m ? s_i[warp][e] : LLONG_MAX;
+            c[r].d = e < m ? sd[e] : INFINITY;
+            c[r].id = e < m ? si[e] : LLONG_MAX;
         }
         __syncwarp();
         bitonic_sort128(c, lane);
@@ -254,12 +241,137 @@ __global__ void __launch_bounds__(kSelWarps * 32) select128_kernel(const float* 
     }
 }
 
+__global__ void __launch_bounds__(kSelWarps * 32) select128_kernel(const float* __restrict__ scores, int64_t B, int n,
+                                                                  const int32_t* __restrict__ nprobe, int P,
+                                                                  int32_t* __restrict__ probes,
+                                                                  int32_t* __restrict__ status) {
+    __shared__ int s_h[kSelWarps][kSelBins];
+    __shared__ float s_d[kSelWarps][128];
+    __shared__ long long s_i[kSelWarps][128];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * kSelWarps + warp;
+    if (b >= B) return;
+    int32_t* out = probes + b * (int64_t)P;
+    const int np = nprobe[b];
+    if (np < 1 || np > P || np > n) {
+        if (lane == 0 && status && np != 0) atomicCAS(status, 0, (int)DADE_EINVAL);
+        for (int r = lane; r < P; r += 32) out[r] = -1;
+        return;
+    }
+    select128_row(scores + b * (int64_t)n, n, np, P, out, s_h[warp], s_d[warp], s_i[warp], lane);
+}
+
+// nprobe <= 128 with per-tile minima from the centroid-distance kernel:
+// tmin holds, per query and 128-centroid tile, the tile's 4 smallest
+// distances (the same FP32 values as the score row).  Their np-th smallest,
+// theta, is at least the row's np-th smallest (a subset's np-th smallest
+// cannot be smaller), so the np smallest of the row are among the scores
+// <= theta: one pass gathers those (with their columns), one bitonic sort
+// orders them by (score, column).  When more than 128 scores are <= theta
+// (ties) the row goes through select128_row instead.
+__global__ void __launch_bounds__(kSelWarps * 32) select_thr_kernel(const float* __restrict__ scores,
+                                                                   const float* __restrict__ tmin, int nct, int64_t B,
+                                                                   int n, const int32_t* __restrict__ nprobe, int P,
+                                                                   int32_t* __restrict__ probes,
+                                                                   int32_t* __restrict__ status) {
+    __shared__ int s_h[kSelWarps][kSelBins];
+    __shared__ float s_d[kSelWarps][128];
+    __shared__ long long s_i[kSelWarps][128];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * kSelWarps + warp;
+    if (b >= B) return;
+    const float* row = scores + b * (int64_t)n;
+    int32_t* out = probes + b * (int64_t)P;
+    const int np = nprobe[b];
+    if (np < 1 || np > P || np > n) {
+        if (lane == 0 && status && np != 0) atomicCAS(status, 0, (int)DADE_EINVAL);
+        for (int r = lane; r < P; r += 32) out[r] = -1;
+        return;
+    }
+    // theta: the np-th smallest of the tiles' 4 smallest (4 * nct <= 128 values)
+    const float* tm = tmin + b * (int64_t)nct * 4;
+    Ent v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = r * 32 + lane;
+        v[r].d = e < 4 * nct ? tm[e] : INFINITY;
+        v[r].id = 0;
+    }
+    bitonic_sort128(v, lane);
+    const float theta = entry_at(v, np - 1).d;
+    bool fallback = !(theta < INFINITY);
+    // the scores <= theta, with their columns, in column order
+    int m = 0;
+    if (!fallback) {
+        const bool vec = (n & 3) == 0;
+        for (int base = 0; base < n && !fallback; base += 128) {
+            float x[4];
+            const int c0 = base + lane * 4;
+            if (vec && c0 + 3 < n) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(row + c0));
+                x[0] = f.x; x[1] = f.y; x[2] = f.z; x[3] = f.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) x[j] = c0 + j < n ? row[c0 + j] : INFINITY;
+            }
+            int c = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c += (c0 + j < n && x[j] <= theta) ? 1 : 0;
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            if (m + tot > 128) {
+                fallback = true;
+                break;
+            }
+            int pos = m + incl - c;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (c0 + j < n && x[j] <= theta) {
+                    s_d[warp][pos] = x[j];
+                    s_i[warp][pos] = c0 + j;
+                    ++pos;
+                }
+            }
+            m += tot;
+        }
+    }
+    __syncwarp();
+    if (fallback) {
+        select128_row(row, n, np, P, out, s_h[warp], s_d[warp], s_i[warp], lane);
+        return;
+    }
+    Ent a[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = r * 32 + lane;
+        a[r].d = e < m ? s_d[warp][e] : INFINITY;
+        a[r].id = e < m ? s_i[warp][e] : LLONG_MAX;
+    }
+    bitonic_sort128(a, lane);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = r * 32 + lane;
+        if (e < P) out[e] = e < np ? (int32_t)a[r].id : -1;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_select_probes(const float* scores, int64_t B, int n, const int32_t* nprobe,
-                                 int P, int32_t* probes, int32_t* status, cudaStream_t st) {
+                                 int P, int32_t* probes, int32_t* status, cudaStream_t st, const float* tmin) {
     if (B <= 0) return cudaSuccess;
     if (P > PMAX || P < 1) return cudaErrorInvalidValue;
+    const int nct = (n + 127) / 128;
+    if (tmin && P <= 128 && 4 * nct <= 128 && P <= 4 * nct) {
+        select_thr_kernel<<<(unsigned)ceil_div(B, kSelWarps), kSelWarps * 32, 0, st>>>(scores, tmin, nct, B, n, nprobe,
+                                                                                      P, probes, status);
+        return cudaGetLastError();
+    }
     if (P <= 128) {
         select128_kernel<<<(unsigned)ceil_div(B, kSelWarps), kSelWarps * 32, 0, st>>>(scores, B, n, nprobe, P, probes,
                                                                                      status);

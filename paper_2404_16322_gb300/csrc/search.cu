@@ -48,6 +48,7 @@ struct Plan {
     float* qnorm = nullptr;
     bool cent_tc = false;        // centroid distances by the pipelined kernel on pre-split operands
     float* qtc = nullptr;        // query TF32 parts in canonical chunks
+    float* tmin = nullptr;       // B x ceil(nlist / 128) x 4: each centroid tile's 4 smallest distances
     char* zero_begin = nullptr;
     size_t zero_bytes = 0;
     int32_t* status_internal = nullptr;
@@ -165,7 +166,10 @@ size_t carve(const dade_index* idx, int64_t B, int32_t delta_d, const dade_searc
     pl->scores = o.probe_in_dev ? nullptr : c.take<float>((size_t)B * nl);
     pl->qnorm = o.probe_in_dev ? nullptr : c.take<float>((size_t)B);
     pl->cent_tc = !o.probe_in_dev && idx->cent_tc_dev.p && centroid_tc_supported(idx->Dpad);
-    if (pl->cent_tc) pl->qtc = c.take<float>((size_t)ceil_div(B, 128) * (idx->Dpad / 8) * 2 * 1024);
+    if (pl->cent_tc) {
+        pl->qtc = c.take<float>((size_t)ceil_div(B, 128) * (idx->Dpad / 8) * 2 * 1024);
+        pl->tmin = c.take<float>((size_t)B * ceil_div(nl, 128) * 4);
+    }
     v.probes = c.take<int32_t>((size_t)B * P);
     v.off_wl = c.take<int32_t>((size_t)nw * nl + 1);
     v.items = c.take<int32_t>((size_t)B * P);
@@ -358,14 +362,14 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
             DADE_CUDA_TRY(launch_split_tc(v.qrot, idx->Dpad, B, idx->Dpad, pl.qtc, st));
             DADE_CUDA_TRY(launch_centroid_dist_tc(pl.qtc, idx->cent_tc_dev.as<float>(), pl.qnorm,
                                                   idx->cnorm_dev.as<float>(), B, idx->nlist, idx->Dpad, pl.scores,
-                                                  v.status, st));
+                                                  pl.tmin, v.status, st));
         } else {
             DADE_CUDA_TRY(launch_tc_l2(v.qrot, idx->Dpad, pl.qnorm, idx->cent_dev.as<float>(), idx->Dpad,
                                        idx->cnorm_dev.as<float>(), pl.scores, idx->nlist, B, idx->nlist, idx->Dpad,
                                        v.status, st));
         }
         DADE_CUDA_TRY(launch_select_probes(pl.scores, B, idx->nlist, nprobe_dev, v.P,
-                                           const_cast<int32_t*>(v.probes), v.status, st));
+                                           const_cast<int32_t*>(v.probes), v.status, st, pl.tmin));
     }
     if (o.probe_out_dev)
         DADE_CUDA_TRY(cudaMemcpyAsync(o.probe_out_dev, v.probes, sizeof(int32_t) * B * v.P,

@@ -422,18 +422,21 @@ def test_queries_per_unit_changes_nothing(G, tiny_pre, kernel, qpu):
         assert np.array_equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("B", [5, 300, 3000])
-def test_probe_lists_at_several_batch_sizes(G, B):
+@pytest.mark.parametrize("nlist,B", [(400, 5), (400, 300), (400, 3000), (2000, 300), (2000, 3000)])
+def test_probe_lists_at_several_batch_sizes(G, nlist, B):
     """The probe step (pipelined tensor-core centroid distances on pre-split
     operands, then the top-nprobe selection) on 400 buckets (three full
-    128-centroid tiles and a ragged one) for 5 / 300 / 3,000 queries (a
-    partial query tile): each list is the nprobe nearest by FP64 distance,
-    sorted, up to centroids within 1e-5 of the boundary; per-query nprobe
-    honoured, -1 beyond it and for inactive slots."""
+    128-centroid tiles and a ragged one: the histogram selection) and 2,000
+    buckets (16 tiles: the one-pass selection under the threshold from the
+    tiles' 4 smallest, with the histogram path for rows where more than 128
+    scores fall below it) for 5 / 300 / 3,000 queries (a partial query
+    tile): each list is the nprobe nearest by FP64 distance, sorted, up to
+    centroids within 1e-5 of the boundary; per-query nprobe honoured, -1
+    beyond it and for inactive slots."""
     import synth as S
     X, Q, T, cfg = S.workload("sift1m", N=60_000, n_queries=B)
     mean, R, _ = G.dade_train_rotation(X, sample_n=20_000, seed=1)
-    idx = G.ivf_build(X, mean, R, 400, kmeans_iters=3, seed=1)
+    idx = G.ivf_build(X, mean, R, nlist, kmeans_iters=3, seed=1)
     try:
         G.dade_set_correction(idx, 16, np.ones(7, np.float32), np.full(7, -np.inf, np.float32))
         rng = np.random.default_rng(B)
