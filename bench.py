@@ -326,6 +326,7 @@ def reference_arm(args):
 UNEVEN_METRIC = ("QPS of 20,000 uneven requests in one call (estimate-and-prune IVF search, vMF-like 10M x 96, "
                  "nlist 4096, K in [1,100], nprobe in [8,256])")
 UNEVEN_SCHEDULES = ((8, 30), (4, 30), (16, 30), (8, 2))
+UNEVEN_BUDGETS = (0, 32 << 30)  # candidate-buffer bound: the library default (8 GiB), 32 GiB
 
 
 def uneven_requests(args, G, torch, world, rank, local):
@@ -357,14 +358,16 @@ def uneven_requests(args, G, torch, world, rank, local):
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stats = torch.zeros((B, 4), dtype=torch.int64, device=dev)
     ws = torch.empty(max(G.dade_search_workspace_size(idx, B, dd, maxK, maxP, mode=m, first_wave=fw,
-                                                      wave_growth_log2=g)
-                         for m in ("prune", "full") for fw, g in UNEVEN_SCHEDULES + ((1, 1),)),
+                                                      wave_growth_log2=g, candidate_budget_bytes=cb)
+                         for m in ("prune", "full") for fw, g in UNEVEN_SCHEDULES + ((1, 1),)
+                         for cb in UNEVEN_BUDGETS),
                      dtype=torch.uint8, device=dev)
+    budget = 0
 
     def search(mode, fw, g, with_stats=False):
         G.dade_search(idx, q, k, npb, dd if mode == "prune" else 0, ids, dists, max_K=maxK, max_nprobe=maxP,
                       mode=mode, first_wave=fw, wave_growth_log2=g, status=status, workspace=ws,
-                      stats=stats if with_stats else None)
+                      stats=stats if with_stats else None, candidate_budget_bytes=budget)
 
     def timed(mode, fw, g, steps, warmup):
         search(mode, fw, g)  # outside the capture: kernel attributes, module loads
@@ -396,11 +399,13 @@ def uneven_requests(args, G, torch, world, rank, local):
         return r10, r1
 
     tried = []
-    for fw, g in UNEVEN_SCHEDULES:
-        per = timed("prune", fw, g, 5, 2)
-        tried.append(dict(first_wave=fw, growth=g, ms=float(np.median(per))))
+    for cb in UNEVEN_BUDGETS:
+        budget = cb
+        for fw, g in UNEVEN_SCHEDULES:
+            per = timed("prune", fw, g, 5, 2)
+            tried.append(dict(first_wave=fw, growth=g, candidate_budget_bytes=cb, ms=float(np.median(per))))
     best = min(tried, key=lambda t: t["ms"])
-    fw, g = best["first_wave"], best["growth"]
+    fw, g, budget = best["first_wave"], best["growth"], best["candidate_budget_bytes"]
     setup_s = time.perf_counter() - t_setup
 
     sampler = ClockSampler(local)
@@ -489,6 +494,7 @@ def uneven_requests(args, G, torch, world, rank, local):
         "config": {"workload": f"vmf10m-shaped: N={len(X)}, D=96, L2-normalised vMF mixture of 2048 components; "
                                f"B={B} requests, K~U[1,100], nprobe~U[8,256]; nlist={nlist}",
                    "delta_d": dd, "first_wave": fw, "wave_growth_log2": g, "slabs": slabs,
+                   "candidate_budget_bytes": budget,
                    "recall@10(K>=10)": r10, "recall@1": r1, "graph": True, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (index {G.dade_index_info_get(idx)['device_bytes'] / 1e9:.1f} GB "
                          "> 129 MB L2)",
@@ -506,7 +512,7 @@ def uneven_requests(args, G, torch, world, rank, local):
                 "d2h_bytes_per_step": int(B * maxK * 12)},
         "gpu_launches": args.steps * G.dade_search_kernel_count(
             idx, q, k, npb, dd, ids, dists, max_K=maxK, max_nprobe=maxP, workspace=ws, status=status,
-            first_wave=fw, wave_growth_log2=g),
+            first_wave=fw, wave_growth_log2=g, candidate_budget_bytes=budget),
         "clocks": clocks,
         "schedules": tried,
         "setup_s": setup_s,
