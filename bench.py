@@ -271,7 +271,7 @@ def blas_kmeans(Xr, nlist, iters, seed, sample_n):
 
 def reference_arm(args):
     """The oracle as the reference arm: the same SIFT-shaped workload (the
-    1M rows, nlist 4096, nprobe 64, K 100, Delta_d 16, first wave 8 and one
+    1M rows, nlist 4096, nprobe 64, K 100, Delta_d 16, first wave 4 and one
     later wave -- the GPU arm's tuned configuration), an index prepared on
     the host (the oracle's FP64 PCA, buckets by a BLAS k-means, tables by
     the oracle's replay and fit on 300 training queries), then steps of a
@@ -283,7 +283,7 @@ def reference_arm(args):
     from oracle import fit, pca, search
     t0 = time.perf_counter()
     X, Q, T, cfg = synth.workload("sift1m")
-    nlist, K, nprobe, dd, fw, gw = cfg["nlist"], cfg["K"], 64, 16, 8, 30
+    nlist, K, nprobe, dd, fw, gw = cfg["nlist"], cfg["K"], 64, 16, 4, 30
     rng = np.random.default_rng(1)
     mu, R, _ = pca.train_rotation(X[np.sort(rng.choice(len(X), 200_000, replace=False))])
     Xr = pca.rotate(X, mu, R)
