@@ -469,3 +469,39 @@ def test_probe_lists_at_several_batch_sizes(G, nlist, B):
         assert same >= 0.95 * int((npb > 0).sum())
     finally:
         idx.close()
+
+
+def test_probe_selection_with_massive_ties(G):
+    """Twelve distinct centroids, each repeated about 170 times over 2,048
+    buckets (every 128-centroid tile holds ~10 copies of each): a query's
+    scores tie in blocks of ~170, more than the one-pass selection holds, so
+    every row takes the histogram path.  The lists must be the nprobe
+    smallest by (distance, list id): the lowest ids among the nearest
+    centroid's copies."""
+    X, Q, T, cfg = synth.workload("tiny", n_queries=64)
+    mean, R, _ = G.dade_train_rotation(X)
+    Xr = (X.astype(np.float64) - mean) @ R.T
+    rng = np.random.default_rng(12)
+    C12 = Xr[rng.choice(len(X), 12, replace=False)].astype(np.float32)
+    nlist = 2048
+    C = C12[np.arange(nlist) % 12]
+    near = np.argmin(((Xr[:, None, :] - C12[None, :, :].astype(np.float64)) ** 2).sum(-1), axis=1)
+    copies = (nlist - 1 - near) // 12 + 1  # copies of centroid j: ids j, j + 12, ...
+    assign = (near + 12 * (np.arange(len(X)) % copies)).astype(np.int32)
+    idx = G.ivf_build(X, mean, R, nlist, centroids=C, assign=assign)
+    try:
+        G.dade_set_correction(idx, 16, np.ones(7, np.float32), np.full(7, -np.inf, np.float32))
+        P = 64
+        npb = np.random.default_rng(3).integers(1, P + 1, len(Q)).astype(np.int32)
+        out = H.gpu_search(G, idx, Q, 10, npb, 16, max_nprobe=P, want=("probes", "qrot"))
+        assert out["status"] == 0
+        Cd = G.dade_index_centroids(idx).astype(np.float64)
+        qr = out["qrot"].astype(np.float64)
+        d = (qr * qr).sum(1)[:, None] + (Cd * Cd).sum(1)[None, :] - 2.0 * qr @ Cd.T
+        for b in range(len(Q)):
+            n = int(npb[b])
+            ref = np.lexsort((np.arange(nlist), d[b]))[:n]
+            assert np.array_equal(out["probes"][b, :n], ref), b
+            assert np.all(out["probes"][b, n:] == -1)
+    finally:
+        idx.close()
