@@ -261,50 +261,6 @@ __global__ void __launch_bounds__(kSelWarps * 32) select128_kernel(const float* 
     select128_row(scores + b * (int64_t)n, n, np, P, out, s_h[warp], s_d[warp], s_i[warp], lane);
 }
 
-// (score, column) pairs, 128 per warp (slot r of lane l = entry 32 r + l),
-// sorted by a bitonic network: the same network as bitonic_sort128 with a
-// 32-bit payload (two shuffles per exchange instead of three).
-struct KV {
-    float d;
-    int c;
-};
-__device__ __forceinline__ bool kv_less(const KV& a, const KV& b) { return a.d < b.d || (a.d == b.d && a.c < b.c); }
-
-__device__ __forceinline__ void kv_sort128(KV (&v)[4], int lane) {
-#pragma unroll
-    for (int k = 2; k <= 128; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int js = j >> 5;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int p = r ^ js;
-                    if (p > r) {
-                        const bool asc = ((r * 32 + lane) & k) == 0;
-                        if (asc ? kv_less(v[p], v[r]) : kv_less(v[r], v[p])) {
-                            const KV t = v[r];
-                            v[r] = v[p];
-                            v[p] = t;
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    KV o;
-                    o.d = __shfl_xor_sync(0xffffffffu, v[r].d, j);
-                    o.c = __shfl_xor_sync(0xffffffffu, v[r].c, j);
-                    const bool asc = ((r * 32 + lane) & k) == 0;
-                    const bool take_min = ((lane & j) == 0) == asc;
-                    const bool o_less = kv_less(o, v[r]);
-                    if (take_min ? o_less : !o_less && (o.d != v[r].d || o.c != v[r].c)) v[r] = o;
-                }
-            }
-        }
-    }
-}
-
 // nprobe <= 128 with per-tile minima from the centroid-distance kernel:
 // tmin holds, per query and 128-centroid tile, the tile's 4 smallest
 // distances (the same FP32 values as the score row).  Their np-th smallest,
