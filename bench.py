@@ -326,7 +326,7 @@ def reference_arm(args):
 UNEVEN_METRIC = ("QPS of 20,000 uneven requests in one call (estimate-and-prune IVF search, vMF-like 10M x 96, "
                  "nlist 4096, K in [1,100], nprobe in [8,256])")
 UNEVEN_SCHEDULES = ((8, 30), (4, 30), (16, 30), (8, 2))
-UNEVEN_BUDGETS = (0, 32 << 30)  # candidate-buffer bound: the library default (8 GiB), 32 GiB
+UNEVEN_BUDGETS = (0, 32 << 30, 96 << 30)  # candidate-buffer bound: the library default (8 GiB), 32, 96 GiB
 
 
 def uneven_requests(args, G, torch, world, rank, local):
