@@ -234,13 +234,38 @@ def oracle_on_library_index(G, idx, X, Q, mean, R, slabs, nprobe, delta_d, K, n_
     m1, beta = G.dade_get_correction(idx, delta_d)
     q = Q[:n_queries]
     threads, times = time_oracle(oidx, m1, beta, nprobe, delta_d, K, [q], first_wave, growth, final_test)
+    # one thread, on a tenth of the sample
+    q1 = q[:max(1, len(q) // 10)]
+    search.set_threads(1)
+    t0 = time.perf_counter()
+    pr = oidx.probe(oidx.rotate_queries(q1), nprobe)
+    search.search(oidx, q1, pr, nprobe, K, delta_d, np.asarray(m1, np.float64), np.asarray(beta, np.float64),
+                  first_wave=first_wave, growth=max(1, growth),
+                  final_rel=search.FINAL_REL if final_test else np.inf)
+    one_thread = len(q1) / (time.perf_counter() - t0)
+    search.set_threads(threads)
     del oidx
     sample = (f"oracle FP64 C loop on the first {len(q)} of the {len(Q)} queries against the same "
               f"{len(X)}-vector {name}-shaped index as the GPU line (the library's rotation, centroids, "
               f"assignment and fitted tables; {slabs} slabs emulated), nprobe {nprobe}, K {K}, delta_d {delta_d}, "
               f"first wave {first_wave}, growth 2^{max(1, growth)}; probing included")
     return dict(value=len(q) / float(np.median(times)), unit="queries/s", cores=threads, kind="oracle",
-                sample=sample)
+                sample=sample, one_thread_value=one_thread, one_thread_queries=len(q1), cpu_model=cpu_model())
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo or lscpu), for the record."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def blas_kmeans(Xr, nlist, iters, seed, sample_n):
@@ -310,7 +335,7 @@ def reference_arm(args):
               f"{len(X)}-vector sift1m-shaped set (nlist {nlist}; the oracle's PCA, buckets by BLAS k-means on a "
               f"200k sample, tables fitted by the oracle on 300 training queries), nprobe {nprobe}, K {K}, "
               f"delta_d {dd}, first wave {fw}, growth 2^{gw}; probing included")
-    cb = dict(value=value, unit="queries/s", cores=threads, kind="oracle", sample=sample)
+    cb = dict(value=value, unit="queries/s", cores=threads, kind="oracle", sample=sample, cpu_model=cpu_model())
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -481,7 +506,7 @@ def uneven_requests(args, G, torch, world, rank, local):
                        first_wave=fw, growth=g)
         cpu_s = time.perf_counter() - t0
         del oidx
-        cpu = dict(value=nq / cpu_s, unit="queries/s", cores=threads, kind="oracle",
+        cpu = dict(value=nq / cpu_s, unit="queries/s", cores=threads, kind="oracle", cpu_model=cpu_model(),
                    sample=f"oracle FP64 C loop on the first {nq} of the {B} requests (their own K and nprobe) "
                           f"against the same {len(X)}-vector index as the GPU line (the library's rotation, "
                           f"centroids, assignment and fitted table; {slabs} slabs emulated), delta_d {dd}, "
