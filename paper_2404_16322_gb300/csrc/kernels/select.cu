@@ -289,24 +289,26 @@ __global__ void __launch_bounds__(kSelWarps * 32) select_thr_kernel(const float*
         return;
     }
     // theta: the np-th smallest of the tiles' 4 smallest (4 * nct <= 128 values)
+    // (non-negative FP32 distances order as their bit patterns: the
+    // np-th smallest is the largest pattern with fewer than np below it,
+    // found bit by bit from the top)
     const float* tm = tmin + b * (int64_t)nct * 4;
-    KV v[4];
+    uint32_t key[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int e = r * 32 + lane;
-        v[r].d = e < 4 * nct ? tm[e] : INFINITY;
-        v[r].c = e;
+        key[r] = __float_as_uint(e < 4 * nct ? tm[e] : INFINITY);
     }
-    kv_sort128(v, lane);
-    float theta;
-    {
-        const int e = np - 1, r = e >> 5;
-        float x = v[0].d;
-        if (r == 1) x = v[1].d;
-        if (r == 2) x = v[2].d;
-        if (r == 3) x = v[3].d;
-        theta = __shfl_sync(0xffffffffu, x, e & 31);
+    uint32_t prefix = 0u;
+#pragma unroll 1
+    for (int bit = 30; bit >= 0; --bit) {
+        const uint32_t cand = prefix | (1u << bit);
+        int below = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) below += __popc(__ballot_sync(0xffffffffu, key[r] < cand));
+        if (below < np) prefix = cand;
     }
+    const float theta = __uint_as_float(prefix);
     bool fallback = !(theta < INFINITY);
     // the scores <= theta, with their columns, in column order
     int m = 0;
