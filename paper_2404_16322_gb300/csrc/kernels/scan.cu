@@ -369,37 +369,53 @@ __global__ void output_kernel(WaveView wv, int64_t* ids, float* dists, const int
 }
 
 // ------------------------------------------------------------ work units
+// One warp per query (lane = probe rank, 32 at a time): per (pass, bucket)
+// the number of queries probing it, and per (pass, query) the query's
+// candidate count (lanes of the same pass are contiguous: their sizes are
+// summed with one warp reduction and added by the first of them).
 __global__ void count_kernel(IndexView ix, WaveView wv) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (b >= wv.B) return;
-    int np = wv.nprobe[b];
+    const int np = wv.nprobe[b];
     const int K = wv.K[b];
     if (np < 1 || np > wv.P || K < 1 || K > wv.Kmax) {
         // nprobe = 0 or K = 0 marks an inactive query slot (no work, padded
         // output); anything else out of range is an error
-        if (!((np == 0 && K >= 0 && K <= wv.Kmax) || (K == 0 && np >= 0 && np <= wv.P)))
+        if (lane == 0 && !((np == 0 && K >= 0 && K <= wv.Kmax) || (K == 0 && np >= 0 && np <= wv.P)))
             atomicCAS(wv.status, 0, (int)DADE_EINVAL);
         return;
     }
-    for (int r = 0; r < np; ++r) {
-        const int l = wv.probes[b * wv.P + r];
-        if (l < 0 || l >= ix.nlist) {
-            atomicCAS(wv.status, 0, (int)DADE_EINVAL);
-            continue;
+    for (int r0 = 0; r0 < np; r0 += 32) {
+        const int r = r0 + lane;
+        int wr = -1;
+        uint32_t size = 0;
+        if (r < np) {
+            const int l = wv.probes[b * wv.P + r];
+            if (l < 0 || l >= ix.nlist) {
+                atomicCAS(wv.status, 0, (int)DADE_EINVAL);
+            } else {
+                wr = pass_of_rank(wv, r);
+                atomicAdd(&wv.cnt_wl[wr * ix.nlist + l], 1);
+                size = (uint32_t)ix.list_size[l];
+            }
         }
-        const int wr = pass_of_rank(wv, r);
-        atomicAdd(&wv.cnt_wl[wr * ix.nlist + l], 1);
-        wv.cand_off[(int64_t)wr * (wv.B + 1) + b] += ix.list_size[l];
+        const unsigned grp = __match_any_sync(0xffffffffu, wr);
+        const uint32_t tot = __reduce_add_sync(grp, size);
+        if (wr >= 0 && lane == __ffs(grp) - 1) wv.cand_off[(int64_t)wr * (wv.B + 1) + b] += tot;
+        __syncwarp();  // the next 32 ranks may add to the same pass's count from another lane
     }
 }
 
+// One warp per query: each probed (pass, bucket) list gets the query once.
 __global__ void scatter_kernel(IndexView ix, WaveView wv) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (b >= wv.B) return;
-    int np = wv.nprobe[b];
+    const int np = wv.nprobe[b];
     const int K = wv.K[b];
     if (np < 1 || np > wv.P || K < 1 || K > wv.Kmax) return;
-    for (int r = 0; r < np; ++r) {
+    for (int r = lane; r < np; r += 32) {
         const int l = wv.probes[b * wv.P + r];
         if (l < 0 || l >= ix.nlist) continue;
         const int wr = pass_of_rank(wv, r);
@@ -635,8 +651,8 @@ cudaError_t launch_fill(float* p, int64_t n, float v, cudaStream_t st) {
 }
 
 cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStream_t st) {
-    const unsigned gb = (unsigned)ceil_div(wv.B, 128);
-    count_kernel<<<gb, 128, 0, st>>>(ix, wv);
+    const unsigned gb = (unsigned)ceil_div(wv.B * 32, 256);  // a warp per query
+    count_kernel<<<gb, 256, 0, st>>>(ix, wv);
     const int64_t nwl = (int64_t)wv.n_waves * ix.nlist;
     seg_scan_kernel<<<1, 1024, 0, st>>>(LoadI32{wv.cnt_wl}, wv.off_wl, nwl, 0);
     LoadUnits lu{wv.cnt_wl, ix.list_size, ix.nlist, {}};
@@ -644,7 +660,7 @@ cudaError_t launch_build_units(const IndexView& ix, const WaveView& wv, cudaStre
     seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(lu, wv.unit_off, (int64_t)ix.nlist, (int64_t)ix.nlist + 1);
     seg_scan_kernel<<<wv.n_waves, 1024, 0, st>>>(LoadCap{wv.cand_off, wv.B + 1}, wv.cand_off, wv.B,
                                                  wv.B + 1);
-    scatter_kernel<<<gb, 128, 0, st>>>(ix, wv);
+    scatter_kernel<<<gb, 256, 0, st>>>(ix, wv);
     expand_units_kernel<<<(unsigned)ceil_div(nwl, 128), 128, 0, st>>>(ix, wv);
     return cudaGetLastError();
 }
