@@ -291,17 +291,22 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const float* __restrict
     }
 }
 
-// ||row||^2 of the first n columns of each of M rows (FP32, in column order).
+// ||row||^2 of the first n columns of each of M rows (FP32): one warp per
+// row, lane l summing columns l, l + 32, ... in order, then a butterfly sum
+// (a fixed order, so the same row always gets the same bits).
 __global__ void row_norms_kernel(const float* __restrict__ X, int64_t ld, int64_t M, int n,
                                  float* __restrict__ out) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (r >= M) return;
     float s = 0.f;
-    for (int j = 0; j < n; ++j) {
+    for (int j = lane; j < n; j += 32) {
         const float v = X[r * ld + j];
         s = fmaf(v, v, s);
     }
-    out[r] = s;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s;
 }
 
 constexpr int kSmem = 5 * TILE_BYTES + 1024;  // five operand parts + alignment slack
@@ -355,7 +360,7 @@ cudaError_t launch_tc_l2(const float* A, int64_t lda, const float* an, const flo
 
 cudaError_t launch_row_norms(const float* X, int64_t ld, int64_t M, int n, float* out, cudaStream_t st) {
     if (M <= 0) return cudaSuccess;
-    row_norms_kernel<<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(X, ld, M, n, out);
+    row_norms_kernel<<<(unsigned)ceil_div(M * 32, 256), 256, 0, st>>>(X, ld, M, n, out);
     return cudaGetLastError();
 }
 
