@@ -355,13 +355,16 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
     if (lane == 0) wv.tau_run[q] = n_out == K ? kth.d : INFINITY;
 }
 
+// One warp per query: its K results (padding -1 / +inf up to its slots).
 __global__ void output_kernel(WaveView wv, int64_t* ids, float* dists, const int64_t* offsets) {
-    const int64_t q = blockIdx.x;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= wv.B) return;
     const int K = wv.K[q];
     const int64_t off = offsets ? offsets[q] : q * wv.Kmax;
     const int kk = offsets ? (int)(offsets[q + 1] - offsets[q]) : wv.Kmax;
     const int n = (K >= 1 && K <= wv.Kmax) ? wv.top_n[q] : 0;
-    for (int k = threadIdx.x; k < kk; k += blockDim.x) {
+    for (int k = lane; k < kk; k += 32) {
         bool v = k < n && k < K;
         ids[off + k] = v ? wv.top_id[q * wv.Kmax + k] : -1;
         dists[off + k] = v ? wv.top_d[q * wv.Kmax + k] : INFINITY;
@@ -707,7 +710,7 @@ cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStr
 cudaError_t launch_output(const WaveView& wv, int64_t* ids, float* dists, const int64_t* offsets,
                           cudaStream_t st) {
     if (wv.B == 0) return cudaSuccess;
-    output_kernel<<<(unsigned)wv.B, 128, 0, st>>>(wv, ids, dists, offsets);
+    output_kernel<<<(unsigned)ceil_div(wv.B * 32, 256), 256, 0, st>>>(wv, ids, dists, offsets);
     return cudaGetLastError();
 }
 
