@@ -276,48 +276,65 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
         kth.d = INFINITY;
         kth.id = LLONG_MAX;
         if (total >= K) kth = entry_at(a, K - 1);
-        // gather up to 128 candidates that are not above the K-th entry
+        // gather up to 128 candidates that are not above the K-th entry's
+        // distance (four loads in flight; their ids are looked up after)
         int m = 0;
-        for (; i0 < cnt && m < 128; i0 += 32) {
-            const int i = i0 + lane;
-            Ent x;
-            x.d = INFINITY;
-            x.id = LLONG_MAX;
-            bool keep = false;
-            if (i < cnt) {
-                x.d = cd[i];
-                keep = x.d <= kth.d && (kbin == kM128Bins || min(kM128Bins - 1, (int)((x.d - lo) * scale)) <= kbin);
-                if (keep) {
-                    x.id = (long long)ix.ids[cp[i]];
-                    keep = !ent_less(kth, x);
+        while (i0 < cnt && m < 128) {
+            float xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u + lane;
+                xv[u] = i < cnt ? cd[i] : INFINITY;
+            }
+            bool stop = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (stop) break;
+                const int i = i0 + 32 * u + lane;
+                const bool keep = i < cnt && xv[u] <= kth.d &&
+                                  (kbin == kM128Bins || min(kM128Bins - 1, (int)((xv[u] - lo) * scale)) <= kbin);
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                const int pos = m + __popc(bal & lanemask_lt());
+                if (keep && pos < 128) {
+                    s_d[warp][pos] = xv[u];
+                    s_i[warp][pos] = i;  // the candidate's index; its id below
                 }
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            const int pos = m + __popc(bal & lanemask_lt());
-            if (keep && pos < 128) {
-                s_d[warp][pos] = x.d;
-                s_i[warp][pos] = x.id;
-            }
-            const int got = __popc(bal);
-            if (m + got > 128) {
-                // the chunk is full: leave the rest of these 32 for the next round
-                const int take = 128 - m;
-                // rank of the (take+1)-th kept lane: resume there
-                int seen = 0, resume = 32;
-                for (int l2 = 0; l2 < 32; ++l2) {
-                    if ((bal >> l2) & 1u) {
-                        if (seen == take) { resume = l2; break; }
-                        ++seen;
+                const int got = __popc(bal);
+                if (m + got > 128) {
+                    // the chunk is full: resume at the first kept lane not taken
+                    const int take = 128 - m;
+                    int seen = 0, resume = 32;
+                    for (int l2 = 0; l2 < 32; ++l2) {
+                        if ((bal >> l2) & 1u) {
+                            if (seen == take) { resume = l2; break; }
+                            ++seen;
+                        }
                     }
+                    m = 128;
+                    i0 += 32 * u + resume;
+                    stop = true;
+                } else {
+                    m += got;
                 }
-                m = 128;
-                i0 += resume;
-                break;
             }
-            m += got;
+            if (!stop) i0 += 128;
         }
         __syncwarp();
         if (m == 0) break;
+        {  // ids of the gathered candidates, four independent lookups per lane
+            int slot[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int e = r * 32 + lane;
+                slot[r] = e < m ? cp[(int)s_i[warp][e]] : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int e = r * 32 + lane;
+                if (e < m) s_i[warp][e] = (long long)ix.ids[slot[r]];
+            }
+        }
+        __syncwarp();
         Ent b[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -327,15 +344,21 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
         }
         __syncwarp();
         bitonic_sort128(b, lane);
-        // a ascending, b reversed descending: the elementwise minimum is a
-        // bitonic sequence of the 128 smallest of both
+        if (total == 0) {
+            // nothing kept yet: the sorted chunk is the list
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const Ent br = shfl_ent(b[3 - r], 31 - lane);
-            if (ent_less(br, a[r])) a[r] = br;
+            for (int r = 0; r < 4; ++r) a[r] = b[r];
+        } else {
+            // a ascending, b reversed descending: the elementwise minimum is a
+            // bitonic sequence of the 128 smallest of both
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const Ent br = shfl_ent(b[3 - r], 31 - lane);
+                if (ent_less(br, a[r])) a[r] = br;
+            }
+#pragma unroll
+            for (int j = 64; j > 0; j >>= 1) bitonic_level(a, j, lane, [](int) { return true; });
         }
-#pragma unroll
-        for (int j = 64; j > 0; j >>= 1) bitonic_level(a, j, lane, [](int) { return true; });
         total = min(128, total + m);
     }
     const int n_out = min(K, total);
