@@ -1,5 +1,6 @@
 // C ABI glue: status/error plumbing, index lifetime, inspection, correction
 // tables, persistence, and the host-side rotation training.
+#include <climits>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -121,6 +122,15 @@ dade_status build_tc_operands(dade_index* idx) {
                                  idx->list_slot_dev.as<int64_t>(), idx->list_size_dev.as<int32_t>(),
                                  idx->tile_base_dev.as<int64_t>(), nl, idx->Dpad, idx->tc_parts, ntiles,
                                  idx->tcslab_dev.as<float>(), 0));
+    {  // may the merges carry 32-bit ids?
+        std::vector<int64_t> h((size_t)idx->total_slots);
+        if (idx->total_slots > 0)
+            DADE_CUDA_TRY(cudaMemcpy(h.data(), idx->ids_dev.p, sizeof(int64_t) * idx->total_slots,
+                                     cudaMemcpyDeviceToHost));
+        bool fit = true;
+        for (int64_t v : h) fit = fit && (v == -1 || (v >= 0 && v < (int64_t)INT_MAX));
+        idx->ids32 = fit ? 1 : 0;
+    }
     if (centroid_tc_supported(idx->Dpad)) {
         DADE_TRY(idx->cent_tc_dev.alloc(sizeof(float) * 2 * 1024 * (size_t)ceil_div(nl, 128) * (idx->Dpad / 8)));
         DADE_CUDA_TRY(launch_split_tc(idx->cent_dev.as<float>(), idx->Dpad, nl, idx->Dpad,

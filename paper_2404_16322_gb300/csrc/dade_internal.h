@@ -154,6 +154,7 @@ struct dade_index {
     std::vector<int64_t> tile_base;    // nlist + 1: first tile of each bucket
     dade::DevBuf tile_base_dev;
     dade::DevBuf tcslab_dev;
+    int32_t ids32 = 0;         // every slot's id is -1 (padding) or in [0, 2^31 - 1)
     dade::DevBuf cent_tc_dev;  // centroid TF32 parts in canonical chunks (probe step; Dpad <= 128)
     // OPQ-L: product quantisation of the stored rotated vectors
     int32_t pq_m = 0, pq_ds = 0;

@@ -188,6 +188,8 @@ constexpr int kM128Warps = 8;
 
 constexpr int kM128Bins = 512;
 
+// E: Ent (64-bit ids) or Ent32 (every id of the index fits in 31 bits).
+template <class E>
 __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix, WaveView wv, int w) {
     __shared__ float s_d[kM128Warps][128];
     __shared__ long long s_i[kM128Warps][128];
@@ -208,12 +210,12 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
     float* td = wv.top_d + q * wv.Kmax;
     int64_t* ti = wv.top_id + q * wv.Kmax;
     const int cur = wv.top_n[q];
-    Ent a[4];
+    E a[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int e = r * 32 + lane;
         a[r].d = e < cur ? td[e] : INFINITY;
-        a[r].id = e < cur ? (long long)ti[e] : LLONG_MAX;
+        a[r].id = e < cur ? (decltype(a[r].id))ti[e] : ent_pad<E>().id;
     }
     int total = cur;  // entries held (up to 128)
     // Many new candidates: only the K smallest of them can enter.  Their
@@ -272,9 +274,7 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
     int i0 = 0;
     while (i0 < cnt) {
         // the current K-th entry bounds what can still enter
-        Ent kth;
-        kth.d = INFINITY;
-        kth.id = LLONG_MAX;
+        E kth = ent_pad<E>();
         if (total >= K) kth = entry_at(a, K - 1);
         // gather up to 128 candidates that are not above the K-th entry's
         // distance (four loads in flight; their ids are looked up after)
@@ -335,12 +335,12 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
             }
         }
         __syncwarp();
-        Ent b[4];
+        E b[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = r * 32 + lane;
             b[r].d = e < m ? s_d[warp][e] : INFINITY;
-            b[r].id = e < m ? s_i[warp][e] : LLONG_MAX;
+            b[r].id = e < m ? (decltype(b[r].id))s_i[warp][e] : ent_pad<E>().id;
         }
         __syncwarp();
         bitonic_sort128(b, lane);
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
             // bitonic sequence of the 128 smallest of both
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const Ent br = shfl_ent(b[3 - r], 31 - lane);
+                const E br = shfl_ent(b[3 - r], 31 - lane);
                 if (ent_less(br, a[r])) a[r] = br;
             }
 #pragma unroll
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kM128Warps * 32) merge128_kernel(IndexView ix,
         wv.top_n[q] = n_out;
         wv.cand_cnt[q] = 0;
     }
-    const Ent kth = entry_at(a, K - 1);
+    const E kth = entry_at(a, K - 1);
     if (lane == 0) wv.tau_run[q] = n_out == K ? kth.d : INFINITY;
 }
 
@@ -716,7 +716,10 @@ cudaError_t launch_wave_scan(const IndexView& ix, const WaveView& wv, int w, boo
 cudaError_t launch_merge(const IndexView& ix, const WaveView& wv, int w, cudaStream_t st) {
     if (wv.B == 0) return cudaSuccess;
     if (wv.Kmax <= 128) {
-        merge128_kernel<<<(unsigned)ceil_div(wv.B, kM128Warps), kM128Warps * 32, 0, st>>>(ix, wv, w);
+        if (ix.ids32)
+            merge128_kernel<Ent32><<<(unsigned)ceil_div(wv.B, kM128Warps), kM128Warps * 32, 0, st>>>(ix, wv, w);
+        else
+            merge128_kernel<Ent><<<(unsigned)ceil_div(wv.B, kM128Warps), kM128Warps * 32, 0, st>>>(ix, wv, w);
         return cudaGetLastError();
     }
     const int smem = kMergeWarps * (2 * wv.Kmax + kMergeChunk) * (int)(sizeof(float) + sizeof(long long));

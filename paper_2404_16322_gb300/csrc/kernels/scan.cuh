@@ -23,6 +23,7 @@ struct IndexView {
     const int64_t* tile_base;  // nlist + 1: first kTcRows-candidate tile of each bucket
     int64_t total_slots;
     int32_t D, Dpad, nb, nlist, dtype, tc_parts;
+    int32_t ids32;             // every id is in [0, 2^31 - 1): the merges sort 32-bit ids
 };
 
 // A wave of probe ranks (tested against one tau) is scanned in one or more

@@ -66,29 +66,47 @@ __device__ uint32_t warp_kth_key(Key keys, int n, int k, int* hist, int lane) {
 // A warp holds 128 (key, id) entries, entry e = 32 r + lane in slot r of
 // lane `lane`, ordered by (key, id).  Bitonic networks over them exchange
 // across lanes with shuffles and across slots with swaps.
+// Ent carries a 64-bit id; Ent32 a 32-bit one (fewer shuffles and
+// registers) where every id fits.
 struct Ent {
     float d;
     long long id;
 };
-__device__ __forceinline__ bool ent_less(const Ent& a, const Ent& b) { return a.d < b.d || (a.d == b.d && a.id < b.id); }
-__device__ __forceinline__ Ent shfl_xor_ent(const Ent& x, int m) {
-    Ent y;
+struct Ent32 {
+    float d;
+    int id;
+};
+template <class E>
+__device__ __forceinline__ bool ent_less(const E& a, const E& b) { return a.d < b.d || (a.d == b.d && a.id < b.id); }
+template <class E>
+__device__ __forceinline__ E shfl_xor_ent(const E& x, int m) {
+    E y;
     y.d = __shfl_xor_sync(0xffffffffu, x.d, m);
     y.id = __shfl_xor_sync(0xffffffffu, x.id, m);
     return y;
 }
-__device__ __forceinline__ Ent shfl_ent(const Ent& x, int src) {
-    Ent y;
+template <class E>
+__device__ __forceinline__ E shfl_ent(const E& x, int src) {
+    E y;
     y.d = __shfl_sync(0xffffffffu, x.d, src);
     y.id = __shfl_sync(0xffffffffu, x.id, src);
+    return y;
+}
+// the padding entry (after every real one)
+template <class E>
+__device__ __forceinline__ E ent_pad() {
+    E y;
+    y.d = INFINITY;
+    y.id = sizeof(y.id) == 8 ? (decltype(y.id))LLONG_MAX : (decltype(y.id))INT_MAX;
     return y;
 }
 
 // Entry e of the 128 (slot e / 32 of lane e % 32), to every lane; the slot
 // is chosen with selects, not an indexed register array.
-__device__ __forceinline__ Ent entry_at(const Ent (&v)[4], int e) {
+template <class E>
+__device__ __forceinline__ E entry_at(const E (&v)[4], int e) {
     const int r = e >> 5;
-    Ent x = v[0];
+    E x = v[0];
     if (r == 1) x = v[1];
     if (r == 2) x = v[2];
     if (r == 3) x = v[3];
@@ -97,8 +115,8 @@ __device__ __forceinline__ Ent entry_at(const Ent (&v)[4], int e) {
 
 // One compare-exchange level (distance j) of a bitonic network over the 128
 // entries; `up(e)` tells whether the block containing entry e sorts upward.
-template <class Up>
-__device__ __forceinline__ void bitonic_level(Ent (&v)[4], int j, int lane, Up up) {
+template <class E, class Up>
+__device__ __forceinline__ void bitonic_level(E (&v)[4], int j, int lane, Up up) {
     if (j >= 32) {
         const int js = j >> 5;
 #pragma unroll
@@ -108,7 +126,7 @@ __device__ __forceinline__ void bitonic_level(Ent (&v)[4], int j, int lane, Up u
                 const bool asc = up(r * 32 + lane);
                 const bool sw = asc ? ent_less(v[p], v[r]) : ent_less(v[r], v[p]);
                 if (sw) {
-                    const Ent t = v[r];
+                    const E t = v[r];
                     v[r] = v[p];
                     v[p] = t;
                 }
@@ -118,7 +136,7 @@ __device__ __forceinline__ void bitonic_level(Ent (&v)[4], int j, int lane, Up u
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = r * 32 + lane;
-            const Ent o = shfl_xor_ent(v[r], j);
+            const E o = shfl_xor_ent(v[r], j);
             const bool lower = (lane & j) == 0;
             const bool asc = up(e);
             // the lower entry of an upward pair keeps the smaller one
@@ -129,7 +147,8 @@ __device__ __forceinline__ void bitonic_level(Ent (&v)[4], int j, int lane, Up u
     }
 }
 
-__device__ __forceinline__ void bitonic_sort128(Ent (&v)[4], int lane) {
+template <class E>
+__device__ __forceinline__ void bitonic_sort128(E (&v)[4], int lane) {
 #pragma unroll
     for (int k = 2; k <= 128; k <<= 1)
 #pragma unroll

@@ -318,6 +318,7 @@ dade_status search_impl(const dade_index* idx, const float* Q, int64_t B, const 
     ix.nlist = idx->nlist;
     ix.dtype = idx->dtype;
     ix.tc_parts = idx->tc_parts;
+    ix.ids32 = idx->ids32;
 
     const bool full = o.mode == DADE_SCAN_FULL;
     const bool pq = o.estimator == DADE_EST_PQ;

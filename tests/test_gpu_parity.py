@@ -505,3 +505,28 @@ def test_probe_selection_with_massive_ties(G):
             assert np.all(out["probes"][b, n:] == -1)
     finally:
         idx.close()
+
+
+def test_ids_beyond_32_bits(G, tiny_pre):
+    """The same index with ids 10^12 + 7 i instead of i (the merges then
+    carry 64-bit ids instead of 32-bit ones): the same results through the
+    id map, ties included (the map is increasing)."""
+    s = tiny_pre
+    inp = s["inp"]
+    X = inp["X"]
+    big = (10 ** 12 + 7 * np.arange(len(X))).astype(np.int64)
+    a = H.build_gpu(G, None, inp, s["cfg"]["nlist"])
+    b = G.ivf_build(X, inp["mu"], inp["R"], s["cfg"]["nlist"], centroids=inp["C32"], assign=inp["assign"], ids=big)
+    try:
+        G.dade_set_correction(b, 16, inp["m1"], inp["beta"])
+        for kw in (dict(K=10, nprobe=8), dict(K=100, nprobe=16)):
+            ra = H.gpu_search(G, a, s["Q"], kw["K"], kw["nprobe"], 16, first_wave=2, growth=30, want=("stats",))
+            rb = H.gpu_search(G, b, s["Q"], kw["K"], kw["nprobe"], 16, first_wave=2, growth=30, want=("stats",))
+            assert ra["status"] == 0 and rb["status"] == 0
+            mapped = np.where(ra["ids"] >= 0, big[np.maximum(ra["ids"], 0)], -1)
+            assert np.array_equal(mapped, rb["ids"])
+            assert np.array_equal(ra["dists"], rb["dists"])
+            assert np.array_equal(ra["stats"], rb["stats"])
+    finally:
+        a.close()
+        b.close()
