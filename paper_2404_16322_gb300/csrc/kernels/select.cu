@@ -167,24 +167,24 @@ __device__ void select128_row(const float* __restrict__ row, int n, int np, int 
         }
         kbin = __shfl_sync(0xffffffffu, kb, src);
     }
-    Ent a[4];
+    Ent32 a[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         a[r].d = INFINITY;
-        a[r].id = LLONG_MAX;
+        a[r].id = INT_MAX;
     }
     int total = 0, i0 = 0;
     while (i0 < n) {
-        Ent kth;
+        Ent32 kth;
         kth.d = INFINITY;
-        kth.id = LLONG_MAX;
+        kth.id = INT_MAX;
         if (total >= np) kth = entry_at(a, np - 1);
         int m = 0;
         for (; i0 < n && m < 128; i0 += 32) {
             const int i = i0 + lane;
-            Ent x;
+            Ent32 x;
             x.d = INFINITY;
-            x.id = LLONG_MAX;
+            x.id = INT_MAX;
             bool keep = false;
             if (i < n) {
                 x.d = row[i];
@@ -216,18 +216,18 @@ __device__ void select128_row(const float* __restrict__ row, int n, int np, int 
         }
         __syncwarp();
         if (m == 0) break;
-        Ent c[4];
+        Ent32 c[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = r * 32 + lane;
             c[r].d = e < m ? sd[e] : INFINITY;
-            c[r].id = e < m ? si[e] : LLONG_MAX;
+            c[r].id = e < m ? si[e] : INT_MAX;
         }
         __syncwarp();
         bitonic_sort128(c, lane);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const Ent cr = shfl_ent(c[3 - r], 31 - lane);
+            const Ent32 cr = shfl_ent(c[3 - r], 31 - lane);
             if (ent_less(cr, a[r])) a[r] = cr;
         }
 #pragma unroll
