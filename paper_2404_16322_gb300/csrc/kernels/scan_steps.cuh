@@ -551,6 +551,57 @@ __device__ __forceinline__ void append_uniform(const WaveView& wv, int w, int q,
     }
 }
 
+// Append this lane's candidate (slot `slot`, valid or not) against every query
+// g < nq of the unit whose distance pd[g] is at most tau[g].  The warp
+// reserves every query's space with one atomic instruction (lane g for query
+// qs[g]) and reads the queries' buffer offsets in the same round trip, then
+// writes query by query.
+__device__ __forceinline__ void append_rows(const WaveView& wv, int w, const int* qs, const float* tau, int nq,
+                                            bool valid, const float (&pd)[kG], int32_t slot, int lane) {
+    static_assert(kG <= 32, "lane g reserves query g's space");
+    uint32_t bits = 0u;
+    int mine = 0;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        if (g < nq) {
+            const bool app = valid && pd[g] <= tau[g];
+            bits |= (uint32_t)app << g;
+            const int cnt = __popc(__ballot_sync(0xffffffffu, app));
+            if (lane == g) mine = cnt;
+        }
+    }
+    int base_mine = 0;
+    long long off_mine = 0, cap_mine = 0;
+    if (lane < nq && mine) {
+        const int q = qs[lane];
+        base_mine = atomicAdd(&wv.cand_cnt[q], mine);
+        const int64_t* co = wv.cand_off + (int64_t)w * (wv.B + 1);
+        off_mine = co[q];
+        cap_mine = co[q + 1] - off_mine;
+    }
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        if (g < nq) {
+            const bool app = (bits >> g) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, app);
+            if (bal) {
+                const int base = __shfl_sync(0xffffffffu, base_mine, g);
+                const long long off = __shfl_sync(0xffffffffu, off_mine, g);
+                const long long cap = __shfl_sync(0xffffffffu, cap_mine, g);
+                if (app) {
+                    const int s = base + __popc(bal & lanemask_lt());
+                    if (s < cap) {
+                        wv.cand_d[off + s] = pd[g];
+                        wv.cand_pos[off + s] = slot;
+                    } else {
+                        atomicCAS(wv.status, 0, (int)DADE_EINVAL);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Append (d, slot) to query q's candidate buffer for every lane with app set;
 // lanes of the same query share one atomic.
 __device__ __forceinline__ void append_any(const WaveView& wv, int w, int q, bool app, float d,
@@ -646,6 +697,10 @@ __global__ void __launch_bounds__(kScanThreads, (NBLK <= 2 && !FULL && !EST) ? 7
         if (s_unit >= total) break;
         const Unit un = unpack_unit(s_desc);
         const int l = un.l, t = un.t, nq = un.nq, nt = un.nt;
+        // the bucket's extent is read before the barrier below, in the same
+        // round trip as the queries' ids and bounds
+        const int64_t slot_l = ix.list_slot[l];
+        const int64_t npad = ix.list_slot[l + 1] - slot_l;
         bool my_inf = true;
         if (tid < nq) {
             const int q = wv.items[un.item + tid];
@@ -657,8 +712,6 @@ __global__ void __launch_bounds__(kScanThreads, (NBLK <= 2 && !FULL && !EST) ? 7
             s_st[tid * 4 + 1] = s_st[tid * 4 + 2] = s_st[tid * 4 + 3] = 0ull;
         }
         const bool all_inf = __syncthreads_and(my_inf);
-        const int64_t slot_l = ix.list_slot[l];
-        const int64_t npad = ix.list_slot[l + 1] - slot_l;
         const int64_t ebase = slot_l * ix.Dpad;
         const int32_t slot0 = (int32_t)(slot_l + (int64_t)t * kT);
         const uint16_t* key = sh.key + warp * kWarpCap;
@@ -673,9 +726,7 @@ __global__ void __launch_bounds__(kScanThreads, (NBLK <= 2 && !FULL && !EST) ? 7
                                                              wv.staged_bytes, want_stats, pd);
             if (!ok) break;
             const int c = warp * 32 + lane;
-#pragma unroll
-            for (int g = 0; g < kG; ++g)
-                if (g < nq) append_uniform(wv, w, s_q[g], c < nt && pd[g] <= s_tau[g], pd[g], slot0 + c, lane);
+            append_rows(wv, w, s_q, s_tau, nq, c < nt, pd, slot0 + c, lane);
             if (want_stats && tid < nq) {
                 s_st[tid * 4 + 2] += (unsigned long long)nt;
                 s_st[tid * 4 + 3] += (unsigned long long)nt * ix.D;
