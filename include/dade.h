@@ -310,7 +310,7 @@ typedef struct {
                              /* The bound grows if it would take more than 128 */
                              /* passes.  Each pass costs a scan launch's tail  */
                              /* and a merge: 20,000 requests on 10M x 96 ran   */
-                             /* 26 passes in 34 ms at 8 GiB, 2 in 19 ms at 96. */
+                             /* 26 passes in 32 ms at 8 GiB, 2 in 18 ms at 96. */
     int32_t queries_per_unit; /* at most this many queries share one staged   */
                              /* tile of a bucket (a work unit); 0: the scan    */
                              /* kernel's maximum (128 on tensor cores, 16 on   */
